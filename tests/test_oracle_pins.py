@@ -1,0 +1,477 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test ties one part of the oracle to something other than itself: the
+worked example printed in Section 2, brute force over tiny inputs by a
+different route (strings, lexicographic order, Python sets), closed forms,
+invariants of canonical k-mers, and hand-worked LCA cases.
+"""
+import collections
+import os
+import random
+import subprocess
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+COMP = {"A": "T", "C": "G", "G": "C", "T": "A"}
+
+
+def _golden(name):
+    out = []
+    with open(os.path.join(GOLD, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                out.append(line.split())
+    return out
+
+
+def _rand_seq(rng, n, alphabet="ACGT", n_rate=0.0, lower_rate=0.0):
+    s = []
+    for _ in range(n):
+        c = rng.choice(alphabet)
+        if rng.random() < n_rate:
+            c = rng.choice("NRY-")
+        elif rng.random() < lower_rate:
+            c = c.lower()
+        s.append(c)
+    return "".join(s)
+
+
+def _revcomp(s):
+    m = {"A": "T", "C": "G", "G": "C", "T": "A", "a": "t", "c": "g", "g": "c", "t": "a"}
+    return "".join(m.get(c, "N") for c in reversed(s))
+
+
+def _brute_sketch(window, k, s):
+    """s smallest distinct h1 values over the window's canonical k-mers, with
+    canonical taken as the lexicographically smaller string (A<C<G<T) of a
+    k-mer and its reverse complement, and the code read as a base-4 numeral."""
+    vals = set()
+    for p in range(len(window) - k + 1):
+        km = window[p:p + k].upper()
+        if any(c not in "ACGT" for c in km):
+            continue
+        rc = "".join(COMP[c] for c in reversed(km))
+        can = min(km, rc)
+        vals.add(oracle.h1(int(can.translate(str.maketrans("ACGT", "0123")), 4)))
+    return sorted(vals)[:s]
+
+
+# ---------------------------------------------------------------- Section 2
+def test_paper_worked_minhash_example():
+    """Section 2: ACTGACTG, k=4, s=2, toy hashes 14, 8, 7, 11, 14 -> {7, 8}."""
+    g = _golden("minhash_example.txt")
+    seq = next(l[1] for l in g if l[0] == "sequence")
+    k = int(next(l[1] for l in g if l[0] == "k"))
+    s = int(next(l[1] for l in g if l[0] == "s"))
+    expect = [int(x) for x in next(l[1:] for l in g if l[0] == "select")]
+    lut = np.full(4 ** k, 0xFFFFFFF0, dtype=np.uint32)
+    for l in g:
+        if l[0] == "hash":
+            # table addressed by the forward code, first base most significant
+            lut[int(l[1].translate(str.maketrans("ACGT", "0123")), 4)] = int(l[2])
+    assert sorted(oracle.sketch_custom(seq, k, s, canonical=False, lut=lut)) == sorted(expect)
+    # the repeated ACTG is counted once: 4 distinct values out of 5 k-mers
+    assert oracle.sketch_custom(seq, k, 8, canonical=False, lut=lut) == [7, 8, 11, 14]
+
+
+# ------------------------------------------------------- encoding, k-mers
+def test_kmer_codes_hand_computed():
+    # A=0 C=1 G=2 T=3, first base most significant
+    assert oracle.kmer("ACGT", 4) == (0b00011011, 0b00011011, 0b00011011)  # ACGT is its own revcomp
+    f, r, c = oracle.kmer("AAAC", 4)
+    assert (f, r, c) == (1, 0b10111111, 1)  # revcomp GTTT = 2,3,3,3
+    f, r, c = oracle.kmer("tttt", 4)
+    assert (f, r, c) == (255, 0, 0)  # lower case like upper case; revcomp AAAA
+    assert oracle.kmer("ACNT", 4) is None
+    assert oracle.kmer("ACGX", 4) is None
+    f, r, c = oracle.kmer("G" * 16, 16)
+    assert f == 0xAAAAAAAA and r == 0x55555555 and c == r
+
+
+def test_palindromes_are_their_own_canonical():
+    for km in ["ACGT", "AATT", "GATC", "GAATTC", "ACGCGT"]:
+        f, r, c = oracle.kmer(km, len(km))
+        assert f == r == c
+
+
+@pytest.mark.parametrize("k", [1, 5, 11, 16])
+def test_canonical_invariance_on_random_kmers(k):
+    rng = random.Random(k)
+    for _ in range(500):
+        km = _rand_seq(rng, k)
+        f, r, c = oracle.kmer(km, k)
+        f2, r2, c2 = oracle.kmer(_revcomp(km), k)
+        assert (f2, r2) == (r, f) and c2 == c == min(f, r)
+
+
+# ------------------------------------------------------------------- h1
+def test_h1_is_a_bijection_exhaustive(tmp_path):
+    """h1 maps all 2^32 words to 2^32 distinct words, so distinct canonical
+    k-mers never tie in a sketch."""
+    lib = oracle.build()
+    exe = str(tmp_path / "h1_bijective")
+    subprocess.check_call(["gcc", "-O2", "-pthread", "-o", exe,
+                           os.path.join(os.path.dirname(__file__), "support", "h1_bijective.c"),
+                           lib, f"-Wl,-rpath,{os.path.dirname(lib)}"])
+    out = subprocess.check_output([exe], timeout=600).decode().strip()
+    assert int(out) == 1 << 32
+
+
+def test_h1_matches_published_lowbias32_structure():
+    """Undo the published steps of lowbias32 (xor-shift 16, multiply by
+    0x7feb352d, xor-shift 15, multiply by 0x846ca68b, xor-shift 16) in reverse
+    order with modular inverses; every value must come back."""
+    M = 1 << 32
+
+    def unxorshift(y, s):
+        x = y
+        for _ in range(32 // s + 1):
+            x = y ^ (x >> s)
+        return x & (M - 1)
+
+    inv1, inv2 = pow(0x7feb352d, -1, M), pow(0x846ca68b, -1, M)
+    rng = random.Random(7)
+    for x in [0, 1, 2, 0xFFFFFFFF, 0x80000000] + [rng.getrandbits(32) for _ in range(2000)]:
+        y = oracle.h1(x)
+        y = unxorshift(y, 16)
+        y = (y * inv2) % M
+        y = unxorshift(y, 15)
+        y = (y * inv1) % M
+        y = unxorshift(y, 16)
+        assert y == x
+    assert oracle.h1(0) == 0  # xor-shift / multiply fixes 0
+
+
+def test_h1_avalanche():
+    """Each input bit flips each output bit with probability close to 1/2."""
+    rng = random.Random(3)
+    xs = [rng.getrandbits(32) for _ in range(3000)]
+    flips = np.zeros((32, 32))
+    for x in xs:
+        hx = oracle.h1(x)
+        for i in range(32):
+            d = hx ^ oracle.h1(x ^ (1 << i))
+            for j in range(32):
+                flips[i, j] += (d >> j) & 1
+    p = flips / len(xs)
+    assert 0.4 < p.min() and p.max() < 0.6
+
+
+# -------------------------------------------------------------- windows
+def test_window_count_closed_form_and_paper_arithmetic():
+    # Section 4.2 defaults: w=127, k=16, overlap k-1 -> stride 112
+    assert 127 - 16 + 1 == 112
+    for L in list(range(0, 600)) + [10 ** 6 + 7]:
+        for k, stride in [(16, 112), (16, 113), (4, 5), (1, 1)]:
+            brute = sum(1 for j in range(L + 1) if j * stride <= L - k) if L >= k else 0
+            assert oracle.num_windows(L, k, stride) == brute
+    # Section 5.2: reads up to the window size give one window, longer reads two
+    assert oracle.num_windows(100, 16, 113) == 1
+    assert oracle.num_windows(128, 16, 113) == 1
+    assert oracle.num_windows(150, 16, 113) == 2
+
+
+def test_windows_tile_all_kmers_once():
+    """With stride = w-k+1 every k-mer start belongs to exactly one window."""
+    for k, w in [(16, 128), (4, 9), (7, 7)]:
+        stride = w - k + 1
+        for L in [k, k + 1, w, w + 1, 3 * w + 5, 1000]:
+            starts = []
+            for j in range(oracle.num_windows(L, k, stride)):
+                starts += list(range(j * stride, min(j * stride + w - k, L - k) + 1))
+            assert sorted(starts) == list(range(L - k + 1))
+
+
+def test_sliding_window_size_is_max_windows_touched():
+    """sws = the most consecutive windows the k-mer starts of a span can hit,
+    by brute force over every placement offset."""
+    k, stride = 16, 113
+    for span in range(k, 1200, 7):
+        brute = max((o + span - k) // stride - o // stride + 1 for o in range(stride))
+        assert oracle.sws(1, span, 0, k, stride) == brute
+    assert oracle.sws(1, 100, 0, 16, 113) == 2
+    assert oracle.sws(1, 150, 0, 16, 113) == 3
+    assert oracle.sws(2, 300, 0, 16, 113) == 4
+    assert oracle.sws(2, 300, 390, 16, 113) == 5
+    assert oracle.sws(1, 15, 0, 16, 113) == 0
+    assert oracle.sws(1, 300, 390, 16, 113) == oracle.sws(1, 300, 0, 16, 113)  # single-end ignores max_insert
+
+
+# ---------------------------------------------------------------- sketch
+@pytest.mark.parametrize("k,w,stride,s", [(16, 128, 113, 16), (4, 12, 5, 3), (8, 20, 13, 4), (16, 40, 7, 32),
+                                          (15, 31, 17, 5), (1, 4, 2, 2)])
+def test_sketch_matches_brute_force(k, w, stride, s):
+    rng = random.Random(k * 1000 + w)
+    for trial in range(6):
+        L = rng.randint(0, 700)
+        seq = _rand_seq(rng, L, n_rate=0.02 * (trial % 3), lower_rate=0.1 * (trial % 2))
+        win_offs, sk, cnt = oracle.sketch(seq, [0, L], k=k, sketch_size=s, window_len=w, window_stride=stride)
+        nw = sum(1 for j in range(L + 1) if j * stride <= L - k) if L >= k else 0
+        assert int(win_offs[1]) == nw
+        for j in range(nw):
+            expect = _brute_sketch(seq[j * stride: min(j * stride + w, L)], k, s)
+            assert list(sk[j][: cnt[j]]) == expect
+
+
+def test_sketch_handles_repeats_and_small_windows():
+    # a homopolymer window has one distinct k-mer: sketch size 1
+    _, sk, cnt = oracle.sketch("A" * 128, [0, 128], k=16, sketch_size=16, window_len=128, window_stride=113)
+    assert list(cnt) == [1] and sk[0][0] == oracle.h1(0)
+    # all-N window: no valid k-mer, but the window id still exists
+    _, sk, cnt = oracle.sketch("N" * 300, [0, 300], k=16, sketch_size=16, window_len=128, window_stride=113)
+    assert list(cnt) == [0, 0, 0]
+
+
+def test_sketch_reverse_complement_invariance():
+    """Section 3.1: canonical k-mers make a window and its reverse complement
+    produce the same sketch."""
+    rng = random.Random(11)
+    for _ in range(60):
+        L = rng.randint(16, 128)
+        seq = _rand_seq(rng, L, n_rate=0.01)
+        a = oracle.sketch(seq, [0, L], k=16, sketch_size=16, window_len=128, window_stride=113)
+        b = oracle.sketch(_revcomp(seq), [0, L], k=16, sketch_size=16, window_len=128, window_stride=113)
+        assert (a[1] == b[1]).all() and (a[2] == b[2]).all()
+
+
+# ------------------------------------------------------------------ build
+def _expected_buckets(seqs, params):
+    """Feature -> sorted capped location list, assembled in Python from the
+    (brute-force pinned) per-window sketches."""
+    offs = np.zeros(len(seqs) + 1, np.uint64)
+    offs[1:] = np.cumsum([len(x) for x in seqs])
+    win_offs, sk, cnt = oracle.sketch("".join(seqs), offs, **params)
+    buckets = collections.defaultdict(list)
+    for t in range(len(seqs)):
+        for j in range(int(win_offs[t + 1] - win_offs[t])):
+            w = int(win_offs[t]) + j
+            for f in sk[w][: cnt[w]]:
+                buckets[int(f)].append((t << 32) | j)
+    return {f: sorted(v)[: params["bucket_cap"]] for f, v in buckets.items()}, offs
+
+
+def test_exhaustive_lookup_on_tiny_tables():
+    rng = random.Random(5)
+    params = dict(k=8, sketch_size=4, window_len=20, window_stride=13, bucket_cap=5)
+    # three small targets over a 2-letter-rich alphabet so that features repeat
+    seqs = [_rand_seq(rng, rng.randint(50, 2500), alphabet="AACG", n_rate=0.01) for _ in range(3)]
+    seqs.append("")  # an empty target has no windows
+    seqs.append(seqs[0][:700])  # a repeated prefix gives shared features
+    expect, offs = _expected_buckets(seqs, params)
+    db = oracle.DB("".join(seqs), offs, **params)
+    keys, counts, locs = db.dump()
+    assert list(keys) == sorted(expect)
+    pos = 0
+    for key, c in zip(keys, counts):
+        assert list(locs[pos:pos + c]) == expect[int(key)]
+        pos += c
+    for key, v in expect.items():
+        got = list(db.lookup(key))
+        assert got == v
+        assert all(a < b for a, b in zip(got, got[1:]))  # strictly ascending (Section 3.1)
+    absent = set(rng.getrandbits(32) for _ in range(20000)) - set(expect)
+    absent |= {k + 1 for k in expect if k + 1 not in expect and k + 1 < 1 << 32}
+    for key in list(absent)[:5000]:
+        assert len(db.lookup(key)) == 0
+    st = db.stats()
+    assert st["n_keys"] == len(expect)
+    assert st["n_locations"] == sum(len(v) for v in expect.values())
+    assert st["n_windows"] == sum(oracle.num_windows(len(x), 8, 13) for x in seqs)
+
+
+def test_bucket_cap_keeps_the_smallest_locations():
+    """Section 3.1 cap (254 by default): a window repeated 300 times on the
+    window grid gives each of its features 300 locations; the 254 smallest
+    (target, window) pairs are kept."""
+    rng = random.Random(9)
+    unit = _rand_seq(rng, 113)
+    seq = unit * 301  # period = stride, so every window has the same content
+    L = 113 * 300 + 15
+    seq = seq[:L]
+    params = dict(k=16, sketch_size=16, window_len=128, window_stride=113, bucket_cap=254)
+    db = oracle.DB(seq, [0, L], **params)
+    st = db.stats()
+    assert st["n_windows"] == 300
+    _, sk, cnt = oracle.sketch(seq[:128], [0, 128], **params)
+    feats = list(sk[0][: cnt[0]])
+    assert len(feats) == 16 and st["n_keys"] == 16 and st["overflow_keys"] == 16
+    for f in feats:
+        assert list(db.lookup(int(f))) == list(range(254))
+    # two targets: all 150 of target 0, then the 104 smallest of target 1
+    L2 = 113 * 150 + 15
+    db2 = oracle.DB(seq[:L2] + seq[:L2], [0, L2, 2 * L2], **params)
+    expect = list(range(150)) + [(1 << 32) | j for j in range(104)]
+    for f in feats:
+        assert list(db2.lookup(int(f))) == expect
+
+
+# -------------------------------------------------------------------- LCA
+def test_lca_hand_worked_cases():
+    g = _golden("lca_tree.txt")
+    parent = [int(x) for x in next(l[1:] for l in g if l[0] == "parent")]
+    n = 0
+    for l in g:
+        if l[0] == "lca":
+            a, b, e = map(int, l[1:])
+            assert oracle.lca(parent, a, b) == e
+            n += 1
+    assert n >= 10
+    assert oracle.lca(parent, 3, oracle.NO_TAXON) == oracle.NO_TAXON
+    # a forest: two roots have no common ancestor
+    forest = [0, 0, 2, 2]
+    assert oracle.lca(forest, 1, 3) == oracle.NO_TAXON
+    assert oracle.lca(forest, 1, 0) == 0
+
+
+# -------------------------------------------------------------- classify
+@pytest.fixture(scope="module")
+def tiny():
+    w = synth.config0(n_reads=1500, n_decoys=200)
+    db = oracle.DB(w.genomes, w.goffs, **w.db_params)
+    return w, db
+
+
+def test_error_free_read_inside_one_window(tiny):
+    """A read lying inside window (t, j) hits (t, j) with every sketch
+    feature of the window that is one of the read's k-mers, so hits is at
+    least that many and t is the top target (the genomes are unrelated)."""
+    w, db = tiny
+    p = w.db_params
+    rng = random.Random(1)
+    gen = bytes(w.genomes).decode()
+    win_offs, sk, cnt = oracle.sketch(w.genomes, w.goffs, **p)
+    reads, roffs = [], [0]
+    want = []
+    for _ in range(60):
+        t = rng.randrange(w.n_targets)
+        nw = int(win_offs[t + 1] - win_offs[t])
+        j = rng.randrange(nw - 1)
+        a = int(w.goffs[t]) + j * 113 + rng.randint(0, 28)
+        read = gen[a:a + 100]
+        if rng.random() < 0.5:
+            read = _revcomp(read)
+        feats = set(int(x) for x in sk[int(win_offs[t]) + j][: cnt[int(win_offs[t]) + j]])
+        read_hashes = set()
+        for q in range(len(read) - 15):
+            km = read[q:q + 16]
+            rc = _revcomp(km)
+            read_hashes.add(oracle.h1(int(min(km, rc).translate(str.maketrans("ACGT", "0123")), 4)))
+        want.append((t, len(feats & read_hashes)))
+        reads.append(read)
+        roffs.append(roffs[-1] + 100)
+    qoffs = np.arange(len(reads) + 1, dtype=np.uint32)
+    label, hits, top = db.classify(w.parent, w.taxon_of_target, "".join(reads), np.array(roffs, np.uint64), qoffs,
+                                   **w.cls_params)
+    for (t, lower), h, tt, lab in zip(want, hits, top, label):
+        assert tt == t
+        assert h >= lower >= 4
+        assert lab == w.taxon_of_target[t]
+
+
+def test_classification_reverse_complement_invariance(tiny):
+    w, db = tiny
+    reads = bytes(w.reads).decode()
+    rc = "".join(_revcomp(reads[int(w.roffs[i]):int(w.roffs[i + 1])]) for i in range(w.n_seq))
+    a = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **w.cls_params)
+    b = db.classify(w.parent, w.taxon_of_target, rc, w.roffs, w.qoffs, **w.cls_params)
+    for x, y in zip(a, b):
+        assert (x == y).all()
+
+
+def test_hits_min_boundary(tiny):
+    w, db = tiny
+    p = dict(w.cls_params)
+    label, hits, top = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **p)
+    sel = np.nonzero(hits > 0)[0][:300]
+    for x in sorted(set(int(h) for h in hits[sel]))[:12]:
+        p_at = dict(p, hits_min=x)
+        p_above = dict(p, hits_min=x + 1)
+        la, _, _ = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **p_at)
+        lb, _, _ = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **p_above)
+        q = hits == x
+        assert (la[q] != oracle.NO_TAXON).all()
+        assert (lb[q] == oracle.NO_TAXON).all()
+
+
+def test_lca_band_boundary():
+    """Two strains of one species share most of their sequence; a read from
+    one of them has two close candidates.  Just inside the band the label is
+    the LCA (the species), just outside it is the top target's strain."""
+    w = synth.config1(seed=77, n_pairs=400, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=0)
+    db = oracle.DB(w.genomes, w.goffs, **w.db_params)
+    p = dict(w.cls_params, hits_min=1)
+    label, hits, top, cands = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, with_cands=True,
+                                          **p)
+    checked = 0
+    for q in range(w.n_queries):
+        c = cands[q]
+        a, b = int(c[0][0]), int(c[1][0])
+        if b == 0 or a == b:
+            continue
+        band = 100 - (100 * b) // a  # smallest band that makes the runner-up close
+        if band < 1 or band > 100:
+            continue
+        close = [int(x[1]) for x in c if x[0] > 0 and 100 * int(x[0]) >= (100 - band) * a]
+        expect_in = w.taxon_of_target[close[0]]
+        for t in close[1:]:
+            expect_in = oracle.lca(w.parent, expect_in, int(w.taxon_of_target[t]))
+        la = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **dict(p, lca_band_pct=band))[0]
+        lb = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs,
+                         **dict(p, lca_band_pct=band - 1))[0]
+        assert la[q] == expect_in
+        assert lb[q] == w.taxon_of_target[int(c[0][1])]
+        checked += 1
+        if checked >= 8:
+            break
+    assert checked >= 3
+
+
+def test_classify_brute_force_tiny():
+    """Window count statistic and sliding-window candidates recomputed from
+    the raw bucket lists with Python counters, every window offset tried."""
+    w = synth.config1(seed=5, n_pairs=300, n_families=1, genera_per_family=1, len_scale=0.01, held_genera=0)
+    p = w.db_params
+    db = oracle.DB(w.genomes, w.goffs, **p)
+    cp = dict(w.cls_params, max_candidates=4)
+    label, hits, top, cands = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, with_cands=True,
+                                          **cp)
+    reads = bytes(w.reads).decode()
+    for q in range(w.n_queries):
+        mates = [reads[int(w.roffs[i]):int(w.roffs[i + 1])] for i in range(int(w.qoffs[q]), int(w.qoffs[q + 1]))]
+        hist = collections.Counter()
+        for m in mates:
+            for j in range(oracle.num_windows(len(m), 16, 113)):
+                for f in _brute_sketch(m[j * 113: j * 113 + 128], 16, 16):
+                    for loc in db.lookup(f):
+                        hist[int(loc)] += 1
+        span = sum(len(m) for m in mates)
+        span = max(span, cp["max_insert"]) if len(mates) > 1 else span
+        sws = -(-(span - 16) // 113) + 1
+        best = {}
+        for loc in hist:
+            t, j0 = loc >> 32, loc & 0xFFFFFFFF
+            sc = sum(hist.get((t << 32) | (j0 + d), 0) for d in range(sws))
+            if t not in best or sc > best[t][0] or (sc == best[t][0] and j0 < best[t][1]):
+                best[t] = (sc, j0)
+        order = sorted(best.items(), key=lambda kv: (-kv[1][0], kv[0]))[: cp["max_candidates"]]
+        got = [(int(c[1]), int(c[0]), int(c[2])) for c in cands[q] if c[0] > 0]
+        assert got == [(t, sc, j0) for t, (sc, j0) in order]
+        assert hits[q] == (order[0][1][0] if order else 0)
+
+
+def test_tiny_workload_is_classified_sensibly(tiny):
+    """Whole-pipeline sanity on the tiny synthetic workload: reads from a
+    strain are labelled with that strain, decoys are not classified."""
+    w, db = tiny
+    label, hits, top = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, **w.cls_params)
+    real = w.truth != synth.NO_GENOME
+    ok = label[real] == w.taxon_of_target[w.truth[real]]
+    assert ok.mean() > 0.9
+    assert (label[~real] == oracle.NO_TAXON).mean() > 0.95
