@@ -1,0 +1,248 @@
+/*
+ * mc.h -- C ABI of the GB300 (sm_103a) MetaCache-GPU hot path.
+ *
+ * MetaCache-GPU (Kobus et al., arXiv 2106.08150) classifies short DNA reads
+ * against a database of reference genomes ("targets").  The database maps
+ * minhash features of reference windows to the locations (target, window)
+ * they occur in (Section 3.1); classification sketches each read, looks its
+ * features up, accumulates the hit locations and labels the read by its top
+ * candidate or by the lowest common ancestor (LCA) of the close candidates
+ * in a taxonomy (Section 3.2).  Every step of both halves runs in CUDA
+ * kernels of this library.
+ *
+ * Conventions for every function:
+ *  - Return value: an mc_status code (MC_OK = 0).  On error a message is
+ *    available from mc_last_error_string() (per calling thread).  No call
+ *    traps or aborts; device-detected errors are written to a status word
+ *    that the library reads back.
+ *  - "device" pointers are CUDA global-memory pointers on the current
+ *    device; "host" pointers are ordinary CPU memory.  Inputs are owned by
+ *    the caller and only read during the call (stream-ordered for device
+ *    inputs); outputs are caller-allocated.
+ *  - Sequences are ASCII bytes; A/C/G/T in either case are bases, every
+ *    other byte is an invalid base (Section 4.2 step 1: "N" and friends).
+ *  - Streams are cudaStream_t values passed as void* (NULL = legacy stream).
+ *
+ * Build and query order: mc_db_create -> mc_db_add_targets (one or more
+ * calls) -> mc_db_finalize -> mc_classify (any number of calls) ->
+ * mc_db_free.  mc_db_add_targets after mc_db_finalize extends the database
+ * (new targets get the next ids); the extension becomes visible to
+ * mc_classify at the next mc_db_finalize.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MC_API_VERSION 1
+
+/* Status codes returned by every entry point. */
+typedef enum mc_status {
+    MC_OK = 0,
+    MC_ERR_ARG = 1,        /* invalid argument (range, null pointer, layout) */
+    MC_ERR_STATE = 2,      /* call not allowed in the database's state */
+    MC_ERR_OOM = 3,        /* device allocation failed or budget exceeded */
+    MC_ERR_TABLE_FULL = 4, /* a table could not hold the data */
+    MC_ERR_TIMEOUT = 5,    /* a bounded device wait gave up */
+    MC_ERR_CUDA = 6,       /* a CUDA runtime call failed */
+    MC_ERR_CAPACITY = 7    /* a size limit of this library was exceeded */
+} mc_status;
+
+#define MC_NO_TAXON 0xFFFFFFFFu  /* label of an unclassified read */
+#define MC_NO_TARGET 0xFFFFFFFFu /* top target of a read without hits */
+
+/* Limits of this implementation. */
+#define MC_MAX_K 16               /* k-mers are packed in 32-bit words */
+#define MC_MAX_SKETCH 32          /* one feature per lane of a warp */
+#define MC_MAX_WINDOW_KMERS 512   /* w - k + 1 */
+#define MC_MAX_CANDIDATES 8       /* m, top hits kept per read */
+#define MC_MAX_QUERY_WINDOWS 64   /* windows of all mates of one query */
+
+typedef struct mc_db mc_db; /* opaque; owns every device allocation it makes */
+
+/* Database parameters, fixed at mc_db_create (Section 4.2: defaults k = 16,
+ * s = 16, window 127 with overlap k-1; the paper's GPU kernels also require
+ * stride % 4 == 0 and w <= 128, which this library does not). */
+typedef struct mc_db_params {
+    uint32_t k;             /* k-mer length, 1..16 */
+    uint32_t sketch_size;   /* s: features per window, 1..32 (Section 3.1) */
+    uint32_t window_len;    /* w: bases per window, k..k+511 (Section 3.1) */
+    uint32_t window_stride; /* distance of window starts, 1..w-k+1 (Section 3.1: w-k+1) */
+    uint32_t bucket_cap;    /* locations kept per feature, 1..65535 (Section 3.1: 254);
+                               the smallest (target, window) pairs are kept */
+    uint32_t reserved;      /* must be 0 */
+    uint64_t max_locations; /* optional capacity hint (0 = none) */
+    uint64_t hbm_budget;    /* bytes the database may hold on the device (0 = no limit) */
+} mc_db_params;
+
+/* Classification parameters, per mc_classify call (Section 3.2). */
+typedef struct mc_classify_params {
+    uint32_t max_candidates; /* m: top hits kept, 1..8 (Section 3.2: usually 2..4) */
+    uint32_t hits_min;       /* minimum top score to classify (Section 5.6: hit threshold) */
+    uint32_t lca_band_pct;   /* 0..100: candidates with score >= (100-band)% of the top score
+                                are "close"; one close candidate -> its taxon, several -> LCA */
+    uint32_t max_insert;     /* read pairs: sliding-window span is max(len1+len2, max_insert) */
+} mc_classify_params;
+
+/* Device memory provider.  alloc returns device memory of at least `bytes`
+ * usable in stream order on `stream` (NULL on failure); free releases it in
+ * stream order.  A provider such as PyTorch's caching allocator can back
+ * every allocation of the library. */
+typedef struct mc_allocator {
+    void* (*alloc)(void* ctx, size_t bytes, void* stream);
+    void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);
+    void* ctx;
+} mc_allocator;
+
+/* Process-wide allocator (NULL restores the default, cudaMallocAsync /
+ * cudaFreeAsync).  Set it before creating databases; a database frees its
+ * memory with the allocator it was created with. */
+int mc_set_allocator(const mc_allocator* allocator);
+
+/* Creates an empty database.
+ *  params : host; validated as documented in mc_db_params.
+ *  n_taxa : number of taxonomy nodes (>= 1); taxon ids are 0..n_taxa-1.
+ *  parent : host, n_taxa entries; parent[x] is x's parent, a root has
+ *           parent[x] == x (NCBI-style tree, Section 3.1).  Cycles are
+ *           rejected with MC_ERR_ARG.
+ *  stream : stream for every build-side call of this database.
+ *  out    : host; receives the handle.
+ * The per-taxon lineage table used for constant-time LCA (Section 3.2) is
+ * built on the device here.  Synchronises `stream`. */
+int mc_db_create(const mc_db_params* params, uint32_t n_taxa, const uint32_t* parent, void* stream,
+                 mc_db** out);
+
+/* Adds targets (reference sequences) to the database (Section 3.1 build
+ * phase, Section 4.2 build pipeline: encode, canonical k-mers, h1, sketch,
+ * insert).
+ *  n_targets : number of sequences in this call (may be 0).
+ *  seq       : device, ASCII bases of all targets back to back.
+ *  offs      : device, n_targets+1 byte offsets into seq, non-decreasing;
+ *              target i is seq[offs[i] .. offs[i+1]).
+ *  taxon     : host, n_targets taxon ids (< n_taxa, or MC_NO_TAXON).
+ *  first_target_id : host out (nullable); ids are assigned densely in
+ *              call order, so target i of this call gets *first + i.
+ * Each target is cut into windows of window_len bases at multiples of
+ * window_stride; window j of a target is location (target, j).  The inputs
+ * are read before the call returns (synchronises the database stream).
+ * MC_ERR_CAPACITY if the database would exceed 2^32-2 windows or 2^32-2
+ * targets. */
+int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint64_t* offs,
+                      const uint32_t* taxon, uint32_t* first_target_id);
+
+/* Publishes everything added so far in the condensed query layout
+ * (Section 3.2 / 4.1: all buckets in one contiguous array, a single-value
+ * hash table from feature to bucket).  Each feature keeps its bucket_cap
+ * smallest locations, sorted ascending.  Idempotent; required before
+ * mc_classify.  Synchronises the database stream. */
+int mc_db_finalize(mc_db* db);
+
+/* Classifies queries (Section 3.2 query phase, Section 4.2 query steps 1-8).
+ *  params    : host.
+ *  n_seq     : number of sequences (mates) in seq.
+ *  seq       : device, ASCII bases of all mates back to back.
+ *  offs      : device, n_seq+1 byte offsets into seq (non-decreasing).
+ *  n_queries : number of queries.
+ *  qoffs     : device, n_queries+1 indices into the sequences: query q is
+ *              mates qoffs[q] .. qoffs[q+1]-1 (1 = single-end, 2 = pair;
+ *              all windows of all mates of a query form one hit list).
+ *              At most MC_MAX_QUERY_WINDOWS windows per query.
+ *  label     : device out, n_queries taxon ids or MC_NO_TAXON.
+ *  hits      : device out, n_queries top scores (0 without hits).
+ *  top_target: device out (nullable), n_queries target ids or MC_NO_TARGET.
+ *  stream    : stream for this call.
+ * Asynchronous: returns after enqueueing.  The call waits (on the device)
+ * for the last mc_db_finalize.  Device-detected errors of a call are
+ * reported by mc_classify_status.  The database must not be changed while
+ * calls are in flight. */
+int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
+                uint32_t* hits, uint32_t* top_target, void* stream);
+
+/* Synchronises `stream` and returns (and clears) the first device-detected
+ * error of earlier mc_classify calls of this database (MC_ERR_CAPACITY for
+ * a query with more distinct hit locations than the largest per-query
+ * histogram holds, or more windows than MC_MAX_QUERY_WINDOWS). */
+int mc_classify_status(const mc_db* db, void* stream);
+
+/* Releases the database and all its device memory (synchronises its stream). */
+void mc_db_free(mc_db* db);
+
+/* ---------------------------------------------------------------------
+ * Inspection and test exports.
+ * ------------------------------------------------------------------- */
+
+typedef struct mc_db_stats_t {
+    uint64_t n_targets;
+    uint64_t n_windows;         /* all windows of all targets */
+    uint64_t n_pairs;           /* (feature, location) pairs offered */
+    uint64_t n_keys;            /* distinct features */
+    uint64_t n_locations;       /* locations stored after the cap */
+    uint64_t overflow_keys;     /* features that had more than bucket_cap locations */
+    uint64_t dropped_locations; /* n_pairs - n_locations */
+    uint64_t table_slots;       /* slots of the feature table */
+    uint64_t max_probe;         /* longest probe distance in the feature table */
+    uint64_t device_bytes;      /* bytes held on the device */
+    double load_factor;         /* n_keys / table_slots */
+    uint32_t finalized;         /* 1 if no additions are pending */
+    uint32_t max_depth;         /* deepest taxonomy level */
+} mc_db_stats_t;
+
+/* Fills *out (host) with the database's counters (no synchronisation). */
+int mc_db_stats(const mc_db* db, mc_db_stats_t* out);
+
+/* Canonical dump of the finalized database: features f with
+ * key_lo <= f < key_hi in ascending order, each with its bucket in
+ * ascending order.  Host outputs: keys[n], counts[n], locs (concatenated
+ * buckets, (target << 32) | window).  If more than max_keys features or
+ * max_locs locations qualify, nothing is written and MC_ERR_CAPACITY is
+ * returned with *n_keys / *n_locs set to the required sizes.
+ * Synchronises the database stream. */
+int mc_db_dump(const mc_db* db, uint64_t key_lo, uint64_t key_hi, uint64_t max_keys, uint64_t max_locs,
+               uint32_t* keys, uint32_t* counts, uint64_t* locs, uint64_t* n_keys, uint64_t* n_locs);
+
+/* Window layout of sequences (Section 3.1): win_offs (device out, n_seq+1)
+ * receives the exclusive prefix sum of ceil((L-k+1)/stride) (0 if L < k).
+ * Asynchronous on `stream`. */
+int mc_window_offsets(const mc_db_params* params, uint32_t n_seq, const uint64_t* offs, uint64_t* win_offs,
+                      void* stream);
+
+/* Minhash sketches of every window (Section 2, Section 4.2 steps 1-3):
+ * sketch[w * sketch_size + i] (device out) = i-th smallest distinct h1
+ * value of window w's valid canonical k-mers, 0 past counts[w] (device
+ * out, n_windows).  win_offs from mc_window_offsets; n_windows =
+ * win_offs[n_seq].  Asynchronous on `stream`. */
+int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const uint64_t* offs,
+              const uint64_t* win_offs, uint64_t n_windows, uint32_t* sketch, uint32_t* counts,
+              void* stream);
+
+/* mc_classify with test outputs.  cands (device out, nullable):
+ * n_queries x max_candidates x {score, target, first window, last window}
+ * of the top candidates (unused slots: score 0, target MC_NO_TARGET).
+ * counters (device out, nullable, 4 x uint64, accumulated): features looked
+ * up, locations gathered, distinct locations, queries sent to the
+ * large-histogram path. */
+int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                      const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
+                      uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,
+                      void* stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* mc_last_error_string(void);
+
+/* Name of a status code. */
+const char* mc_status_string(int status);
+
+/* MC_API_VERSION of the loaded library. */
+int mc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

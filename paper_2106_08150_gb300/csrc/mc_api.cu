@@ -1,0 +1,586 @@
+// C ABI of the library (include/mc.h): argument checking, device memory
+// ownership and the orchestration of the build and query kernels.  Every
+// step of the method itself runs in the kernels of mc_build.cu and
+// mc_classify.cu; this file only validates, allocates, copies metadata and
+// launches.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <numeric>
+#include <vector>
+
+#include "mc_internal.h"
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+int fail(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    cudaGetLastError();  // clear sticky-free errors
+    if (e == cudaErrorMemoryAllocation) return fail(MC_ERR_OOM, "%s: out of device memory", what);
+    return fail(MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define MC_CU(call)                                   \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+void* default_alloc(void*, size_t bytes, void* stream) {
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, (cudaStream_t)stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void default_free(void*, void* p, size_t, void* stream) { cudaFreeAsync(p, (cudaStream_t)stream); }
+
+std::mutex g_alloc_mu;
+mc_allocator g_alloc = {default_alloc, default_free, nullptr};
+bool g_pool_configured = false;
+
+// Keep freed blocks of the default stream-ordered pool instead of returning
+// them to the driver at every synchronisation (per-call scratch is reused).
+void configure_default_pool() {
+    if (g_pool_configured) return;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    cudaGetLastError();
+    g_pool_configured = true;
+}
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+namespace mc {
+void* Mem::alloc(size_t bytes, cudaStream_t s) const { return a.alloc(a.ctx, bytes, (void*)s); }
+void Mem::free(void* p, size_t bytes, cudaStream_t s) const {
+    if (p) a.free(a.ctx, p, bytes, (void*)s);
+}
+}  // namespace mc
+
+struct mc_db {
+    mc::Mem mem;
+    cudaStream_t stream = nullptr;
+    mc::SketchParams sp{};
+    uint32_t cap = 0;
+    uint64_t hbm_budget = 0;
+    // taxonomy
+    uint32_t n_taxa = 0;
+    DevBuf depth, lineage;
+    uint32_t lin_stride = 0, max_depth = 0;
+    // targets
+    uint32_t n_targets = 0;
+    DevBuf taxon;  // u32 per target
+    DevBuf wbase;  // u32 global window base per target, n_targets+1 entries
+    uint64_t n_windows = 0;
+    // additions not yet finalized
+    DevBuf pending;  // u64 pairs
+    uint64_t pending_n = 0, pending_real = 0;
+    // published condensed layout
+    DevBuf kept_pairs, locs, table;
+    uint64_t n_kept = 0, n_keys = 0, table_len = 0, overflow_keys = 0, n_pairs = 0;
+    uint32_t log_t = 1, max_probe = 0;
+    bool dirty = false, has_table = false;
+    cudaEvent_t ready = nullptr;
+    DevBuf status;  // u32 device status word
+};
+
+namespace {
+
+void release(mc_db* db, DevBuf& b) {
+    if (b.p) db->mem.free(b.p, b.bytes, db->stream);
+    b = DevBuf();
+}
+
+bool grab(mc_db* db, DevBuf& b, size_t bytes) {
+    b.p = bytes ? db->mem.alloc(bytes, db->stream) : nullptr;
+    b.bytes = bytes;
+    return bytes == 0 || b.p != nullptr;
+}
+
+uint64_t held_bytes(const mc_db* db) {
+    return db->depth.bytes + db->lineage.bytes + db->taxon.bytes + db->wbase.bytes + db->pending.bytes +
+           db->kept_pairs.bytes + db->locs.bytes + db->table.bytes + db->status.bytes;
+}
+
+bool within_budget(const mc_db* db, uint64_t extra) {
+    return db->hbm_budget == 0 || held_bytes(db) + extra <= db->hbm_budget;
+}
+
+// Grows b to hold at least `need` bytes, keeping the first `keep` bytes.
+int grow(mc_db* db, DevBuf& b, size_t need, size_t keep, const char* what) {
+    if (b.bytes >= need) return MC_OK;
+    size_t nb = std::max(need, b.bytes + b.bytes / 2);
+    if (!within_budget(db, nb)) return fail(MC_ERR_OOM, "%s: hbm_budget exceeded", what);
+    DevBuf n;
+    if (!grab(db, n, nb)) return fail(MC_ERR_OOM, "%s: cannot allocate %zu bytes", what, nb);
+    if (keep) MC_CU(cudaMemcpyAsync(n.p, b.p, keep, cudaMemcpyDeviceToDevice, db->stream));
+    release(db, b);
+    b = n;
+    return MC_OK;
+}
+
+int check_params(const mc_db_params* p) {
+    if (!p) return fail(MC_ERR_ARG, "params is NULL");
+    if (p->k < 1 || p->k > MC_MAX_K) return fail(MC_ERR_ARG, "k must be in 1..%d", MC_MAX_K);
+    if (p->sketch_size < 1 || p->sketch_size > MC_MAX_SKETCH)
+        return fail(MC_ERR_ARG, "sketch_size must be in 1..%d", MC_MAX_SKETCH);
+    if (p->window_len < p->k || p->window_len > 512) return fail(MC_ERR_ARG, "window_len must be in k..512");
+    if (p->window_len - p->k + 1 > MC_MAX_WINDOW_KMERS) return fail(MC_ERR_ARG, "window has too many k-mers");
+    if (p->window_stride < 1 || p->window_stride > p->window_len - p->k + 1)
+        return fail(MC_ERR_ARG, "window_stride must be in 1..window_len-k+1");
+    if (p->bucket_cap < 1 || p->bucket_cap > 65535) return fail(MC_ERR_ARG, "bucket_cap must be in 1..65535");
+    if (p->reserved != 0) return fail(MC_ERR_ARG, "reserved must be 0");
+    return MC_OK;
+}
+
+mc::SketchParams sketch_params(const mc_db_params* p) {
+    return mc::SketchParams{p->k, p->sketch_size, p->window_len, p->window_stride};
+}
+
+int check_cls(const mc_classify_params* p) {
+    if (!p) return fail(MC_ERR_ARG, "classify params is NULL");
+    if (p->max_candidates < 1 || p->max_candidates > MC_MAX_CANDIDATES)
+        return fail(MC_ERR_ARG, "max_candidates must be in 1..%d", MC_MAX_CANDIDATES);
+    if (p->lca_band_pct > 100) return fail(MC_ERR_ARG, "lca_band_pct must be in 0..100");
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_version(void) { return MC_API_VERSION; }
+
+const char* mc_last_error_string(void) { return g_err; }
+
+const char* mc_status_string(int s) {
+    switch (s) {
+        case MC_OK: return "MC_OK";
+        case MC_ERR_ARG: return "MC_ERR_ARG";
+        case MC_ERR_STATE: return "MC_ERR_STATE";
+        case MC_ERR_OOM: return "MC_ERR_OOM";
+        case MC_ERR_TABLE_FULL: return "MC_ERR_TABLE_FULL";
+        case MC_ERR_TIMEOUT: return "MC_ERR_TIMEOUT";
+        case MC_ERR_CUDA: return "MC_ERR_CUDA";
+        case MC_ERR_CAPACITY: return "MC_ERR_CAPACITY";
+        default: return "unknown";
+    }
+}
+
+int mc_set_allocator(const mc_allocator* a) {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    if (a && (!a->alloc || !a->free)) return fail(MC_ERR_ARG, "allocator needs alloc and free");
+    g_alloc = a ? *a : mc_allocator{default_alloc, default_free, nullptr};
+    return MC_OK;
+}
+
+int mc_db_create(const mc_db_params* params, uint32_t n_taxa, const uint32_t* parent, void* stream, mc_db** out) {
+    g_err[0] = 0;
+    if (!out) return fail(MC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n_taxa < 1) return fail(MC_ERR_ARG, "n_taxa must be >= 1");
+    if (!parent) return fail(MC_ERR_ARG, "parent is NULL");
+    for (uint32_t i = 0; i < n_taxa; ++i)
+        if (parent[i] >= n_taxa) return fail(MC_ERR_ARG, "parent[%u] = %u is out of range", i, parent[i]);
+    mc_db* db = new mc_db();
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        db->mem.a = g_alloc;
+        if (g_alloc.alloc == default_alloc) configure_default_pool();
+    }
+    db->stream = (cudaStream_t)stream;
+    db->sp = sketch_params(params);
+    db->cap = params->bucket_cap;
+    db->hbm_budget = params->hbm_budget;
+    db->n_taxa = n_taxa;
+    auto bail = [&](int code) {
+        mc_db_free(db);
+        return code;
+    };
+    if (cudaEventCreateWithFlags(&db->ready, cudaEventDisableTiming) != cudaSuccess)
+        return bail(cuda_fail(cudaGetLastError(), "cudaEventCreate"));
+    DevBuf d_parent, flags;
+    if (!grab(db, d_parent, (size_t)n_taxa * 4) || !grab(db, db->depth, (size_t)n_taxa * 4) ||
+        !grab(db, flags, 8) || !grab(db, db->status, 4))
+        return bail(fail(MC_ERR_OOM, "mc_db_create: allocation failed"));
+    auto free_tmp = [&]() {
+        release(db, d_parent);
+        release(db, flags);
+    };
+    uint32_t host_flags[2] = {0, 0};
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_parent.p, parent, (size_t)n_taxa * 4, cudaMemcpyHostToDevice, db->stream)) ||
+        (e = cudaMemsetAsync(flags.p, 0, 8, db->stream)) || (e = cudaMemsetAsync(db->status.p, 0, 4, db->stream)) ||
+        (e = mc::taxonomy_depths((uint32_t*)d_parent.p, n_taxa, (uint32_t*)db->depth.p, (uint32_t*)flags.p,
+                                 (uint32_t*)flags.p + 1, db->stream)) ||
+        (e = cudaMemcpyAsync(host_flags, flags.p, 8, cudaMemcpyDeviceToHost, db->stream)) ||
+        (e = cudaStreamSynchronize(db->stream))) {
+        free_tmp();
+        return bail(cuda_fail(e, "mc_db_create taxonomy"));
+    }
+    if (host_flags[1]) {
+        free_tmp();
+        return bail(fail(MC_ERR_ARG, "parent array has a cycle"));
+    }
+    db->max_depth = host_flags[0];
+    db->lin_stride = db->max_depth + 1;
+    if (!grab(db, db->lineage, (size_t)n_taxa * db->lin_stride * 4)) {
+        free_tmp();
+        return bail(fail(MC_ERR_OOM, "mc_db_create: lineage allocation failed"));
+    }
+    if ((e = mc::taxonomy_lineage((uint32_t*)d_parent.p, n_taxa, (uint32_t*)db->depth.p, (uint32_t*)db->lineage.p,
+                                  db->lin_stride, db->stream)) ||
+        (e = cudaStreamSynchronize(db->stream))) {
+        free_tmp();
+        return bail(cuda_fail(e, "mc_db_create lineage"));
+    }
+    free_tmp();
+    // window base of target 0
+    if (!grab(db, db->wbase, 4 * 1024)) return bail(fail(MC_ERR_OOM, "mc_db_create: allocation failed"));
+    if ((e = cudaMemsetAsync(db->wbase.p, 0, 4, db->stream)) || (e = cudaStreamSynchronize(db->stream)))
+        return bail(cuda_fail(e, "mc_db_create"));
+    *out = db;
+    return MC_OK;
+}
+
+int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint64_t* offs, const uint32_t* taxon,
+                      uint32_t* first_target_id) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    if (first_target_id) *first_target_id = db->n_targets;
+    if (n_targets == 0) return MC_OK;
+    if (!seq || !offs || !taxon) return fail(MC_ERR_ARG, "seq, offs and taxon must not be NULL");
+    if ((uint64_t)db->n_targets + n_targets >= 0xFFFFFFFFull) return fail(MC_ERR_CAPACITY, "too many targets");
+    for (uint32_t i = 0; i < n_targets; ++i)
+        if (taxon[i] >= db->n_taxa && taxon[i] != MC_NO_TAXON)
+            return fail(MC_ERR_ARG, "taxon[%u] = %u is out of range", i, taxon[i]);
+    cudaStream_t s = db->stream;
+    mc::Tmp<uint64_t> win_offs(db->mem, (size_t)n_targets + 1, s);
+    mc::Tmp<unsigned long long> ctr(db->mem, 2, s);
+    if (!win_offs.ok() || !ctr.ok()) return fail(MC_ERR_OOM, "mc_db_add_targets: allocation failed");
+    MC_CU(cudaMemsetAsync(ctr.ptr, 0, 16, s));
+    MC_CU(mc::window_offsets(db->mem, db->sp, n_targets, offs, win_offs.ptr, (uint32_t*)ctr.ptr, s));
+    uint64_t nw = 0;
+    unsigned long long bad = 0;
+    MC_CU(cudaMemcpyAsync(&nw, win_offs.ptr + n_targets, 8, cudaMemcpyDeviceToHost, s));
+    MC_CU(cudaMemcpyAsync(&bad, ctr.ptr, 8, cudaMemcpyDeviceToHost, s));
+    MC_CU(cudaStreamSynchronize(s));
+    if (bad) return fail(MC_ERR_ARG, "offs must be non-decreasing");
+    if (db->n_windows + nw >= 0xFFFFFFFFull) return fail(MC_ERR_CAPACITY, "more than 2^32-2 windows");
+    int rc;
+    const uint32_t t0 = db->n_targets;
+    if ((rc = grow(db, db->taxon, (size_t)(t0 + n_targets) * 4, (size_t)t0 * 4, "taxon"))) return rc;
+    if ((rc = grow(db, db->wbase, (size_t)(t0 + n_targets + 1) * 4, (size_t)(t0 + 1) * 4, "wbase"))) return rc;
+    const uint64_t npairs = nw * db->sp.s;
+    if ((rc = grow(db, db->pending, (db->pending_n + npairs) * 8, db->pending_n * 8, "pending pairs"))) return rc;
+    MC_CU(cudaMemcpyAsync((uint32_t*)db->taxon.p + t0, taxon, (size_t)n_targets * 4, cudaMemcpyHostToDevice, s));
+    // global window bases of the new targets: n_windows + win_offs[i]
+    {
+        std::vector<uint64_t> h(n_targets + 1);
+        MC_CU(cudaMemcpyAsync(h.data(), win_offs.ptr, h.size() * 8, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaStreamSynchronize(s));
+        std::vector<uint32_t> wb(n_targets + 1);
+        for (uint32_t i = 0; i <= n_targets; ++i) wb[i] = (uint32_t)(db->n_windows + h[i]);
+        MC_CU(cudaMemcpyAsync((uint32_t*)db->wbase.p + t0, wb.data(), wb.size() * 4, cudaMemcpyHostToDevice, s));
+        MC_CU(mc::emit_pairs(db->sp, n_targets, (const uint8_t*)seq, offs, win_offs.ptr, nw, (uint32_t)db->n_windows,
+                             (uint64_t*)db->pending.p + db->pending_n, ctr.ptr + 1, s));
+        unsigned long long real = 0;
+        MC_CU(cudaMemcpyAsync(&real, ctr.ptr + 1, 8, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaStreamSynchronize(s));
+        db->pending_n += npairs;
+        db->pending_real += real;
+    }
+    db->n_windows += nw;
+    db->n_targets += n_targets;
+    db->dirty = true;
+    return MC_OK;
+}
+
+int mc_db_finalize(mc_db* db) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    if (!db->dirty && db->has_table) return MC_OK;
+    cudaStream_t s = db->stream;
+    const uint64_t n_old = db->n_kept;
+    const uint64_t n_total = n_old + db->pending_n;
+    const uint64_t n_real = n_old + db->pending_real;
+    // sort input: previously kept pairs (sorted) followed by the new pairs
+    DevBuf a, b;
+    if (n_old == 0) {
+        a = db->pending;
+        db->pending = DevBuf();
+    } else {
+        if (!within_budget(db, n_total * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
+        if (!grab(db, a, n_total * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
+        MC_CU(cudaMemcpyAsync(a.p, db->kept_pairs.p, n_old * 8, cudaMemcpyDeviceToDevice, s));
+        if (db->pending_n)
+            MC_CU(cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s));
+        release(db, db->pending);
+    }
+    auto cleanup = [&]() {
+        release(db, a);
+        release(db, b);
+    };
+    if (!grab(db, b, n_total * 8)) {
+        cleanup();
+        return fail(MC_ERR_OOM, "finalize: allocation failed");
+    }
+    cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)a.p, (uint64_t*)b.p, n_total, n_real, s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return cuda_fail(e, "finalize: sort");
+    }
+    release(db, b);
+    mc::FinalizeOut fo;
+    e = mc::finalize_pairs(db->mem, (const uint64_t*)a.p, n_real, db->cap, (const uint32_t*)db->wbase.p,
+                           db->n_targets, &fo, s);
+    cleanup();
+    if (e != cudaSuccess) return cuda_fail(e, "finalize: layout");
+    release(db, db->kept_pairs);
+    release(db, db->locs);
+    release(db, db->table);
+    db->kept_pairs = DevBuf{fo.kept_pairs, fo.n_kept * 8};
+    db->locs = DevBuf{fo.locs, fo.n_kept * 8};
+    db->table = DevBuf{fo.table, fo.table_bytes};
+    db->n_pairs += db->pending_real;
+    db->pending_n = db->pending_real = 0;
+    db->n_kept = fo.n_kept;
+    db->n_keys = fo.n_keys;
+    db->table_len = fo.table_len;
+    db->log_t = fo.log_t;
+    db->max_probe = fo.max_probe;
+    db->overflow_keys = fo.overflow_keys;
+    db->dirty = false;
+    db->has_table = true;
+    MC_CU(cudaEventRecord(db->ready, s));
+    MC_CU(cudaStreamSynchronize(s));
+    return MC_OK;
+}
+
+static int classify_impl(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                         const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
+                         uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters, void* stream) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (!db->has_table) return fail(MC_ERR_STATE, "mc_classify before mc_db_finalize");
+    if (n_queries == 0) return MC_OK;
+    if (!seq || !offs || !qoffs || !label || !hits) return fail(MC_ERR_ARG, "NULL input or output pointer");
+    (void)n_seq;
+    cudaStream_t s = (cudaStream_t)stream;
+    MC_CU(cudaStreamWaitEvent(s, db->ready, 0));
+    mc::ClassifyDb cdb;
+    cdb.table = (const uint4*)db->table.p;
+    cdb.log_t = db->log_t;
+    cdb.max_probe = db->max_probe;
+    cdb.locs = (const uint64_t*)db->locs.p;
+    cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
+    cdb.n_targets = db->n_targets;
+    cdb.lineage = (const uint32_t*)db->lineage.p;
+    cdb.depth = (const uint32_t*)db->depth.p;
+    cdb.lin_stride = db->lin_stride;
+    cdb.n_taxa = db->n_taxa;
+    cdb.sp = db->sp;
+    mc::ClassifyQuery q;
+    q.seq = (const uint8_t*)seq;
+    q.offs = offs;
+    q.qoffs = qoffs;
+    q.n_q = n_queries;
+    q.m = params->max_candidates;
+    q.hits_min = params->hits_min;
+    q.band = params->lca_band_pct;
+    q.max_insert = params->max_insert;
+    q.label = label;
+    q.hits = hits;
+    q.top_target = top_target;
+    q.cands = cands;
+    q.counters = (unsigned long long*)counters;
+    q.status = (uint32_t*)db->status.p;
+    MC_CU(mc::classify_launch(db->mem, cdb, q, s));
+    return MC_OK;
+}
+
+int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label, uint32_t* hits,
+                uint32_t* top_target, void* stream) {
+    return classify_impl(db, params, n_seq, seq, offs, n_queries, qoffs, label, hits, top_target, nullptr, nullptr,
+                         stream);
+}
+
+int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                      const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
+                      uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters, void* stream) {
+    return classify_impl(db, params, n_seq, seq, offs, n_queries, qoffs, label, hits, top_target, cands, counters,
+                         stream);
+}
+
+int mc_classify_status(const mc_db* db, void* stream) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    MC_CU(cudaStreamSynchronize((cudaStream_t)stream));
+    uint32_t st = 0;
+    MC_CU(cudaMemcpy(&st, db->status.p, 4, cudaMemcpyDeviceToHost));
+    MC_CU(cudaMemset(db->status.p, 0, 4));
+    if (st == mc::DEV_ERR_CAPACITY)
+        return fail(MC_ERR_CAPACITY, "a query exceeded the per-query window or histogram capacity");
+    if (st) return fail(MC_ERR_ARG, "device reported status %u", st);
+    return MC_OK;
+}
+
+void mc_db_free(mc_db* db) {
+    if (!db) return;
+    cudaStreamSynchronize(db->stream);
+    release(db, db->depth);
+    release(db, db->lineage);
+    release(db, db->taxon);
+    release(db, db->wbase);
+    release(db, db->pending);
+    release(db, db->kept_pairs);
+    release(db, db->locs);
+    release(db, db->table);
+    release(db, db->status);
+    cudaStreamSynchronize(db->stream);
+    if (db->ready) cudaEventDestroy(db->ready);
+    cudaGetLastError();
+    delete db;
+}
+
+int mc_db_stats(const mc_db* db, mc_db_stats_t* out) {
+    g_err[0] = 0;
+    if (!db || !out) return fail(MC_ERR_ARG, "NULL argument");
+    std::memset(out, 0, sizeof *out);
+    out->n_targets = db->n_targets;
+    out->n_windows = db->n_windows;
+    out->n_pairs = db->n_pairs + db->pending_real;
+    out->n_keys = db->n_keys;
+    out->n_locations = db->n_kept;
+    out->overflow_keys = db->overflow_keys;
+    out->dropped_locations = out->n_pairs - db->n_kept;
+    out->table_slots = db->has_table ? (1ull << db->log_t) : 0;
+    out->max_probe = db->max_probe;
+    out->device_bytes = held_bytes(db);
+    out->load_factor = out->table_slots ? (double)db->n_keys / (double)out->table_slots : 0.0;
+    out->finalized = db->dirty ? 0 : 1;
+    out->max_depth = db->max_depth;
+    return MC_OK;
+}
+
+int mc_db_dump(const mc_db* db, uint64_t key_lo, uint64_t key_hi, uint64_t max_keys, uint64_t max_locs,
+               uint32_t* keys, uint32_t* counts, uint64_t* locs, uint64_t* n_keys, uint64_t* n_locs) {
+    g_err[0] = 0;
+    if (!db || !n_keys || !n_locs) return fail(MC_ERR_ARG, "NULL argument");
+    if (!db->has_table) return fail(MC_ERR_STATE, "mc_db_dump before mc_db_finalize");
+    cudaStream_t s = db->stream;
+    const uint64_t cap = std::max<uint64_t>(max_keys, 1);
+    mc::Tmp<uint32_t> dkeys(db->mem, cap, s), dcnt(db->mem, cap, s);
+    mc::Tmp<uint64_t> doff(db->mem, cap, s);
+    mc::Tmp<unsigned long long> dn(db->mem, 1, s);
+    if (!dkeys.ok() || !dcnt.ok() || !doff.ok() || !dn.ok()) return fail(MC_ERR_OOM, "dump: allocation failed");
+    MC_CU(cudaMemsetAsync(dn.ptr, 0, 8, s));
+    MC_CU(mc::dump_select((const uint4*)db->table.p, db->table_len, key_lo, key_hi, dkeys.ptr, doff.ptr, dcnt.ptr, cap,
+                          dn.ptr, s));
+    unsigned long long nsel = 0;
+    MC_CU(cudaMemcpyAsync(&nsel, dn.ptr, 8, cudaMemcpyDeviceToHost, s));
+    MC_CU(cudaStreamSynchronize(s));
+    *n_keys = nsel;
+    *n_locs = 0;
+    if (nsel > max_keys) return fail(MC_ERR_CAPACITY, "dump: %llu features qualify", nsel);
+    std::vector<uint32_t> hk(nsel), hc(nsel);
+    std::vector<uint64_t> ho(nsel);
+    if (nsel) {
+        MC_CU(cudaMemcpyAsync(hk.data(), dkeys.ptr, nsel * 4, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaMemcpyAsync(hc.data(), dcnt.ptr, nsel * 4, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaMemcpyAsync(ho.data(), doff.ptr, nsel * 8, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaStreamSynchronize(s));
+    }
+    std::vector<uint64_t> order(nsel);
+    std::iota(order.begin(), order.end(), 0);
+    std::sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) { return hk[x] < hk[y]; });
+    uint64_t total = 0;
+    for (uint64_t i = 0; i < nsel; ++i) total += hc[i];
+    *n_locs = total;
+    if (total > max_locs) return fail(MC_ERR_CAPACITY, "dump: %llu locations qualify", (unsigned long long)total);
+    std::vector<uint64_t> src(nsel), dst(nsel);
+    std::vector<uint32_t> cnt(nsel);
+    uint64_t acc = 0;
+    for (uint64_t i = 0; i < nsel; ++i) {
+        uint64_t o = order[i];
+        if (keys) keys[i] = hk[o];
+        if (counts) counts[i] = hc[o];
+        src[i] = ho[o];
+        cnt[i] = hc[o];
+        dst[i] = acc;
+        acc += hc[o];
+    }
+    if (locs && total) {
+        mc::Tmp<uint64_t> dsrc(db->mem, nsel, s), ddst(db->mem, nsel, s), dout(db->mem, total, s);
+        mc::Tmp<uint32_t> dc(db->mem, nsel, s);
+        if (!dsrc.ok() || !ddst.ok() || !dout.ok() || !dc.ok()) return fail(MC_ERR_OOM, "dump: allocation failed");
+        MC_CU(cudaMemcpyAsync(dsrc.ptr, src.data(), nsel * 8, cudaMemcpyHostToDevice, s));
+        MC_CU(cudaMemcpyAsync(ddst.ptr, dst.data(), nsel * 8, cudaMemcpyHostToDevice, s));
+        MC_CU(cudaMemcpyAsync(dc.ptr, cnt.data(), nsel * 4, cudaMemcpyHostToDevice, s));
+        MC_CU(mc::dump_gather((const uint64_t*)db->locs.p, dsrc.ptr, dc.ptr, ddst.ptr, nsel, dout.ptr, s));
+        MC_CU(cudaMemcpyAsync(locs, dout.ptr, total * 8, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaStreamSynchronize(s));
+    }
+    return MC_OK;
+}
+
+int mc_window_offsets(const mc_db_params* params, uint32_t n_seq, const uint64_t* offs, uint64_t* win_offs,
+                      void* stream) {
+    g_err[0] = 0;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (!win_offs || (n_seq && !offs)) return fail(MC_ERR_ARG, "NULL argument");
+    mc::Mem mem;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        mem.a = g_alloc;
+    }
+    mc::Tmp<uint32_t> bad(mem, 1, (cudaStream_t)stream);
+    if (!bad.ok()) return fail(MC_ERR_OOM, "allocation failed");
+    MC_CU(cudaMemsetAsync(bad.ptr, 0, 4, (cudaStream_t)stream));
+    MC_CU(mc::window_offsets(mem, sketch_params(params), n_seq, offs, win_offs, bad.ptr, (cudaStream_t)stream));
+    return MC_OK;
+}
+
+int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const uint64_t* offs,
+              const uint64_t* win_offs, uint64_t n_windows, uint32_t* sketch, uint32_t* counts, void* stream) {
+    g_err[0] = 0;
+    int rc = check_params(params);
+    if (rc) return rc;
+    if (n_windows == 0) return MC_OK;
+    if (!seq || !offs || !win_offs || !sketch || !counts) return fail(MC_ERR_ARG, "NULL argument");
+    MC_CU(mc::sketch_windows(sketch_params(params), n_seq, (const uint8_t*)seq, offs, win_offs, n_windows, sketch,
+                             counts, (cudaStream_t)stream));
+    return MC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,718 @@
+// Database build kernels (Section 3.1 build phase, Section 4.1 GPU hash
+// tables, Section 4.2 build pipeline) for sm_103a.
+//
+// GB300 design.  The paper inserts each (feature, location) pair into a
+// multi-bucket hash table with warp-aggregated atomics.  Here the build is
+// organised around streaming HBM passes instead of random-sector updates:
+//   1. sketch + emit: one warp per window computes its sketch (shared with
+//      the query path, mc_sketch.cuh) and writes (h2(feature) << 32 |
+//      global window) pairs in window order;
+//   2. a stable LSD radix sort (4 passes of 8 bits over the upper word)
+//      groups the pairs by feature while keeping them in window order,
+//      which is (target, window) order, so every bucket comes out sorted;
+//   3. finalize keeps the first `cap` pairs of each feature (Section 3.1:
+//      at most 254 locations per feature; the smallest are kept, as in the
+//      CPU version that inserts in ascending order), converts global windows
+//      to (target, window) locations, and lays out the condensed layout of
+//      Section 4.1: one contiguous location array plus a feature table;
+//   4. the feature table is an ordered linear-probing table built without
+//      atomics: features arrive sorted by h2, so slot(k) = max(home(k),
+//      slot(k-1)+1) = k + max_{k'<=k}(home(k') - k'), a max-scan.
+// Every step reads and writes HBM in coalesced streams; the only random
+// accesses of the whole database life are the lookups of the query path.
+#include <cstdio>
+
+#include "mc_internal.h"
+#include "mc_sketch.cuh"
+
+namespace mc {
+
+namespace {
+
+constexpr int BT = 256;  // threads of the streaming kernels
+constexpr int NWARP = BT / 32;
+
+inline uint32_t grid_for(uint64_t tiles, uint32_t per_sm = 8) {
+    uint64_t g = (uint64_t)NUM_SMS_HINT * per_sm;
+    if (tiles < g) g = tiles;
+    return (uint32_t)(g ? g : 1);
+}
+
+struct OpSum {
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a + b; }
+};
+struct OpMaxU {
+    __device__ __forceinline__ uint64_t operator()(uint64_t a, uint64_t b) const { return a > b ? a : b; }
+};
+struct OpMaxI {
+    __device__ __forceinline__ int64_t operator()(int64_t a, int64_t b) const { return a > b ? a : b; }
+};
+
+template <class T, class Op>
+__device__ __forceinline__ T warp_inclusive(T v, Op op) {
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        T o = __shfl_up_sync(FULL_MASK, v, d);
+        if ((int)lane_id() >= d) v = op(v, o);
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one value per thread (BT threads).  Returns
+// the exclusive prefix; *total receives the block aggregate.  `sm` needs
+// NWARP entries.  Contains two __syncthreads.
+template <class T, class Op>
+__device__ __forceinline__ T block_exclusive(T v, T identity, Op op, T* sm, T* total) {
+    T inc = warp_inclusive(v, op);
+    const int w = threadIdx.x >> 5;
+    const int l = lane_id();
+    if (l == 31) sm[w] = inc;
+    __syncthreads();
+    T warp_pre = identity, tot = identity;
+#pragma unroll
+    for (int i = 0; i < NWARP; ++i) {
+        T x = sm[i];
+        if (i < w) warp_pre = op(warp_pre, x);
+        tot = op(tot, x);
+    }
+    T ex = __shfl_up_sync(FULL_MASK, inc, 1);
+    if (l == 0) ex = identity;
+    *total = tot;
+    __syncthreads();
+    return op(warp_pre, ex);
+}
+
+template <class T, class Op>
+__device__ __forceinline__ T block_reduce(T v, T identity, Op op, T* sm) {
+    T tot;
+    block_exclusive(v, identity, op, sm, &tot);
+    return tot;
+}
+
+// ------------------------------------------------------------------ scan
+constexpr int SCAN_ITEMS = 8;
+constexpr uint64_t SCAN_TILE = (uint64_t)BT * SCAN_ITEMS;
+
+__global__ void __launch_bounds__(BT) k_scan_tile_sums(const uint64_t* __restrict__ in, uint64_t n,
+                                                       uint64_t* __restrict__ sums, uint64_t n_tiles) {
+    __shared__ uint64_t sm[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * SCAN_TILE, acc = 0;
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            if (e < n) acc += in[e];
+        }
+        uint64_t tot = block_reduce(acc, (uint64_t)0, OpSum(), sm);
+        if (threadIdx.x == 0) sums[tile] = tot;
+    }
+}
+
+// Exclusive scan of each tile with its prefix (tile_pre, or 0 if null).
+// The element of round i, thread t is base + i*BT + t (sequential order).
+__global__ void __launch_bounds__(BT) k_scan_downsweep(const uint64_t* in, uint64_t* out, uint64_t n,
+                                                       const uint64_t* __restrict__ tile_pre, uint64_t n_tiles,
+                                                       uint64_t* total) {
+    __shared__ uint64_t sm[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * SCAN_TILE;
+        uint64_t carry = tile_pre ? tile_pre[tile] : 0;
+        for (int i = 0; i < SCAN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            uint64_t v = e < n ? in[e] : 0;
+            uint64_t tot;
+            uint64_t ex = block_exclusive(v, (uint64_t)0, OpSum(), sm, &tot);
+            if (e < n) out[e] = carry + ex;
+            carry += tot;
+        }
+        if (tile == n_tiles - 1 && threadIdx.x == 0 && total) *total = carry;
+    }
+}
+
+}  // namespace
+
+cudaError_t scan_exclusive_sum(const Mem& mem, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t s) {
+    if (n == 0) return cudaMemsetAsync(out, 0, sizeof(uint64_t), s);
+    uint64_t n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    if (n_tiles == 1) {
+        k_scan_downsweep<<<1, BT, 0, s>>>(in, out, n, nullptr, 1, out + n);
+        return cudaGetLastError();
+    }
+    Tmp<uint64_t> sums(mem, n_tiles + 1, s);
+    if (!sums.ok()) return cudaErrorMemoryAllocation;
+    k_scan_tile_sums<<<grid_for(n_tiles), BT, 0, s>>>(in, n, sums.ptr, n_tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = scan_exclusive_sum(mem, sums.ptr, sums.ptr, n_tiles, s);
+    if (e != cudaSuccess) return e;
+    k_scan_downsweep<<<grid_for(n_tiles), BT, 0, s>>>(in, out, n, sums.ptr, n_tiles, out + n);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ window offsets
+namespace {
+__global__ void k_window_counts(const uint64_t* __restrict__ offs, uint32_t n, uint32_t k, uint32_t stride,
+                                uint64_t* __restrict__ cnt, uint32_t* bad) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint64_t a = offs[i], b = offs[i + 1];
+        if (b < a) {
+            atomicMax(bad, 1u);
+            cnt[i] = 0;
+        } else {
+            cnt[i] = num_windows(b - a, k, stride);
+        }
+    }
+}
+}  // namespace
+
+cudaError_t window_offsets(const Mem& mem, const SketchParams& p, uint32_t n_seq, const uint64_t* offs,
+                           uint64_t* win_offs, uint32_t* bad_offs, cudaStream_t s) {
+    if (n_seq > 0) {
+        k_window_counts<<<grid_for((n_seq + BT - 1) / BT), BT, 0, s>>>(offs, n_seq, p.k, p.stride, win_offs,
+                                                                         bad_offs);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return scan_exclusive_sum(mem, win_offs, win_offs, n_seq, s);
+}
+
+// ---------------------------------------------------------------- sketch
+namespace {
+constexpr uint32_t WINDOWS_PER_TASK = 16;
+
+// One warp per window; a warp takes WINDOWS_PER_TASK consecutive windows
+// and walks the sequences they belong to.  EMIT = build pairs, else the
+// debug sketch export.
+template <int R, bool EMIT>
+__global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, const uint8_t* __restrict__ seq,
+                                               const uint64_t* __restrict__ offs,
+                                               const uint64_t* __restrict__ win_offs, uint64_t n_windows,
+                                               uint32_t gw_base, uint64_t* __restrict__ pairs,
+                                               uint32_t* __restrict__ sketch, uint32_t* __restrict__ counts,
+                                               unsigned long long* real_pairs) {
+    const uint32_t lane = lane_id();
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t n_tasks = (n_windows + WINDOWS_PER_TASK - 1) / WINDOWS_PER_TASK;
+    unsigned long long real = 0;
+    for (uint64_t task = warp; task < n_tasks; task += n_warps) {
+        uint64_t w0 = task * WINDOWS_PER_TASK;
+        uint64_t w1 = min(w0 + WINDOWS_PER_TASK, n_windows);
+        // sequence of w0: last i with win_offs[i] <= w0
+        uint32_t lo = 0, hi = n_seq;  // invariant: win_offs[lo] <= w0 < win_offs[hi]
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (win_offs[mid] <= w0) lo = mid; else hi = mid;
+        }
+        uint32_t t = lo;
+        for (uint64_t lw = w0; lw < w1; ++lw) {
+            while (win_offs[t + 1] <= lw) ++t;
+            uint64_t j = lw - win_offs[t];
+            uint64_t L = offs[t + 1] - offs[t];
+            uint32_t f;
+            uint32_t cnt = warp_sketch<R>(seq + offs[t], L, j * p.stride, p, f);
+            if (EMIT) {
+                if (lane < p.s) {
+                    uint64_t v = lane < cnt ? (((uint64_t)hash_h2(f) << 32) | (uint32_t)(gw_base + lw)) : SENTINEL_PAIR;
+                    pairs[lw * p.s + lane] = v;
+                }
+                real += cnt;
+            } else {
+                if (lane < p.s) sketch[lw * p.s + lane] = lane < cnt ? f : 0u;
+                if (lane == 0) counts[lw] = cnt;
+            }
+        }
+    }
+    if (EMIT && lane == 0 && real) atomicAdd(real_pairs, real);
+}
+
+template <bool EMIT>
+cudaError_t launch_sketch(const SketchParams& p, uint32_t n_seq, const uint8_t* seq, const uint64_t* offs,
+                          const uint64_t* win_offs, uint64_t n_windows, uint32_t gw_base, uint64_t* pairs,
+                          uint32_t* sketch, uint32_t* counts, unsigned long long* real, cudaStream_t s) {
+    if (n_windows == 0) return cudaSuccess;
+    uint64_t tasks = (n_windows + WINDOWS_PER_TASK - 1) / WINDOWS_PER_TASK;
+    uint64_t blocks = (tasks + NWARP - 1) / NWARP;
+    uint32_t g = grid_for(blocks, 16);
+    int r = sketch_r_for(p.w);
+    if (r == 4)
+        k_sketch<4, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real);
+    else if (r == 8)
+        k_sketch<8, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real);
+    else
+        k_sketch<16, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts,
+                                            real);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t sketch_windows(const SketchParams& p, uint32_t n_seq, const uint8_t* seq, const uint64_t* offs,
+                           const uint64_t* win_offs, uint64_t n_windows, uint32_t* sketch, uint32_t* counts,
+                           cudaStream_t s) {
+    return launch_sketch<false>(p, n_seq, seq, offs, win_offs, n_windows, 0, nullptr, sketch, counts, nullptr, s);
+}
+
+cudaError_t emit_pairs(const SketchParams& p, uint32_t n_targets, const uint8_t* seq, const uint64_t* offs,
+                       const uint64_t* win_offs, uint64_t n_windows, uint32_t gw_base, uint64_t* pairs,
+                       unsigned long long* real_pairs, cudaStream_t s) {
+    return launch_sketch<true>(p, n_targets, seq, offs, win_offs, n_windows, gw_base, pairs, nullptr, nullptr,
+                               real_pairs, s);
+}
+
+// ------------------------------------------------------------ radix sort
+namespace {
+constexpr int RS_ITEMS = 16;
+constexpr uint64_t RS_TILE = (uint64_t)BT * RS_ITEMS;  // 4096 pairs
+// element of (warp w, round i, lane l) in a tile: w*32*RS_ITEMS + i*32 + l
+
+__global__ void __launch_bounds__(BT) k_radix_hist(const uint64_t* __restrict__ in, uint64_t n, uint32_t shift,
+                                                   int filter, uint64_t* __restrict__ hist, uint64_t n_tiles) {
+    __shared__ uint32_t sh[NWARP][256];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < NWARP * 256; i += BT) (&sh[0][0])[i] = 0;
+        __syncthreads();
+        uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
+#pragma unroll 4
+        for (int i = 0; i < RS_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * 32;
+            if (e < n) {
+                uint64_t v = in[e];
+                if (!(filter && v == SENTINEL_PAIR)) atomicAdd(&sh[w][(uint32_t)(v >> shift) & 255u], 1u);
+            }
+        }
+        __syncthreads();
+        uint32_t sum = 0;
+#pragma unroll
+        for (int i = 0; i < NWARP; ++i) sum += sh[i][threadIdx.x];
+        hist[(uint64_t)threadIdx.x * n_tiles + tile] = sum;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(BT) k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                      uint64_t n, uint32_t shift, int filter,
+                                                      const uint64_t* __restrict__ offs, uint64_t n_tiles) {
+    __shared__ uint32_t wc[NWARP][257];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        for (int i = threadIdx.x; i < NWARP * 257; i += BT) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        uint64_t v[RS_ITEMS];
+        uint32_t dr[RS_ITEMS];
+        uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * 32;
+            bool ok = e < n;
+            v[i] = ok ? in[e] : SENTINEL_PAIR;
+            uint32_t d = (!ok || (filter && v[i] == SENTINEL_PAIR)) ? 256u : ((uint32_t)(v[i] >> shift) & 255u);
+            uint32_t peers = __match_any_sync(FULL_MASK, d);
+            uint32_t rank = __popc(peers & lt);
+            uint32_t before = wc[w][d];
+            __syncwarp();
+            if (rank == 0) wc[w][d] = before + __popc(peers);
+            __syncwarp();
+            dr[i] = (d << 16) | (before + rank);
+        }
+        __syncthreads();
+        {
+            uint32_t run = 0;
+#pragma unroll
+            for (int i = 0; i < NWARP; ++i) {
+                uint32_t c = wc[i][threadIdx.x];
+                wc[i][threadIdx.x] = run;
+                run += c;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; ++i) {
+            uint32_t d = dr[i] >> 16;
+            if (d < 256u) {
+                uint64_t pos = offs[(uint64_t)d * n_tiles + tile] + wc[w][d] + (dr[i] & 0xFFFFu);
+                out[pos] = v[i];
+            }
+        }
+        __syncthreads();
+    }
+}
+}  // namespace
+
+cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_total, uint64_t n_real, cudaStream_t s) {
+    if (n_total == 0) return cudaSuccess;
+    uint64_t max_tiles = (n_total + RS_TILE - 1) / RS_TILE;
+    Tmp<uint64_t> hist(mem, 256 * max_tiles + 1, s);
+    if (!hist.ok()) return cudaErrorMemoryAllocation;
+    uint64_t* src = a;
+    uint64_t* dst = b;
+    for (int pass = 0; pass < 4; ++pass) {
+        uint64_t n = pass == 0 ? n_total : n_real;
+        if (n == 0) break;
+        uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+        uint32_t shift = 32 + 8 * pass;
+        int filter = pass == 0;
+        uint32_t g = grid_for(tiles);
+        k_radix_hist<<<g, BT, 0, s>>>(src, n, shift, filter, hist.ptr, tiles);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        e = scan_exclusive_sum(mem, hist.ptr, hist.ptr, 256 * tiles, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<g, BT, 0, s>>>(src, dst, n, shift, filter, hist.ptr, tiles);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        uint64_t* t = src;
+        src = dst;
+        dst = t;
+    }
+    // after 4 passes the data is back in `a`
+    return cudaSuccess;
+}
+
+// --------------------------------------------------------------- finalize
+namespace {
+constexpr int FIN_ITEMS = 8;
+constexpr uint64_t FIN_TILE = (uint64_t)BT * FIN_ITEMS;  // element = base + i*BT + t
+
+__device__ __forceinline__ uint32_t hk_of(uint64_t v) { return (uint32_t)(v >> 32); }
+
+__device__ __forceinline__ bool run_start(const uint64_t* __restrict__ a, uint64_t e, uint64_t v) {
+    return e == 0 || hk_of(a[e - 1]) != hk_of(v);
+}
+
+// Tile maximum of run-start indices.
+__global__ void __launch_bounds__(BT) k_fin_runmax(const uint64_t* __restrict__ a, uint64_t n,
+                                                   uint64_t* __restrict__ tmax, uint64_t n_tiles) {
+    __shared__ uint64_t sm[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * FIN_TILE, m = 0;
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            if (e < n && run_start(a, e, a[e])) m = max(m, e);
+        }
+        uint64_t tot = block_reduce(m, (uint64_t)0, OpMaxU(), sm);
+        if (threadIdx.x == 0) tmax[tile] = tot;
+    }
+}
+
+// Exclusive max-scan of tile maxima (single block; tiles fit comfortably).
+__global__ void __launch_bounds__(BT) k_exclusive_max_u64(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
+                                                          uint64_t n) {
+    __shared__ uint64_t sm[NWARP];
+    uint64_t carry = 0;
+    for (uint64_t base = 0; base < n; base += BT) {
+        uint64_t e = base + threadIdx.x;
+        uint64_t v = e < n ? in[e] : 0;
+        uint64_t tot;
+        uint64_t ex = block_exclusive(v, (uint64_t)0, OpMaxU(), sm, &tot);
+        if (e < n) out[e] = max(carry, ex);
+        carry = max(carry, tot);
+    }
+}
+
+__global__ void __launch_bounds__(BT) k_exclusive_max_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
+                                                          uint64_t n, int64_t* total) {
+    __shared__ int64_t sm[NWARP];
+    int64_t carry = INT64_MIN;
+    for (uint64_t base = 0; base < n; base += BT) {
+        uint64_t e = base + threadIdx.x;
+        int64_t v = e < n ? in[e] : INT64_MIN;
+        int64_t tot;
+        int64_t ex = block_exclusive(v, (int64_t)INT64_MIN, OpMaxI(), sm, &tot);
+        if (e < n) out[e] = max(carry, ex);
+        carry = max(carry, tot);
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// Per element: run start, kept (rank in run < cap).  MODE 0: tile sums of
+// kept and run starts.  MODE 1: emit outputs at the scanned positions.
+template <int MODE>
+__global__ void __launch_bounds__(BT) k_fin_pass(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
+                                                 const uint64_t* __restrict__ tpre_max, uint64_t n_tiles,
+                                                 uint64_t* __restrict__ tkept, uint64_t* __restrict__ tkeys,
+                                                 const uint32_t* __restrict__ wbase, uint32_t n_targets,
+                                                 uint64_t* __restrict__ locs, uint64_t* __restrict__ kept_pairs,
+                                                 uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
+                                                 uint64_t* __restrict__ kstart, unsigned long long* overflow) {
+    __shared__ uint64_t sm[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * FIN_TILE;
+        uint64_t rs_carry = tpre_max[tile];
+        uint64_t kept_carry = MODE == 1 ? tkept[tile] : 0;
+        uint64_t key_carry = MODE == 1 ? tkeys[tile] : 0;
+        uint64_t n_over = 0;
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            bool in_range = e < n;
+            uint64_t v = in_range ? a[e] : 0;
+            bool st = in_range && run_start(a, e, v);
+            uint64_t tot;
+            // inclusive max-scan of start indices = exclusive scan combined with own
+            uint64_t ex = block_exclusive(st ? e : (uint64_t)0, (uint64_t)0, OpMaxU(), sm, &tot);
+            uint64_t rstart = max(rs_carry, st ? e : ex);
+            rs_carry = max(rs_carry, tot);
+            bool kept = in_range && (e - rstart) < cap;
+            if (in_range && (e - rstart) == cap) ++n_over;
+            uint64_t kt, nt;
+            uint64_t kex = block_exclusive((uint64_t)kept, (uint64_t)0, OpSum(), sm, &kt);
+            uint64_t sex = block_exclusive((uint64_t)st, (uint64_t)0, OpSum(), sm, &nt);
+            if (MODE == 1) {
+                uint64_t kpos = kept_carry + kex;
+                if (kept) {
+                    uint32_t gw = (uint32_t)v;
+                    // target of the global window: last t with wbase[t] <= gw
+                    uint32_t lo = 0, hi = n_targets;
+                    while (hi - lo > 1) {
+                        uint32_t mid = (lo + hi) >> 1;
+                        if (wbase[mid] <= gw) lo = mid; else hi = mid;
+                    }
+                    locs[kpos] = ((uint64_t)lo << 32) | (gw - wbase[lo]);
+                    kept_pairs[kpos] = v;
+                }
+                if (st) {
+                    uint64_t kidx = key_carry + sex;
+                    khk[kidx] = hk_of(v);
+                    koff[kidx] = kpos;
+                    kstart[kidx] = e;
+                }
+            }
+            kept_carry += kt;
+            key_carry += nt;
+        }
+        if (MODE == 0) {
+            if (threadIdx.x == 0) {
+                tkept[tile] = kept_carry;
+                tkeys[tile] = key_carry;
+            }
+        } else {
+            uint64_t o = block_reduce(n_over, (uint64_t)0, OpSum(), sm);
+            if (threadIdx.x == 0 && o) atomicAdd(overflow, (unsigned long long)o);
+        }
+    }
+}
+
+__device__ __forceinline__ uint64_t home_slot(uint32_t hk, uint32_t log_t) {
+    return log_t >= 32 ? hk : (hk >> (32 - log_t));
+}
+
+// Tile maxima of home(k) - k.
+__global__ void __launch_bounds__(BT) k_tab_dispmax(const uint32_t* __restrict__ khk, uint64_t n, uint32_t log_t,
+                                                    int64_t* __restrict__ tmax, uint64_t n_tiles) {
+    __shared__ int64_t sm[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * FIN_TILE;
+        int64_t m = INT64_MIN;
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            if (e < n) m = max(m, (int64_t)home_slot(khk[e], log_t) - (int64_t)e);
+        }
+        int64_t tot = block_reduce(m, (int64_t)INT64_MIN, OpMaxI(), sm);
+        if (threadIdx.x == 0) tmax[tile] = tot;
+    }
+}
+
+// slot(k) = k + max(prefix, inclusive max of home - k); writes the entry.
+__global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ khk, const uint64_t* __restrict__ koff,
+                                                 const uint64_t* __restrict__ kstart, uint64_t n, uint32_t cap,
+                                                 uint32_t log_t, const int64_t* __restrict__ tpre, uint64_t n_tiles,
+                                                 uint4* __restrict__ table, unsigned int* max_disp) {
+    __shared__ int64_t sm[NWARP];
+    __shared__ uint64_t smu[NWARP];
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        uint64_t base = tile * FIN_TILE;
+        int64_t carry = tpre[tile];
+        uint64_t dmax = 0;
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
+            bool in_range = e < n;
+            uint32_t hk = in_range ? khk[e] : 0;
+            uint64_t home = home_slot(hk, log_t);
+            int64_t a = in_range ? (int64_t)home - (int64_t)e : INT64_MIN;
+            int64_t tot;
+            int64_t ex = block_exclusive(a, (int64_t)INT64_MIN, OpMaxI(), sm, &tot);
+            int64_t inc = max(carry, max(ex, a));
+            carry = max(carry, tot);
+            if (in_range) {
+                uint64_t slot = (uint64_t)((int64_t)e + inc);
+                uint64_t len = kstart[e + 1] - kstart[e];
+                uint32_t cnt = (uint32_t)(len < cap ? len : cap);
+                uint64_t off = koff[e];
+                table[slot] = make_uint4(hk, cnt, (uint32_t)off, (uint32_t)(off >> 32));
+                dmax = max(dmax, slot - home);
+            }
+        }
+        uint64_t dm = block_reduce(dmax, (uint64_t)0, OpMaxU(), smu);
+        if (threadIdx.x == 0) atomicMax(max_disp, (unsigned int)min(dm, (uint64_t)0xFFFFFFFFu));
+    }
+}
+}  // namespace
+
+cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
+                           uint32_t n_targets, FinalizeOut* out, cudaStream_t s) {
+    cudaError_t e;
+    *out = FinalizeOut();
+    uint64_t tiles = (n + FIN_TILE - 1) / FIN_TILE;
+    uint32_t g = grid_for(tiles ? tiles : 1);
+    // counters: [0] overflow keys, [1] max displacement (u32 in low word)
+    Tmp<unsigned long long> ctr(mem, 4, s);
+    if (!ctr.ok()) return cudaErrorMemoryAllocation;
+    if ((e = cudaMemsetAsync(ctr.ptr, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    uint64_t host_tot[2] = {0, 0};
+    Tmp<uint64_t> tmax(mem, tiles + 1, s), tpre(mem, tiles + 1, s), tkept(mem, tiles + 1, s),
+        tkeys(mem, tiles + 1, s);
+    if (!tmax.ok() || !tpre.ok() || !tkept.ok() || !tkeys.ok()) return cudaErrorMemoryAllocation;
+    if (n > 0) {
+        k_fin_runmax<<<g, BT, 0, s>>>(sorted, n, tmax.ptr, tiles);
+        k_exclusive_max_u64<<<1, BT, 0, s>>>(tmax.ptr, tpre.ptr, tiles);
+        k_fin_pass<0><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, nullptr, 0, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, nullptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = scan_exclusive_sum(mem, tkept.ptr, tkept.ptr, tiles, s)) != cudaSuccess) return e;
+        if ((e = scan_exclusive_sum(mem, tkeys.ptr, tkeys.ptr, tiles, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&host_tot[0], tkept.ptr + tiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&host_tot[1], tkeys.ptr + tiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
+    const uint64_t n_kept = host_tot[0], n_keys = host_tot[1];
+    Tmp<uint64_t> locs(mem, n_kept, s), kpairs(mem, n_kept, s), koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
+    Tmp<uint32_t> khk(mem, n_keys, s);
+    if (!locs.ok() || !kpairs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
+    if (n > 0) {
+        k_fin_pass<1><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, wbase, n_targets,
+                                       locs.ptr, kpairs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    }
+    // feature table: T = power of two >= 2 * n_keys (load factor <= 1/2)
+    uint32_t log_t = 1;
+    while ((1ull << log_t) < 2 * n_keys) ++log_t;
+    uint64_t T = 1ull << log_t;
+    uint64_t ktiles = (n_keys + FIN_TILE - 1) / FIN_TILE;
+    int64_t host_maxa = INT64_MIN;
+    Tmp<int64_t> kt_max(mem, ktiles + 1, s), kt_pre(mem, ktiles + 1, s);
+    if (!kt_max.ok() || !kt_pre.ok()) return cudaErrorMemoryAllocation;
+    if (n_keys > 0) {
+        k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles);
+        k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(&host_maxa, kt_pre.ptr + ktiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    }
+    uint64_t last_slot = n_keys ? (uint64_t)((int64_t)(n_keys - 1) + host_maxa) : 0;
+    uint64_t table_len = (last_slot + 1 > T ? last_slot + 1 : T) + 2;
+    Tmp<uint4> table(mem, table_len, s);
+    if (!table.ok()) return cudaErrorMemoryAllocation;
+    if ((e = cudaMemsetAsync(table.ptr, 0, table_len * sizeof(uint4), s)) != cudaSuccess) return e;
+    if (n_keys > 0) {
+        k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t, kt_pre.ptr,
+                                                   ktiles, table.ptr, (unsigned int*)(ctr.ptr + 1));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    unsigned long long host_ctr[2] = {0, 0};
+    if ((e = cudaMemcpyAsync(host_ctr, ctr.ptr, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    out->n_keys = n_keys;
+    out->n_kept = n_kept;
+    out->overflow_keys = host_ctr[0];
+    out->max_probe = (uint32_t)(host_ctr[1] & 0xFFFFFFFFull);
+    out->log_t = log_t;
+    out->table_len = table_len;
+    out->table_bytes = table_len * sizeof(uint4);
+    out->locs = locs.release();
+    out->kept_pairs = kpairs.release();
+    out->table = table.release();
+    return cudaSuccess;
+}
+
+// -------------------------------------------------------------- taxonomy
+namespace {
+__global__ void k_tax_depth(const uint32_t* __restrict__ parent, uint32_t n, uint32_t* __restrict__ depth,
+                            uint32_t* max_depth, uint32_t* cycle) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        uint32_t d = 0, y = x;
+        while (parent[y] != y) {
+            y = parent[y];
+            if (++d > n) {
+                atomicMax(cycle, 1u);
+                d = 0;
+                break;
+            }
+        }
+        depth[x] = d;
+        atomicMax(max_depth, d);
+    }
+}
+
+__global__ void k_tax_lineage(const uint32_t* __restrict__ parent, uint32_t n, const uint32_t* __restrict__ depth,
+                              uint32_t* __restrict__ lin, uint32_t stride) {
+    for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+        uint32_t y = x;
+        for (int64_t d = depth[x]; d >= 0; --d) {
+            lin[(uint64_t)x * stride + d] = y;
+            y = parent[y];
+        }
+    }
+}
+}  // namespace
+
+cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* depth, uint32_t* max_depth,
+                            uint32_t* cycle_flag, cudaStream_t s) {
+    k_tax_depth<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, max_depth, cycle_flag);
+    return cudaGetLastError();
+}
+
+cudaError_t taxonomy_lineage(const uint32_t* parent, uint32_t n_taxa, const uint32_t* depth, uint32_t* lin,
+                             uint32_t stride, cudaStream_t s) {
+    k_tax_lineage<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, lin, stride);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ dump
+namespace {
+__global__ void k_dump_select(const uint4* __restrict__ table, uint64_t len, uint64_t lo, uint64_t hi,
+                              uint32_t* keys, uint64_t* offs, uint32_t* counts, uint64_t cap,
+                              unsigned long long* n_sel) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < len; i += (uint64_t)gridDim.x * blockDim.x) {
+        uint4 e = table[i];
+        if (e.y == 0) continue;
+        uint64_t key = hash_h2_inverse(e.x);
+        if (key < lo || key >= hi) continue;
+        unsigned long long idx = atomicAdd(n_sel, 1ull);
+        if (idx < cap) {
+            keys[idx] = (uint32_t)key;
+            offs[idx] = (uint64_t)e.z | ((uint64_t)e.w << 32);
+            counts[idx] = e.y;
+        }
+    }
+}
+
+__global__ void k_dump_gather(const uint64_t* __restrict__ locs, const uint64_t* __restrict__ src_off,
+                              const uint32_t* __restrict__ counts, const uint64_t* __restrict__ dst_off, uint64_t n,
+                              uint64_t* __restrict__ out) {
+    for (uint64_t i = blockIdx.x; i < n; i += gridDim.x)
+        for (uint32_t j = threadIdx.x; j < counts[i]; j += blockDim.x) out[dst_off[i] + j] = locs[src_off[i] + j];
+}
+}  // namespace
+
+cudaError_t dump_select(const uint4* table, uint64_t table_len, uint64_t lo, uint64_t hi, uint32_t* keys,
+                        uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel, cudaStream_t s) {
+    if (table_len == 0) return cudaSuccess;
+    k_dump_select<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, lo, hi, keys, offs, counts,
+                                                                      cap, n_sel);
+    return cudaGetLastError();
+}
+
+cudaError_t dump_gather(const uint64_t* locs, const uint64_t* src_off, const uint32_t* counts, const uint64_t* dst_off,
+                        uint64_t n, uint64_t* out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_dump_gather<<<grid_for(n, 32), 128, 0, s>>>(locs, src_off, counts, dst_off, n, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mc

@@ -1,0 +1,111 @@
+// Shared device helpers of the sm_103a MetaCache-GPU kernels: base encoding,
+// k-mer hashing (h1) and table-slot hashing (h2), warp helpers and the
+// internal launch interface between the translation units.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mc {
+
+constexpr uint32_t FULL_MASK = 0xFFFFFFFFu;
+constexpr uint32_t NO_TAXON = 0xFFFFFFFFu;
+constexpr uint64_t SENTINEL_PAIR = ~0ull;  // marks an unused (feature, window) slot
+constexpr uint64_t EMPTY_LOC = ~0ull;      // empty histogram slot (target 2^32-1 is never assigned)
+constexpr int MAX_M = 8;
+constexpr int MAX_S = 32;
+constexpr int NUM_SMS_HINT = 152;
+
+// Device status word values (ordered: a larger code wins with atomicMax).
+constexpr uint32_t DEV_OK = 0;
+constexpr uint32_t DEV_ERR_CAPACITY = 7;
+constexpr uint32_t DEV_ERR_ARG = 1;
+
+struct SketchParams {
+    uint32_t k;       // k-mer length
+    uint32_t s;       // sketch size
+    uint32_t w;       // window length
+    uint32_t stride;  // window stride
+};
+
+// ---------------------------------------------------------------- hashing
+// h1: the lowbias32 mixer (C. Wellons, hash-prospector), a bijection on
+// 32-bit words, applied to the canonical k-mer code (Section 3.1).
+__host__ __device__ __forceinline__ uint32_t hash_h1(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x7feb352dU;
+    x ^= x >> 15;
+    x *= 0x846ca68bU;
+    x ^= x >> 16;
+    return x;
+}
+
+// h2: MurmurHash3's 32-bit finalizer, a second bijection used only to place
+// features in the table (Section 3.1: "to counteract the biased distribution
+// of sketch values a second hash function h2 is applied").  Layout only: it
+// does not change any result.
+__host__ __device__ __forceinline__ uint32_t hash_h2(uint32_t x) {
+    x ^= x >> 16;
+    x *= 0x85ebca6bU;
+    x ^= x >> 13;
+    x *= 0xc2b2ae35U;
+    x ^= x >> 16;
+    return x;
+}
+
+__host__ __device__ constexpr uint32_t mul_inverse(uint32_t a) {
+    // Newton iteration for the inverse of an odd number modulo 2^32
+    uint32_t x = a;
+    for (int i = 0; i < 5; ++i) x *= 2u - a * x;
+    return x;
+}
+
+__host__ __device__ __forceinline__ uint32_t unxorshift(uint32_t y, int s) {
+    uint32_t x = y;
+    for (int i = 0; i < 32 / s + 1; ++i) x = y ^ (x >> s);
+    return x;
+}
+
+// Inverse of h2 (to report features in dumps).
+__host__ __device__ __forceinline__ uint32_t hash_h2_inverse(uint32_t y) {
+    y = unxorshift(y, 16);
+    y *= mul_inverse(0xc2b2ae35U);
+    y = unxorshift(y, 13);
+    y *= mul_inverse(0x85ebca6bU);
+    y = unxorshift(y, 16);
+    return y;
+}
+
+// ------------------------------------------------------------- encoding
+// 2-bit code of an ASCII base: A/a -> 0, C/c -> 1, G/g -> 2, T/t -> 3 (bits
+// 1 and 2 of the ASCII code decide it).  Only meaningful when valid.
+__device__ __forceinline__ uint32_t base_code(uint32_t c) { return ((c >> 1) ^ (c >> 2)) & 3u; }
+
+// A, C, G, T in either case; every other byte is an invalid base.
+__device__ __forceinline__ uint32_t base_valid(uint32_t c) {
+    uint32_t u = (c | 0x20u) - 0x61u;  // 'a' -> 0 ... 't' -> 19
+    return (u < 20u) ? ((0x80045u >> u) & 1u) : 0u;
+}
+
+// Reverse complement of a k-mer code held in the low 2k bits (first base
+// most significant): reverse the 2-bit digits, complement each.
+__device__ __forceinline__ uint32_t revcomp_code(uint32_t fwd, uint32_t k) {
+    uint32_t r = __brev(fwd);
+    r = ((r >> 1) & 0x55555555u) | ((r & 0x55555555u) << 1);  // restore bit order inside digits
+    r = ~r;
+    return r >> (32 - 2 * k);
+}
+
+__host__ __device__ __forceinline__ uint64_t num_windows(uint64_t L, uint32_t k, uint32_t stride) {
+    return L < k ? 0 : (L - k + stride) / stride;
+}
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+}  // namespace mc

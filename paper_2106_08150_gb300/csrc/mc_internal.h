@@ -1,0 +1,133 @@
+// Internal interface between the translation units of libmc (host side).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/mc.h"
+#include "mc_common.cuh"
+
+namespace mc {
+
+// Device memory through the database's allocator (stream-ordered).
+struct Mem {
+    mc_allocator a;
+    void* alloc(size_t bytes, cudaStream_t s) const;
+    void free(void* p, size_t bytes, cudaStream_t s) const;
+};
+
+// A scoped temporary device buffer, freed in stream order.
+template <class T>
+struct Tmp {
+    const Mem* mem = nullptr;
+    cudaStream_t stream = nullptr;
+    T* ptr = nullptr;
+    size_t bytes = 0;
+    Tmp() = default;
+    Tmp(const Mem& m, size_t n, cudaStream_t s) : mem(&m), stream(s), bytes(n * sizeof(T)) {
+        ptr = bytes ? static_cast<T*>(m.alloc(bytes, s)) : nullptr;
+    }
+    Tmp(const Tmp&) = delete;
+    Tmp& operator=(const Tmp&) = delete;
+    ~Tmp() {
+        if (ptr) mem->free(ptr, bytes, stream);
+    }
+    bool ok() const { return bytes == 0 || ptr != nullptr; }
+    T* release() {
+        T* p = ptr;
+        ptr = nullptr;
+        return p;
+    }
+};
+
+// ------------------------------------------------------------ mc_build.cu
+// Exclusive prefix sum of n u64 values into out[0..n); out[n] = total.
+// in may alias out.
+cudaError_t scan_exclusive_sum(const Mem& mem, const uint64_t* in, uint64_t* out, uint64_t n, cudaStream_t s);
+
+// win_offs[i] = exclusive prefix of windows per sequence, win_offs[n] =
+// total.  Sets *bad_offs (device) if offs decreases.
+cudaError_t window_offsets(const Mem& mem, const SketchParams& p, uint32_t n_seq, const uint64_t* offs,
+                           uint64_t* win_offs, uint32_t* bad_offs, cudaStream_t s);
+
+// Debug sketch export (mc_sketch).
+cudaError_t sketch_windows(const SketchParams& p, uint32_t n_seq, const uint8_t* seq, const uint64_t* offs,
+                           const uint64_t* win_offs, uint64_t n_windows, uint32_t* sketch, uint32_t* counts,
+                           cudaStream_t s);
+
+// Build: sketch every window of the call's targets and write its (h2(f) <<
+// 32 | global window) pairs to pairs[lw * s + i] (sentinel past the
+// sketch).  *real_pairs (device) += pairs written.
+cudaError_t emit_pairs(const SketchParams& p, uint32_t n_targets, const uint8_t* seq, const uint64_t* offs,
+                       const uint64_t* win_offs, uint64_t n_windows, uint32_t gw_base, uint64_t* pairs,
+                       unsigned long long* real_pairs, cudaStream_t s);
+
+// Stable LSD radix sort of pairs by their upper 32 bits (4 passes of 8
+// bits).  The first pass drops sentinel pairs.  in holds n_total entries
+// on entry, the n_real sorted real pairs on return; tmp has n_total room.
+cudaError_t sort_pairs(const Mem& mem, uint64_t* in, uint64_t* tmp, uint64_t n_total, uint64_t n_real,
+                       cudaStream_t s);
+
+struct FinalizeOut {
+    uint64_t n_keys = 0;
+    uint64_t n_kept = 0;
+    uint64_t overflow_keys = 0;
+    uint64_t* locs = nullptr;      // n_kept, (target << 32) | window
+    uint64_t* kept_pairs = nullptr; // n_kept, (h2 << 32) | global window
+    uint4* table = nullptr;         // table_len entries {h2, count, offset lo, offset hi}
+    uint64_t table_len = 0;
+    uint64_t table_bytes = 0;
+    uint32_t log_t = 0;
+    uint32_t max_probe = 0;
+};
+
+// Condensed layout from sorted pairs: keep the first `cap` pairs of each
+// feature, convert global windows to (target, window), build the ordered
+// linear-probing feature table.  wbase: n_targets+1 global window bases.
+cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
+                           uint32_t n_targets, FinalizeOut* out, cudaStream_t s);
+
+// Taxonomy: depth per node and lineage rows lin[x * stride + d].
+cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* depth, uint32_t* max_depth,
+                            uint32_t* cycle_flag, cudaStream_t s);
+cudaError_t taxonomy_lineage(const uint32_t* parent, uint32_t n_taxa, const uint32_t* depth, uint32_t* lin,
+                             uint32_t stride, cudaStream_t s);
+
+// Dump support: entries of the table whose feature is in [lo, hi).
+cudaError_t dump_select(const uint4* table, uint64_t table_len, uint64_t lo, uint64_t hi, uint32_t* keys,
+                        uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel, cudaStream_t s);
+cudaError_t dump_gather(const uint64_t* locs, const uint64_t* src_off, const uint32_t* counts, const uint64_t* dst_off,
+                        uint64_t n, uint64_t* out, cudaStream_t s);
+
+// --------------------------------------------------------- mc_classify.cu
+struct ClassifyDb {
+    const uint4* table;
+    uint32_t log_t;
+    uint32_t max_probe;
+    const uint64_t* locs;
+    const uint32_t* taxon_of_target;
+    uint32_t n_targets;
+    const uint32_t* lineage;
+    const uint32_t* depth;
+    uint32_t lin_stride;
+    uint32_t n_taxa;
+    SketchParams sp;
+};
+
+struct ClassifyQuery {
+    const uint8_t* seq;
+    const uint64_t* offs;
+    const uint32_t* qoffs;
+    uint32_t n_q;
+    uint32_t m, hits_min, band, max_insert;
+    uint32_t* label;
+    uint32_t* hits;
+    uint32_t* top_target;
+    uint32_t* cands;
+    unsigned long long* counters;
+    uint32_t* status;
+};
+
+cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& q, cudaStream_t s);
+
+}  // namespace mc

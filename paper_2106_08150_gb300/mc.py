@@ -1,0 +1,283 @@
+"""Thin Python binding of libmc (include/mc.h): the same entry points, with
+arguments marshalled from PyTorch tensors.  Every step of the method runs in
+the library's CUDA kernels; PyTorch only provides device memory and streams.
+
+Importing this module fails loudly when libmc.so has not been built: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmc.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "mc.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+MC_OK, MC_ERR_ARG, MC_ERR_STATE, MC_ERR_OOM, MC_ERR_TABLE_FULL, MC_ERR_TIMEOUT, MC_ERR_CUDA, MC_ERR_CAPACITY = range(8)
+MC_NO_TAXON = 0xFFFFFFFF
+MC_NO_TARGET = 0xFFFFFFFF
+MC_MAX_CANDIDATES = 8
+
+
+class McError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_lib.mc_status_string(code).decode()}: {msg}")
+        self.code = code
+
+
+class mc_db_params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("sketch_size", ctypes.c_uint32), ("window_len", ctypes.c_uint32),
+                ("window_stride", ctypes.c_uint32), ("bucket_cap", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("max_locations", ctypes.c_uint64), ("hbm_budget", ctypes.c_uint64)]
+
+
+class mc_classify_params(ctypes.Structure):
+    _fields_ = [("max_candidates", ctypes.c_uint32), ("hits_min", ctypes.c_uint32),
+                ("lca_band_pct", ctypes.c_uint32), ("max_insert", ctypes.c_uint32)]
+
+
+class mc_db_stats_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ["n_targets", "n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys", "dropped_locations",
+                 "table_slots", "max_probe", "device_bytes"]] + \
+               [("load_factor", ctypes.c_double), ("finalized", ctypes.c_uint32), ("max_depth", ctypes.c_uint32)]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+
+
+class mc_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+_vp, _u32, _u64, _i = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+_SIGS = {
+    "mc_version": ([], _i),
+    "mc_last_error_string": ([], ctypes.c_char_p),
+    "mc_status_string": ([_i], ctypes.c_char_p),
+    "mc_set_allocator": ([ctypes.POINTER(mc_allocator)], _i),
+    "mc_db_create": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, ctypes.POINTER(_vp)], _i),
+    "mc_db_add_targets": ([_vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_u32)], _i),
+    "mc_db_finalize": ([_vp], _i),
+    "mc_classify": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp], _i),
+    "mc_classify_debug": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp,
+                           _vp, _vp], _i),
+    "mc_classify_status": ([_vp, _vp], _i),
+    "mc_db_free": ([_vp], None),
+    "mc_db_stats": ([_vp, ctypes.POINTER(mc_db_stats_t)], _i),
+    "mc_db_dump": ([_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i),
+    "mc_window_offsets": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp], _i),
+    "mc_sketch": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp, _u64, _vp, _vp, _vp], _i),
+}
+for _name, (_args, _res) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes, _f.restype = _args, _res
+
+
+def declared_symbols() -> list[str]:
+    """Function names declared in include/mc.h."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(mc_\w+)\s*\(", text, re.M)))
+
+
+def _check(code: int):
+    if code != MC_OK:
+        raise McError(code, _lib.mc_last_error_string().decode())
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def db_params(k=16, sketch_size=16, window_len=128, window_stride=113, bucket_cap=254, max_locations=0,
+              hbm_budget=0) -> mc_db_params:
+    return mc_db_params(k, sketch_size, window_len, window_stride, bucket_cap, 0, max_locations, hbm_budget)
+
+
+def classify_params(max_candidates=4, hits_min=4, lca_band_pct=10, max_insert=0) -> mc_classify_params:
+    return mc_classify_params(max_candidates, hits_min, lca_band_pct, max_insert)
+
+
+# ------------------------------------------------------------ allocator
+_torch_alloc_refs = None
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route every device allocation of the library through PyTorch's
+    caching allocator (mc_set_allocator)."""
+    global _torch_alloc_refs
+    if not enable:
+        _check(_lib.mc_set_allocator(None))
+        _torch_alloc_refs = None
+        return
+    import torch
+
+    def _alloc(ctx, size, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), torch.cuda.current_device(), stream or 0)
+        except Exception:
+            return None
+
+    def _free(ctx, ptr, size, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a = mc_allocator(ALLOC_FN(_alloc), FREE_FN(_free), None)
+    _torch_alloc_refs = a  # keep the callbacks alive
+    _check(_lib.mc_set_allocator(ctypes.byref(a)))
+
+
+# ------------------------------------------------------------- C-ABI calls
+def mc_version() -> int:
+    return _lib.mc_version()
+
+
+def mc_db_create(params: mc_db_params, n_taxa: int, parent: np.ndarray, stream=None) -> int:
+    parent = np.ascontiguousarray(parent, dtype=np.uint32)
+    h = _vp()
+    _check(_lib.mc_db_create(ctypes.byref(params), n_taxa, parent.ctypes.data, _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
+def mc_db_add_targets(db: int, n_targets: int, seq, offs, taxon: np.ndarray) -> int:
+    taxon = np.ascontiguousarray(taxon, dtype=np.uint32)
+    first = _u32()
+    _check(_lib.mc_db_add_targets(db, n_targets, _ptr(seq), _ptr(offs), taxon.ctypes.data, ctypes.byref(first)))
+    return first.value
+
+
+def mc_db_finalize(db: int):
+    _check(_lib.mc_db_finalize(db))
+
+
+def mc_classify(db: int, params: mc_classify_params, n_seq: int, seq, offs, n_queries: int, qoffs, label, hits,
+                top_target=None, stream=None):
+    _check(_lib.mc_classify(db, ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), n_queries, _ptr(qoffs),
+                            _ptr(label), _ptr(hits), _ptr(top_target), _stream(stream)))
+
+
+def mc_classify_debug(db: int, params: mc_classify_params, n_seq: int, seq, offs, n_queries: int, qoffs, label,
+                      hits, top_target=None, cands=None, counters=None, stream=None):
+    _check(_lib.mc_classify_debug(db, ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), n_queries, _ptr(qoffs),
+                                  _ptr(label), _ptr(hits), _ptr(top_target), _ptr(cands), _ptr(counters),
+                                  _stream(stream)))
+
+
+def mc_classify_status(db: int, stream=None):
+    _check(_lib.mc_classify_status(db, _stream(stream)))
+
+
+def mc_db_free(db: int):
+    _lib.mc_db_free(db)
+
+
+def mc_db_stats(db: int) -> dict:
+    st = mc_db_stats_t()
+    _check(_lib.mc_db_stats(db, ctypes.byref(st)))
+    return {n: getattr(st, n) for n, _ in mc_db_stats_t._fields_}
+
+
+def mc_db_dump(db: int, key_lo: int = 0, key_hi: int = 1 << 32):
+    """(keys, counts, locs) of features in [key_lo, key_hi), ascending."""
+    nk, nl = _u64(), _u64()
+    code = _lib.mc_db_dump(db, key_lo, key_hi, 0, 0, None, None, None, ctypes.byref(nk), ctypes.byref(nl))
+    if code not in (MC_OK, MC_ERR_CAPACITY):
+        _check(code)
+    if code == MC_ERR_CAPACITY and nk.value > 0:
+        # sizes of locations are reported once the features fit
+        code = _lib.mc_db_dump(db, key_lo, key_hi, nk.value, 0, None, None, None, ctypes.byref(nk),
+                               ctypes.byref(nl))
+        if code not in (MC_OK, MC_ERR_CAPACITY):
+            _check(code)
+    keys = np.zeros(max(1, nk.value), dtype=np.uint32)
+    counts = np.zeros(max(1, nk.value), dtype=np.uint32)
+    locs = np.zeros(max(1, nl.value), dtype=np.uint64)
+    _check(_lib.mc_db_dump(db, key_lo, key_hi, nk.value, nl.value, keys.ctypes.data, counts.ctypes.data,
+                           locs.ctypes.data, ctypes.byref(nk), ctypes.byref(nl)))
+    return keys[:nk.value], counts[:nk.value], locs[:nl.value]
+
+
+def mc_window_offsets(params: mc_db_params, n_seq: int, offs, win_offs, stream=None):
+    _check(_lib.mc_window_offsets(ctypes.byref(params), n_seq, _ptr(offs), _ptr(win_offs), _stream(stream)))
+
+
+def mc_sketch(params: mc_db_params, n_seq: int, seq, offs, win_offs, n_windows: int, sketch, counts, stream=None):
+    _check(_lib.mc_sketch(ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), _ptr(win_offs), n_windows,
+                          _ptr(sketch), _ptr(counts), _stream(stream)))
+
+
+# ------------------------------------------------------- convenience layer
+@dataclass
+class Database:
+    """Owning handle: create, add targets, finalize, classify, free."""
+    handle: int
+    params: mc_db_params
+
+    @classmethod
+    def create(cls, parent, stream=None, **params) -> "Database":
+        p = db_params(**params)
+        return cls(mc_db_create(p, len(parent), parent, stream), p)
+
+    def add_targets(self, seq, offs, taxon) -> int:
+        return mc_db_add_targets(self.handle, len(taxon), seq, offs, taxon)
+
+    def finalize(self):
+        mc_db_finalize(self.handle)
+
+    def stats(self) -> dict:
+        return mc_db_stats(self.handle)
+
+    def dump(self, lo=0, hi=1 << 32):
+        return mc_db_dump(self.handle, lo, hi)
+
+    def classify(self, seq, offs, qoffs, *, label=None, hits=None, top_target=None, cands=None, counters=None,
+                 stream=None, **cparams):
+        """Device tensors in, device tensors out: (label, hits, top_target[, cands])."""
+        import torch
+        nq = qoffs.numel() - 1
+        dev = seq.device
+        label = torch.empty(nq, dtype=torch.int32, device=dev) if label is None else label
+        hits = torch.empty(nq, dtype=torch.int32, device=dev) if hits is None else hits
+        top_target = torch.empty(nq, dtype=torch.int32, device=dev) if top_target is None else top_target
+        cp = classify_params(**cparams)
+        mc_classify_debug(self.handle, cp, offs.numel() - 1, seq, offs, nq, qoffs, label, hits, top_target, cands,
+                          counters, stream)
+        return label, hits, top_target
+
+    def free(self):
+        if self.handle:
+            mc_db_free(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
