@@ -1,0 +1,465 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 MetaCache-GPU hot path.
+
+One step = the whole hot path over one batch of synthetic input: build the
+database from the reference genomes (sketch, sort, cap, condensed layout)
+and classify every read pair against it (the paper's on-the-fly mode,
+Section 5.4).  The default workload is the mid-size configuration: 1,000
+genomes (~3.4 Gbp) in 100 genera, 10M paired-end 2x150 bp reads.
+
+Prints one JSON line.  `value` is read pairs classified per second over the
+whole step (build included); `build_gbps` and `classify_mreads_s` split it.
+`--impl reference` times the CPU oracle (the reference arm of this build) on
+a bounded sample of the same workload, in the same unit.
+
+Multi-GPU: the path shards by reads with a replicated database (no data-path
+collective), so N ranks run independent replicas (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "build Gbp/s; classify Mreads/s; served p50/p99 latency, oracle-exact labels"
+UNIT = "Mreads/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["mid", "small", "tiny"], default="mid",
+                    help="mid = 1,000 genomes / 10M pairs (the measured configuration); small/tiny for profiling")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-genera", type=int, default=2)
+    ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------- workload
+def make_workload(name: str, rank: int):
+    import synth
+    if name == "mid":
+        w = synth.config1(seed=1001)
+    elif name == "small":
+        w = synth.config1(seed=1001, n_families=1, genera_per_family=10, n_pairs=1_000_000)
+    else:
+        w = synth.config1(seed=1001, n_families=1, genera_per_family=2, len_scale=0.1, n_pairs=50_000)
+    if rank:
+        # replicas classify their own reads against the same database
+        reads, roffs, qoffs, truth = synth.simulate_reads(
+            1001 + 7919 * rank, w.n_queries, w.genomes, w.goffs, paired=True, len_lo=150, len_hi=150, sub=0.005,
+            indel=0.0005, frag_b=300.0, frag_sd_abs=30.0)
+        w.reads, w.roffs, w.qoffs, w.truth = reads, roffs, qoffs, truth
+    return w
+
+
+def workload_config(w, args, n_gpus):
+    return {
+        "workload": w.name,
+        "genomes": w.n_targets,
+        "genome_bp": w.n_bp,
+        "read_pairs": w.n_queries,
+        "mate_len": 150,
+        "k": w.db_params["k"], "sketch_size": w.db_params["sketch_size"], "window_len": w.db_params["window_len"],
+        "window_stride": w.db_params["window_stride"], "bucket_cap": w.db_params["bucket_cap"],
+        "max_candidates": w.cls_params["max_candidates"], "hits_min": w.cls_params["hits_min"],
+        "lca_band_pct": w.cls_params["lca_band_pct"], "max_insert": w.cls_params["max_insert"],
+        "step": "build database from all genomes + classify all read pairs (on-the-fly)",
+        "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single",
+        "l2": "inputs larger than L2 (genomes 3.4 GB, reads 3 GB)" if args.workload == "mid" else "small workload",
+        "recipe": w.recipe,
+    }
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi clocks/throttle samples while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------ roofline models
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_2106_08150_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
+    """Algorithmic HBM bytes of ALL launches of `kernel` in one step (see
+    the design doc, roofline section, for the per-unit figures)."""
+    n_win = st["n_windows"]
+    s = w.db_params["sketch_size"]
+    slots = n_win * s  # emitted pair slots (sentinels included)
+    n_real = st["n_pairs"]
+    if kernel == "sketch_emit":
+        return w.n_bp * 1.0 + slots * 8.0  # read each base once, write the pair slots
+    if kernel == "radix_scatter":
+        return (slots + 3 * n_real) * 8.0 + 4 * n_real * 8.0  # read every input once, write every real pair
+    if kernel == "radix_hist":
+        return (slots + 3 * n_real) * 8.0
+    if kernel in ("fin_count", "fin_runmax"):
+        return n_real * 8.0
+    if kernel == "fin_emit":
+        return n_real * 8.0 + st["n_locations"] * 16.0 + st["n_keys"] * 20.0
+    if kernel == "tab_emit":
+        return st["n_keys"] * 20.0 + st["n_keys"] * 16.0
+    if kernel == "classify_smem" and ctr is not None:
+        # bases + mate offsets + query offsets, one 32 B table sector per
+        # feature looked up, the 32 B sectors of every gathered bucket,
+        # 12 B of outputs per query
+        n_reads_bytes = int(w.roffs[-1]) + 8 * (w.n_seq + 1) + 4 * (w.n_queries + 1)
+        return n_reads_bytes + 32.0 * float(ctr[0]) + 32.0 * float(ctr[5]) + 12.0 * w.n_queries
+    return None
+
+
+def load_traffic():
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return {}
+    try:
+        return json.load(open(p))
+    except ValueError:
+        return {}
+
+
+# ----------------------------------------------------------- GPU arm
+def run_gpu(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+    from paper_2106_08150_gb300 import mc
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    mc.use_torch_allocator()
+    t_gen = time.time()
+    w = make_workload(args.workload, rank)
+    t_gen = time.time() - t_gen
+    stream = torch.cuda.Stream(device=dev)
+
+    def to_dev(a):
+        a = np.ascontiguousarray(a)
+        if a.dtype == np.uint64:
+            a = a.view(np.int64)
+        elif a.dtype == np.uint32:
+            a = a.view(np.int32)
+        return torch.from_numpy(a).to(dev)
+
+    g, go = to_dev(w.genomes), to_dev(w.goffs)
+    r, ro, qo = to_dev(w.reads), to_dev(w.roffs), to_dev(w.qoffs)
+    nq = w.n_queries
+    label = torch.empty(nq, dtype=torch.int32, device=dev)
+    hits = torch.empty(nq, dtype=torch.int32, device=dev)
+    top = torch.empty(nq, dtype=torch.int32, device=dev)
+    cp = mc.classify_params(**w.cls_params)
+    torch.cuda.synchronize()
+
+    def step(seq_g, off_g, seq_r, off_r, off_q, evs=None):
+        db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+        db.add_targets(seq_g, off_g, w.taxon_of_target)
+        db.finalize()
+        if evs is not None:
+            evs.append(torch.cuda.Event(enable_timing=True))
+            evs[-1].record(stream)
+        mc.mc_classify(db.handle, cp, w.n_seq, seq_r, off_r, nq, off_q, label, hits, top, stream=stream)
+        db.free()  # synchronises the database stream
+        return db
+
+    # untimed: database statistics and classify counters for the roofline
+    db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+    db.add_targets(g, go, w.taxon_of_target)
+    db.finalize()
+    st = db.stats()
+    ctr = torch.zeros(6, dtype=torch.int64, device=dev)
+    mc.mc_classify_debug(db.handle, cp, w.n_seq, r, ro, nq, qo, label, hits, top, None, ctr, stream=stream)
+    mc.mc_classify_status(db.handle, stream)
+    ctr = ctr.cpu().numpy()
+    db.free()
+    torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step(g, go, r, ro, qo)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    mc.mc_trace_report(reset=True)
+    mc.mc_trace_enable(True)
+    launches0 = mc.mc_kernel_launches()
+    ev_start = torch.cuda.Event(enable_timing=True)
+    ev_end = torch.cuda.Event(enable_timing=True)
+    mids, starts = [], []
+    ev_start.record(stream)
+    for _ in range(args.steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        starts.append(e0)
+        step(g, go, r, ro, qo, mids)
+    ev_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches = mc.mc_kernel_launches() - launches0
+    mc.mc_trace_enable(False)
+    trace = mc.mc_trace_report(reset=True)
+    clk = clocks.stop()
+    total_ms = ev_start.elapsed_time(ev_end)
+    build_ms = sum(a.elapsed_time(b) for a, b in zip(starts, mids))
+    ends = starts[1:] + [ev_end]
+    cls_ms = sum(a.elapsed_time(b) for a, b in zip(mids, ends))
+
+    # max over ranks
+    t = torch.tensor([total_ms, build_ms, cls_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms, build_ms, cls_ms = t.tolist()
+
+    # end-to-end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        hg, hgo = torch.from_numpy(w.genomes).pin_memory(), torch.from_numpy(w.goffs.view(np.int64)).pin_memory()
+        hr, hro = torch.from_numpy(w.reads).pin_memory(), torch.from_numpy(w.roffs.view(np.int64)).pin_memory()
+        hqo = torch.from_numpy(w.qoffs.view(np.int32)).pin_memory()
+        hl = torch.empty(nq, dtype=torch.int32).pin_memory()
+        hh = torch.empty(nq, dtype=torch.int32).pin_memory()
+        h2d = sum(x.numel() * x.element_size() for x in (hg, hgo, hr, hro, hqo))
+        d2h = 2 * nq * 4
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                dg, dgo = hg.to(dev, non_blocking=True), hgo.to(dev, non_blocking=True)
+                dr, dro, dqo = hr.to(dev, non_blocking=True), hro.to(dev, non_blocking=True), hqo.to(dev, non_blocking=True)
+            step(dg, dgo, dr, dro, dqo)
+            with torch.cuda.stream(stream):
+                hl.copy_(label, non_blocking=True)
+                hh.copy_(hits, non_blocking=True)
+            stream.synchronize()
+
+        for _ in range(args.warmup):
+            e2e_step()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        e2e_ms = (time.perf_counter() - t0) * 1e3
+        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e_ms = te.item()
+        e2e = {"value": world * nq * args.steps / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": e2e_ms / args.steps}
+
+    # roofline of the dominant kernel
+    kernels = {k: {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)} for k, (n, ms) in trace.items()}
+    dom = max(kernels, key=lambda k: kernels[k]["total_ms"]) if kernels else None
+    peak, peak_src = measured_peaks()
+    roof = None
+    if dom:
+        per_step_bytes = algorithmic_bytes(dom, w, st, ctr)
+        per_launch_count = kernels[dom]["launches"] / args.steps
+        traffic_db = load_traffic()
+        traffic = None
+        tinfo = traffic_db.get(dom)
+        if tinfo and tinfo.get("src_sha") == kernel_source_hash() and tinfo.get("workload") == args.workload:
+            traffic = tinfo.get("bytes_per_launch")
+        if per_step_bytes is not None:
+            per_launch_bytes = per_step_bytes / per_launch_count
+            achieved = per_launch_bytes / (kernels[dom]["avg_ms"] * 1e-3) / 1e9
+            roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic,
+                    "algorithmic_bytes_per_launch": per_launch_bytes, "peak_source": peak_src + " (burst)"}
+
+    value = world * nq * args.steps / (total_ms * 1e-3) / 1e6
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(w, args, world),
+        "build_gbps": round(world * w.n_bp * args.steps / (build_ms * 1e-3) / 1e9, 3),
+        "classify_mreads_s": round(world * nq * args.steps / (cls_ms * 1e-3) / 1e6, 3),
+        "classify_mates_mreads_s": round(world * w.n_seq * args.steps / (cls_ms * 1e-3) / 1e6, 3),
+        "build_ms_per_step": round(build_ms / args.steps, 3), "classify_ms_per_step": round(cls_ms / args.steps, 3),
+        "db": {k: st[k] for k in ["n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys", "table_slots",
+                                  "max_probe", "load_factor"]},
+        "classify_counters": {"features": int(ctr[0]), "locations": int(ctr[1]), "distinct_locations": int(ctr[2]),
+                              "large_path_queries": int(ctr[3]), "features_found": int(ctr[4]),
+                              "bucket_sectors": int(ctr[5])},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4)} for k, v in kernels.items()},
+        "clocks": clk,
+        "generation_s": round(t_gen, 1),
+    }
+    return out, w
+
+
+# ------------------------------------------------------------ CPU arms
+def oracle_sample(w, n_genera: int, n_pairs: int):
+    """A bounded slice of the workload: the first n_genera genera (10 genomes
+    each) and read pairs drawn from them, generated like the full reads."""
+    import synth
+    n_t = min(w.n_targets, 10 * n_genera)
+    hi = int(w.goffs[n_t])
+    genomes, goffs = w.genomes[:hi], w.goffs[:n_t + 1].copy()
+    reads, roffs, qoffs, _ = synth.simulate_reads(
+        4242, n_pairs, genomes, goffs, paired=True, len_lo=150, len_hi=150, sub=0.005, indel=0.0005, frag_b=300.0,
+        frag_sd_abs=30.0)
+    return genomes, goffs, reads, roffs, qoffs, n_t
+
+
+def time_oracle(w, n_genera: int, n_pairs: int):
+    import oracle
+    cores = os.cpu_count() or 1
+    genomes, goffs, reads, roffs, qoffs, n_t = oracle_sample(w, n_genera, n_pairs)
+    t0 = time.perf_counter()
+    odb = oracle.DB(genomes, goffs, n_threads=cores, **w.db_params)
+    tb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    odb.classify(w.parent, w.taxon_of_target, reads, roffs, qoffs, n_threads=cores, **w.cls_params)
+    tc = time.perf_counter() - t0
+    bp = int(goffs[-1])
+    # scale each half to the full workload
+    t_full = tb * (w.n_bp / bp) + tc * (w.n_queries / n_pairs)
+    value = w.n_queries / t_full / 1e6
+    sample = (f"oracle build of {n_t} genomes ({bp / 1e6:.1f} Mbp, {tb:.2f} s) + classify of {n_pairs} pairs "
+              f"({tc:.2f} s) on {cores} threads, each scaled to the full workload ({w.n_bp / 1e9:.2f} Gbp, "
+              f"{w.n_queries} pairs)")
+    return {"value": round(value, 5), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+            "build_gbps": round(bp / tb / 1e9, 5), "classify_mreads_s": round(n_pairs / tc / 1e6, 5)}, tb + tc
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle as it stands, bounded sample per step."""
+    w = make_workload(args.workload, 0)
+    n_gen, n_pairs = max(1, args.cpu_sample_genera // 2), max(1000, args.cpu_sample_pairs // 4)
+    for _ in range(args.warmup):
+        time_oracle(w, n_gen, n_pairs)
+    vals, secs = [], 0.0
+    last = None
+    for _ in range(args.steps):
+        last, s = time_oracle(w, n_gen, n_pairs)
+        vals.append(last["value"])
+        secs += s
+    value = statistics.median(vals)
+    cb = dict(last, value=value)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs / args.steps * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "config": workload_config(w, args, world), "cpu_baseline": cb,
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+# ------------------------------------------------------------------ main
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return 0
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    out, w = run_gpu(args, rank, world, local_rank)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            cb, _ = time_oracle(w, args.cpu_sample_genera, args.cpu_sample_pairs)
+            out["cpu_baseline"] = cb
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

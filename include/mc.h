@@ -224,13 +224,32 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
 /* mc_classify with test outputs.  cands (device out, nullable):
  * n_queries x max_candidates x {score, target, first window, last window}
  * of the top candidates (unused slots: score 0, target MC_NO_TARGET).
- * counters (device out, nullable, 4 x uint64, accumulated): features looked
+ * counters (device out, nullable, 6 x uint64, accumulated): features looked
  * up, locations gathered, distinct locations, queries sent to the
- * large-histogram path. */
+ * large-histogram path, features found, 32-byte sectors of the gathered
+ * buckets. */
 int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                       const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,
                       void* stream);
+
+/* ---------------------------------------------------------------------
+ * Tracing and launch accounting (no counterpart in the paper beyond its
+ * per-stage breakdown, Section 5.5).
+ * ------------------------------------------------------------------- */
+
+/* Enables (1) or disables (0) tracing: each kernel launch of the library is
+ * bracketed by CUDA events recorded on the stream it is launched on. */
+int mc_trace_enable(int on);
+
+/* Synchronises the recorded events and writes one line per kernel,
+ * "name launches total_ms", to buf (host, NUL-terminated, truncated to
+ * len).  Returns the number of bytes the full report needs (excluding the
+ * NUL).  reset != 0 clears the accumulated times afterwards. */
+int mc_trace_report(char* buf, size_t len, int reset);
+
+/* Number of kernel launches the library has issued in this process. */
+uint64_t mc_kernel_launches(void);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* mc_last_error_string(void);

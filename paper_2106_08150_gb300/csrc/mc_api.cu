@@ -4,6 +4,8 @@
 // mc_classify.cu; this file only validates, allocates, copies metadata and
 // launches.
 #include <algorithm>
+#include <atomic>
+#include <string>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -74,7 +76,45 @@ struct DevBuf {
 
 }  // namespace
 
+namespace {
+// ---- launch accounting and tracing
+std::atomic<uint64_t> g_launches{0};
+std::atomic<int> g_trace_on{0};
+std::mutex g_trace_mu;
+struct TraceRec {
+    const char* name;
+    cudaEvent_t a, b;
+};
+std::vector<TraceRec> g_trace_pending;
+struct TraceAcc {
+    uint64_t n = 0;
+    double ms = 0;
+};
+std::vector<std::pair<std::string, TraceAcc>> g_trace_acc;
+}  // namespace
+
 namespace mc {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+TraceScope::TraceScope(const char* name, cudaStream_t s) : stream(s) {
+    if (!g_trace_on.load(std::memory_order_relaxed)) return;
+    TraceRec r{name, nullptr, nullptr};
+    if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    cudaEventRecord(r.a, s);
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    slot = (int)g_trace_pending.size();
+    g_trace_pending.push_back(r);
+}
+
+TraceScope::~TraceScope() {
+    if (slot < 0) return;
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    if (slot < (int)g_trace_pending.size()) cudaEventRecord(g_trace_pending[slot].b, stream);
+}
+
 void* Mem::alloc(size_t bytes, cudaStream_t s) const { return a.alloc(a.ctx, bytes, (void*)s); }
 void Mem::free(void* p, size_t bytes, cudaStream_t s) const {
     if (p) a.free(a.ctx, p, bytes, (void*)s);
@@ -174,6 +214,47 @@ int check_cls(const mc_classify_params* p) {
 extern "C" {
 
 int mc_version(void) { return MC_API_VERSION; }
+
+uint64_t mc_kernel_launches(void) { return g_launches.load(); }
+
+int mc_trace_enable(int on) {
+    g_trace_on.store(on ? 1 : 0);
+    return MC_OK;
+}
+
+int mc_trace_report(char* buf, size_t len, int reset) {
+    std::lock_guard<std::mutex> lock(g_trace_mu);
+    for (TraceRec& r : g_trace_pending) {
+        float ms = 0;
+        if (cudaEventSynchronize(r.b) == cudaSuccess && cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+            auto it = std::find_if(g_trace_acc.begin(), g_trace_acc.end(),
+                                   [&](const std::pair<std::string, TraceAcc>& x) { return x.first == r.name; });
+            if (it == g_trace_acc.end()) {
+                g_trace_acc.push_back({r.name, TraceAcc()});
+                it = g_trace_acc.end() - 1;
+            }
+            it->second.n += 1;
+            it->second.ms += ms;
+        }
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    cudaGetLastError();
+    g_trace_pending.clear();
+    std::string out;
+    char line[256];
+    for (auto& x : g_trace_acc) {
+        snprintf(line, sizeof line, "%s %llu %.6f\n", x.first.c_str(), (unsigned long long)x.second.n, x.second.ms);
+        out += line;
+    }
+    if (buf && len) {
+        size_t n = std::min(len - 1, out.size());
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    if (reset) g_trace_acc.clear();
+    return (int)out.size();
+}
 
 const char* mc_last_error_string(void) { return g_err; }
 

@@ -135,17 +135,17 @@ cudaError_t scan_exclusive_sum(const Mem& mem, const uint64_t* in, uint64_t* out
     if (n == 0) return cudaMemsetAsync(out, 0, sizeof(uint64_t), s);
     uint64_t n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     if (n_tiles == 1) {
-        k_scan_downsweep<<<1, BT, 0, s>>>(in, out, n, nullptr, 1, out + n);
+        MC_LAUNCH("scan_downsweep", s, k_scan_downsweep<<<1, BT, 0, s>>>(in, out, n, nullptr, 1, out + n));
         return cudaGetLastError();
     }
     Tmp<uint64_t> sums(mem, n_tiles + 1, s);
     if (!sums.ok()) return cudaErrorMemoryAllocation;
-    k_scan_tile_sums<<<grid_for(n_tiles), BT, 0, s>>>(in, n, sums.ptr, n_tiles);
+    MC_LAUNCH("scan_tile_sums", s, k_scan_tile_sums<<<grid_for(n_tiles), BT, 0, s>>>(in, n, sums.ptr, n_tiles));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = scan_exclusive_sum(mem, sums.ptr, sums.ptr, n_tiles, s);
     if (e != cudaSuccess) return e;
-    k_scan_downsweep<<<grid_for(n_tiles), BT, 0, s>>>(in, out, n, sums.ptr, n_tiles, out + n);
+    MC_LAUNCH("scan_downsweep", s, k_scan_downsweep<<<grid_for(n_tiles), BT, 0, s>>>(in, out, n, sums.ptr, n_tiles, out + n));
     return cudaGetLastError();
 }
 
@@ -168,8 +168,8 @@ __global__ void k_window_counts(const uint64_t* __restrict__ offs, uint32_t n, u
 cudaError_t window_offsets(const Mem& mem, const SketchParams& p, uint32_t n_seq, const uint64_t* offs,
                            uint64_t* win_offs, uint32_t* bad_offs, cudaStream_t s) {
     if (n_seq > 0) {
-        k_window_counts<<<grid_for((n_seq + BT - 1) / BT), BT, 0, s>>>(offs, n_seq, p.k, p.stride, win_offs,
-                                                                         bad_offs);
+        MC_LAUNCH("window_counts", s, k_window_counts<<<grid_for((n_seq + BT - 1) / BT), BT, 0, s>>>(offs, n_seq, p.k, p.stride, win_offs,
+                                                                         bad_offs));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -236,12 +236,12 @@ cudaError_t launch_sketch(const SketchParams& p, uint32_t n_seq, const uint8_t* 
     uint32_t g = grid_for(blocks, 16);
     int r = sketch_r_for(p.w);
     if (r == 4)
-        k_sketch<4, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real);
+        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<4, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real));
     else if (r == 8)
-        k_sketch<8, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real);
+        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<8, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real));
     else
-        k_sketch<16, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts,
-                                            real);
+        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<16, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts,
+                                            real));
     return cudaGetLastError();
 }
 }  // namespace
@@ -356,12 +356,12 @@ cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_tota
         uint32_t shift = 32 + 8 * pass;
         int filter = pass == 0;
         uint32_t g = grid_for(tiles);
-        k_radix_hist<<<g, BT, 0, s>>>(src, n, shift, filter, hist.ptr, tiles);
+        MC_LAUNCH("radix_hist", s, k_radix_hist<<<g, BT, 0, s>>>(src, n, shift, filter, hist.ptr, tiles));
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         e = scan_exclusive_sum(mem, hist.ptr, hist.ptr, 256 * tiles, s);
         if (e != cudaSuccess) return e;
-        k_radix_scatter<<<g, BT, 0, s>>>(src, dst, n, shift, filter, hist.ptr, tiles);
+        MC_LAUNCH("radix_scatter", s, k_radix_scatter<<<g, BT, 0, s>>>(src, dst, n, shift, filter, hist.ptr, tiles));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t* t = src;
@@ -568,10 +568,10 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
         tkeys(mem, tiles + 1, s);
     if (!tmax.ok() || !tpre.ok() || !tkept.ok() || !tkeys.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
-        k_fin_runmax<<<g, BT, 0, s>>>(sorted, n, tmax.ptr, tiles);
-        k_exclusive_max_u64<<<1, BT, 0, s>>>(tmax.ptr, tpre.ptr, tiles);
-        k_fin_pass<0><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, nullptr, 0, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr);
+        MC_LAUNCH("fin_runmax", s, k_fin_runmax<<<g, BT, 0, s>>>(sorted, n, tmax.ptr, tiles));
+        MC_LAUNCH("exclusive_max_u64", s, k_exclusive_max_u64<<<1, BT, 0, s>>>(tmax.ptr, tpre.ptr, tiles));
+        MC_LAUNCH("fin_count", s, k_fin_pass<0><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, nullptr, 0, nullptr,
+                                       nullptr, nullptr, nullptr, nullptr, nullptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = scan_exclusive_sum(mem, tkept.ptr, tkept.ptr, tiles, s)) != cudaSuccess) return e;
         if ((e = scan_exclusive_sum(mem, tkeys.ptr, tkeys.ptr, tiles, s)) != cudaSuccess) return e;
@@ -584,8 +584,8 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     Tmp<uint32_t> khk(mem, n_keys, s);
     if (!locs.ok() || !kpairs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
-        k_fin_pass<1><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, wbase, n_targets,
-                                       locs.ptr, kpairs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr);
+        MC_LAUNCH("fin_emit", s, k_fin_pass<1><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, wbase, n_targets,
+                                       locs.ptr, kpairs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     }
@@ -598,8 +598,8 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     Tmp<int64_t> kt_max(mem, ktiles + 1, s), kt_pre(mem, ktiles + 1, s);
     if (!kt_max.ok() || !kt_pre.ok()) return cudaErrorMemoryAllocation;
     if (n_keys > 0) {
-        k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles);
-        k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles);
+        MC_LAUNCH("tab_dispmax", s, k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles));
+        MC_LAUNCH("exclusive_max_i64", s, k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(&host_maxa, kt_pre.ptr + ktiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
@@ -610,8 +610,8 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     if (!table.ok()) return cudaErrorMemoryAllocation;
     if ((e = cudaMemsetAsync(table.ptr, 0, table_len * sizeof(uint4), s)) != cudaSuccess) return e;
     if (n_keys > 0) {
-        k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t, kt_pre.ptr,
-                                                   ktiles, table.ptr, (unsigned int*)(ctr.ptr + 1));
+        MC_LAUNCH("tab_emit", s, k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t, kt_pre.ptr,
+                                                   ktiles, table.ptr, (unsigned int*)(ctr.ptr + 1)));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     unsigned long long host_ctr[2] = {0, 0};
@@ -663,13 +663,13 @@ __global__ void k_tax_lineage(const uint32_t* __restrict__ parent, uint32_t n, c
 
 cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* depth, uint32_t* max_depth,
                             uint32_t* cycle_flag, cudaStream_t s) {
-    k_tax_depth<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, max_depth, cycle_flag);
+    MC_LAUNCH("tax_depth", s, k_tax_depth<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, max_depth, cycle_flag));
     return cudaGetLastError();
 }
 
 cudaError_t taxonomy_lineage(const uint32_t* parent, uint32_t n_taxa, const uint32_t* depth, uint32_t* lin,
                              uint32_t stride, cudaStream_t s) {
-    k_tax_lineage<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, lin, stride);
+    MC_LAUNCH("tax_lineage", s, k_tax_lineage<<<grid_for((n_taxa + BT - 1) / BT), BT, 0, s>>>(parent, n_taxa, depth, lin, stride));
     return cudaGetLastError();
 }
 
@@ -703,15 +703,15 @@ __global__ void k_dump_gather(const uint64_t* __restrict__ locs, const uint64_t*
 cudaError_t dump_select(const uint4* table, uint64_t table_len, uint64_t lo, uint64_t hi, uint32_t* keys,
                         uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel, cudaStream_t s) {
     if (table_len == 0) return cudaSuccess;
-    k_dump_select<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, lo, hi, keys, offs, counts,
-                                                                      cap, n_sel);
+    MC_LAUNCH("dump_select", s, k_dump_select<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, lo, hi, keys, offs, counts,
+                                                                      cap, n_sel));
     return cudaGetLastError();
 }
 
 cudaError_t dump_gather(const uint64_t* locs, const uint64_t* src_off, const uint32_t* counts, const uint64_t* dst_off,
                         uint64_t n, uint64_t* out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    k_dump_gather<<<grid_for(n, 32), 128, 0, s>>>(locs, src_off, counts, dst_off, n, out);
+    MC_LAUNCH("dump_gather", s, k_dump_gather<<<grid_for(n, 32), 128, 0, s>>>(locs, src_off, counts, dst_off, n, out));
     return cudaGetLastError();
 }
 

@@ -227,7 +227,7 @@ __device__ __forceinline__ void write_unclassified(const ClassifyQuery& Q, uint3
 
 template <int R>
 __device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
-                             unsigned long long (&ctr)[3]) {
+                             unsigned long long (&ctr)[5]) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     const SketchParams& p = db.sp;
@@ -244,7 +244,7 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
 
     // 1. sketch + lookup: list of (bucket offset, size) of found features
     uint32_t n_list = 0;
-    uint64_t n_feat = 0;
+    uint64_t n_feat = 0, n_sect = 0;
     for (uint32_t i = m0; i < m1; ++i) {
         uint64_t L = Q.offs[i + 1] - Q.offs[i];
         uint64_t nw = num_windows(L, p.k, p.stride);
@@ -261,6 +261,8 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
                 uint32_t idx = n_list + __popc(found & lt);
                 S.l_off[idx] = off;
                 S.l_cnt[idx] = c;
+                // 32-byte sectors the bucket occupies (for the roofline counters)
+                n_sect += ((off * 8 + (uint64_t)c * 8 - 1) >> 5) - ((off * 8) >> 5) + 1;
             }
             n_list += __popc(found);
         }
@@ -310,6 +312,8 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
     ctr[0] += n_feat;
     ctr[1] += H;
     ctr[2] += distinct;
+    ctr[3] += n_list;
+    ctr[4] += n_sect;  // per lane; summed over the warp at flush
 
     // 3. sliding-window scores (Section 4.6)
     uint64_t span = (m1 - m0 <= 1) ? span_sum : (span_sum > Q.max_insert ? span_sum : (uint64_t)Q.max_insert);
@@ -368,11 +372,19 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
     return Q_DONE;
 }
 
-__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, unsigned long long (&ctr)[3]) {
+// counters: [0] features looked up, [1] locations gathered, [2] distinct
+// locations, [3] queries on the large path, [4] features found, [5] 32-byte
+// sectors of the gathered buckets.
+__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, unsigned long long (&ctr)[5]) {
+    unsigned long long sect = ctr[4];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) sect += __shfl_xor_sync(FULL_MASK, sect, o);
     if (Q.counters && lane_id() == 0) {
         atomicAdd(Q.counters + 0, ctr[0]);
         atomicAdd(Q.counters + 1, ctr[1]);
         atomicAdd(Q.counters + 2, ctr[2]);
+        atomicAdd(Q.counters + 4, ctr[3]);
+        atomicAdd(Q.counters + 5, sect);
     }
 }
 
@@ -394,7 +406,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_smem(ClassifyDb 
     S.kcap = KA;
     S.list_cap = list_cap;
     S.win_cap = WIN_A;
-    unsigned long long ctr[3] = {0, 0, 0};
+    unsigned long long ctr[5] = {0, 0, 0, 0, 0};
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t q = gw; q < Q.n_q; q += nw) {
@@ -429,7 +441,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_large(ClassifyDb
     S.l_pre = glpre + (uint64_t)gw * (LIST_B + 1);
     S.list_cap = LIST_B;
     S.win_cap = MC_MAX_QUERY_WINDOWS;
-    unsigned long long ctr[3] = {0, 0, 0};
+    unsigned long long ctr[5] = {0, 0, 0, 0, 0};
     const uint32_t n = *ovf_n;
     unsigned long long n_large = 0;
     for (;;) {
@@ -478,7 +490,7 @@ cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery
     uint64_t cap_blocks = (uint64_t)sms * occ * 8;
     uint32_t g = (uint32_t)(blocks < cap_blocks ? blocks : cap_blocks);
     if (g == 0) return cudaSuccess;
-    ka<<<g, CLS_WARPS * 32, smem, s>>>(db, Q, list_cap, ovf.ptr, ovf_n);
+    MC_LAUNCH("classify_smem", s, ka<<<g, CLS_WARPS * 32, smem, s>>>(db, Q, list_cap, ovf.ptr, ovf_n));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
 
     // large path (persistent warps, exits at once if nothing was queued)
@@ -488,8 +500,8 @@ cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery
     Tmp<uint32_t> gcnts(mem, b_warps * KB_SLOTS, s), glcnt(mem, b_warps * LIST_B, s),
         glpre(mem, b_warps * (LIST_B + 1), s);
     if (!gkeys.ok() || !gloff.ok() || !gcnts.ok() || !glcnt.ok() || !glpre.ok()) return cudaErrorMemoryAllocation;
-    k_classify_large<R><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, gkeys.ptr, gcnts.ptr,
-                                                           gloff.ptr, glcnt.ptr, glpre.ptr);
+    MC_LAUNCH("classify_large", s, k_classify_large<R><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, gkeys.ptr, gcnts.ptr,
+                                                           gloff.ptr, glcnt.ptr, glpre.ptr));
     return cudaGetLastError();
 }
 

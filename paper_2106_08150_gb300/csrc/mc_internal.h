@@ -9,6 +9,21 @@
 
 namespace mc {
 
+// Launch accounting and optional per-kernel event tracing (mc_api.cu).
+void note_launch();
+struct TraceScope {
+    int slot = -1;
+    cudaStream_t stream = nullptr;
+    TraceScope(const char* name, cudaStream_t s);
+    ~TraceScope();
+};
+#define MC_LAUNCH(name, stream, ...)                \
+    do {                                            \
+        ::mc::TraceScope trace_scope_((name), (stream)); \
+        __VA_ARGS__;                                \
+        ::mc::note_launch();                        \
+    } while (0)
+
 // Device memory through the database's allocator (stream-ordered).
 struct Mem {
     mc_allocator a;

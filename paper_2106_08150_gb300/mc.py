@@ -79,6 +79,9 @@ _SIGS = {
     "mc_db_dump": ([_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i),
     "mc_window_offsets": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp], _i),
     "mc_sketch": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp, _u64, _vp, _vp, _vp], _i),
+    "mc_trace_enable": ([_i], _i),
+    "mc_trace_report": ([ctypes.c_char_p, ctypes.c_size_t, _i], _i),
+    "mc_kernel_launches": ([], _u64),
 }
 for _name, (_args, _res) in _SIGS.items():
     _f = getattr(_lib, _name)
@@ -88,7 +91,7 @@ for _name, (_args, _res) in _SIGS.items():
 def declared_symbols() -> list[str]:
     """Function names declared in include/mc.h."""
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(mc_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|uint64_t|const char\*)\s+(mc_\w+)\s*\(", text, re.M)))
 
 
 def _check(code: int):
@@ -231,6 +234,26 @@ def mc_window_offsets(params: mc_db_params, n_seq: int, offs, win_offs, stream=N
 def mc_sketch(params: mc_db_params, n_seq: int, seq, offs, win_offs, n_windows: int, sketch, counts, stream=None):
     _check(_lib.mc_sketch(ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), _ptr(win_offs), n_windows,
                           _ptr(sketch), _ptr(counts), _stream(stream)))
+
+
+def mc_trace_enable(on: bool = True):
+    _check(_lib.mc_trace_enable(int(on)))
+
+
+def mc_trace_report(reset: bool = True) -> dict:
+    """{kernel: (launches, total_ms)} of the traced launches since the last reset."""
+    n = _lib.mc_trace_report(None, 0, 0)
+    buf = ctypes.create_string_buffer(n + 1)
+    _lib.mc_trace_report(buf, n + 1, int(reset))
+    out = {}
+    for line in buf.value.decode().splitlines():
+        name, cnt, ms = line.split()
+        out[name] = (int(cnt), float(ms))
+    return out
+
+
+def mc_kernel_launches() -> int:
+    return int(_lib.mc_kernel_launches())
 
 
 # ------------------------------------------------------- convenience layer
