@@ -159,8 +159,9 @@ def kernel_source_hash() -> str:
 
 
 def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
-    """Algorithmic HBM bytes of ALL launches of `kernel` in one step (see
-    the design doc, roofline section, for the per-unit figures)."""
+    """Algorithmic HBM bytes of ALL launches of `kernel` in one step: every
+    input the kernel needs read once and every output written once, random
+    probes and bucket reads counted in whole 32-byte sectors."""
     n_win = st["n_windows"]
     s = w.db_params["sketch_size"]
     slots = n_win * s  # emitted pair slots (sentinels included)
@@ -171,18 +172,21 @@ def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
         return (slots + 3 * n_real) * 8.0 + 4 * n_real * 8.0  # read every input once, write every real pair
     if kernel == "radix_hist":
         return (slots + 3 * n_real) * 8.0
-    if kernel in ("fin_count", "fin_runmax"):
+    if kernel == "fin_count":
         return n_real * 8.0
     if kernel == "fin_emit":
-        return n_real * 8.0 + st["n_locations"] * 16.0 + st["n_keys"] * 20.0
+        return n_real * 8.0 + st["n_locations"] * 8.0 + st["n_keys"] * 20.0
     if kernel == "tab_emit":
         return st["n_keys"] * 20.0 + st["n_keys"] * 16.0
-    if kernel == "classify_smem" and ctr is not None:
-        # bases + mate offsets + query offsets, one 32 B table sector per
-        # feature looked up, the 32 B sectors of every gathered bucket,
-        # 12 B of outputs per query
-        n_reads_bytes = int(w.roffs[-1]) + 8 * (w.n_seq + 1) + 4 * (w.n_queries + 1)
-        return n_reads_bytes + 32.0 * float(ctr[0]) + 32.0 * float(ctr[5]) + 12.0 * w.n_queries
+    if ctr is None:
+        return None
+    reads_in = int(w.roffs[-1]) + 8 * (w.n_seq + 1) + 4 * (w.n_queries + 1)
+    if kernel == "classify_lookup":
+        # bases + offsets, one 32 B table sector per feature, bucket list + metadata out
+        return reads_in + 32.0 * float(ctr[0]) + 8.0 * float(ctr[4]) + 16.0 * w.n_queries
+    if kernel == "classify_score":
+        # metadata + bucket list in, the 32 B sectors of every gathered bucket, 12 B of outputs
+        return 16.0 * w.n_queries + 8.0 * float(ctr[4]) + 32.0 * float(ctr[5]) + 12.0 * w.n_queries
     return None
 
 

@@ -62,6 +62,8 @@ typedef enum mc_status {
 #define MC_MAX_WINDOW_KMERS 512   /* w - k + 1 */
 #define MC_MAX_CANDIDATES 8       /* m, top hits kept per read */
 #define MC_MAX_QUERY_WINDOWS 64   /* windows of all mates of one query */
+#define MC_MAX_QUERY_MATES 31     /* sequences (mates) of one query */
+#define MC_MAX_INSERT 65536       /* largest max_insert */
 
 typedef struct mc_db mc_db; /* opaque; owns every device allocation it makes */
 
@@ -86,7 +88,8 @@ typedef struct mc_classify_params {
     uint32_t hits_min;       /* minimum top score to classify (Section 5.6: hit threshold) */
     uint32_t lca_band_pct;   /* 0..100: candidates with score >= (100-band)% of the top score
                                 are "close"; one close candidate -> its taxon, several -> LCA */
-    uint32_t max_insert;     /* read pairs: sliding-window span is max(len1+len2, max_insert) */
+    uint32_t max_insert;     /* read pairs: sliding-window span is max(len1+len2, max_insert);
+                                0..MC_MAX_INSERT */
 } mc_classify_params;
 
 /* Device memory provider.  alloc returns device memory of at least `bytes`
@@ -151,7 +154,9 @@ int mc_db_finalize(mc_db* db);
  *  qoffs     : device, n_queries+1 indices into the sequences: query q is
  *              mates qoffs[q] .. qoffs[q+1]-1 (1 = single-end, 2 = pair;
  *              all windows of all mates of a query form one hit list).
- *              At most MC_MAX_QUERY_WINDOWS windows per query.
+ *              At most MC_MAX_QUERY_MATES mates and MC_MAX_QUERY_WINDOWS
+ *              windows per query (larger queries are left unclassified and
+ *              reported by mc_classify_status).
  *  label     : device out, n_queries taxon ids or MC_NO_TAXON.
  *  hits      : device out, n_queries top scores (0 without hits).
  *  top_target: device out (nullable), n_queries target ids or MC_NO_TARGET.

@@ -140,7 +140,7 @@ struct mc_db {
     DevBuf pending;  // u64 pairs
     uint64_t pending_n = 0, pending_real = 0;
     // published condensed layout
-    DevBuf kept_pairs, locs, table;
+    DevBuf locs, table;
     uint64_t n_kept = 0, n_keys = 0, table_len = 0, overflow_keys = 0, n_pairs = 0;
     uint32_t log_t = 1, max_probe = 0;
     bool dirty = false, has_table = false;
@@ -163,7 +163,7 @@ bool grab(mc_db* db, DevBuf& b, size_t bytes) {
 
 uint64_t held_bytes(const mc_db* db) {
     return db->depth.bytes + db->lineage.bytes + db->taxon.bytes + db->wbase.bytes + db->pending.bytes +
-           db->kept_pairs.bytes + db->locs.bytes + db->table.bytes + db->status.bytes;
+           db->locs.bytes + db->table.bytes + db->status.bytes;
 }
 
 bool within_budget(const mc_db* db, uint64_t extra) {
@@ -206,6 +206,7 @@ int check_cls(const mc_classify_params* p) {
     if (p->max_candidates < 1 || p->max_candidates > MC_MAX_CANDIDATES)
         return fail(MC_ERR_ARG, "max_candidates must be in 1..%d", MC_MAX_CANDIDATES);
     if (p->lca_band_pct > 100) return fail(MC_ERR_ARG, "lca_band_pct must be in 0..100");
+    if (p->max_insert > MC_MAX_INSERT) return fail(MC_ERR_ARG, "max_insert must be <= %d", MC_MAX_INSERT);
     return MC_OK;
 }
 
@@ -419,7 +420,8 @@ int mc_db_finalize(mc_db* db) {
     } else {
         if (!within_budget(db, n_total * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
         if (!grab(db, a, n_total * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
-        MC_CU(cudaMemcpyAsync(a.p, db->kept_pairs.p, n_old * 8, cudaMemcpyDeviceToDevice, s));
+        MC_CU(mc::reconstruct_pairs((const uint4*)db->table.p, db->table_len, (const uint64_t*)db->locs.p,
+                                    (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s));
         if (db->pending_n)
             MC_CU(cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s));
         release(db, db->pending);
@@ -443,10 +445,8 @@ int mc_db_finalize(mc_db* db) {
                            db->n_targets, &fo, s);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "finalize: layout");
-    release(db, db->kept_pairs);
     release(db, db->locs);
     release(db, db->table);
-    db->kept_pairs = DevBuf{fo.kept_pairs, fo.n_kept * 8};
     db->locs = DevBuf{fo.locs, fo.n_kept * 8};
     db->table = DevBuf{fo.table, fo.table_bytes};
     db->n_pairs += db->pending_real;
@@ -543,7 +543,6 @@ void mc_db_free(mc_db* db) {
     release(db, db->taxon);
     release(db, db->wbase);
     release(db, db->pending);
-    release(db, db->kept_pairs);
     release(db, db->locs);
     release(db, db->table);
     release(db, db->status);

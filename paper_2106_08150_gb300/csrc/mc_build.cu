@@ -179,6 +179,7 @@ cudaError_t window_offsets(const Mem& mem, const SketchParams& p, uint32_t n_seq
 // ---------------------------------------------------------------- sketch
 namespace {
 constexpr uint32_t WINDOWS_PER_TASK = 16;
+constexpr int SK_NW = 2;  // windows sketched together by a warp
 
 // One warp per window; a warp takes WINDOWS_PER_TASK consecutive windows
 // and walks the sequences they belong to.  EMIT = build pairs, else the
@@ -190,7 +191,9 @@ __global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, c
                                                uint32_t gw_base, uint64_t* __restrict__ pairs,
                                                uint32_t* __restrict__ sketch, uint32_t* __restrict__ counts,
                                                unsigned long long* real_pairs) {
+    __shared__ uint32_t cand_sm[NWARP][SK_NW * 32];
     const uint32_t lane = lane_id();
+    uint32_t* cand = cand_sm[threadIdx.x >> 5];
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t n_warps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t n_tasks = (n_windows + WINDOWS_PER_TASK - 1) / WINDOWS_PER_TASK;
@@ -205,21 +208,42 @@ __global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, c
             if (win_offs[mid] <= w0) lo = mid; else hi = mid;
         }
         uint32_t t = lo;
-        for (uint64_t lw = w0; lw < w1; ++lw) {
-            while (win_offs[t + 1] <= lw) ++t;
-            uint64_t j = lw - win_offs[t];
-            uint64_t L = offs[t + 1] - offs[t];
-            uint32_t f;
-            uint32_t cnt = warp_sketch<R>(seq + offs[t], L, j * p.stride, p, f);
-            if (EMIT) {
-                if (lane < p.s) {
-                    uint64_t v = lane < cnt ? (((uint64_t)hash_h2(f) << 32) | (uint32_t)(gw_base + lw)) : SENTINEL_PAIR;
-                    pairs[lw * p.s + lane] = v;
+        for (uint64_t lw = w0; lw < w1; lw += SK_NW) {
+            const uint8_t* sq[SK_NW];
+            uint64_t Ls[SK_NW], wss[SK_NW];
+            bool act[SK_NW];
+#pragma unroll
+            for (int i = 0; i < SK_NW; ++i) {
+                const uint64_t x = lw + i;
+                act[i] = x < w1;
+                if (act[i]) {
+                    while (win_offs[t + 1] <= x) ++t;
+                    sq[i] = seq + offs[t];
+                    Ls[i] = offs[t + 1] - offs[t];
+                    wss[i] = (x - win_offs[t]) * p.stride;
+                } else {
+                    sq[i] = seq;
+                    Ls[i] = 0;
+                    wss[i] = 0;
                 }
-                real += cnt;
-            } else {
-                if (lane < p.s) sketch[lw * p.s + lane] = lane < cnt ? f : 0u;
-                if (lane == 0) counts[lw] = cnt;
+            }
+            uint32_t f[SK_NW], cnt[SK_NW];
+            warp_sketch_multi<R, SK_NW>(sq, Ls, wss, act, p, cand, f, cnt);
+#pragma unroll
+            for (int i = 0; i < SK_NW; ++i) {
+                if (!act[i]) continue;
+                const uint64_t x = lw + i;
+                if (EMIT) {
+                    if (lane < p.s) {
+                        uint64_t v = lane < cnt[i] ? (((uint64_t)hash_h2(f[i]) << 32) | (uint32_t)(gw_base + x))
+                                                   : SENTINEL_PAIR;
+                        pairs[x * p.s + lane] = v;
+                    }
+                    real += cnt[i];
+                } else {
+                    if (lane < p.s) sketch[x * p.s + lane] = lane < cnt[i] ? f[i] : 0u;
+                    if (lane == 0) counts[x] = cnt[i];
+                }
             }
         }
     }
@@ -291,51 +315,70 @@ __global__ void __launch_bounds__(BT) k_radix_hist(const uint64_t* __restrict__ 
     }
 }
 
+// Stable scatter of one pass.  Each tile ranks its elements by digit
+// (warp match + per-warp counters keep input order among equal digits),
+// stages them in shared memory in digit order, and writes every digit's run
+// to its global offset with consecutive threads on consecutive addresses.
 __global__ void __launch_bounds__(BT) k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
                                                       uint64_t n, uint32_t shift, int filter,
                                                       const uint64_t* __restrict__ offs, uint64_t n_tiles) {
     __shared__ uint32_t wc[NWARP][257];
+    __shared__ uint32_t dstart[256];
+    __shared__ uint64_t gbase[256];
+    __shared__ uint64_t staged[RS_TILE];
+    __shared__ uint64_t sm[NWARP];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         for (int i = threadIdx.x; i < NWARP * 257; i += BT) (&wc[0][0])[i] = 0;
+        gbase[threadIdx.x] = offs[(uint64_t)threadIdx.x * n_tiles + tile];
         __syncthreads();
         uint64_t v[RS_ITEMS];
         uint32_t dr[RS_ITEMS];
-        uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
+        const uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; ++i) {
-            uint64_t e = base + (uint64_t)i * 32;
-            bool ok = e < n;
-            v[i] = ok ? in[e] : SENTINEL_PAIR;
-            uint32_t d = (!ok || (filter && v[i] == SENTINEL_PAIR)) ? 256u : ((uint32_t)(v[i] >> shift) & 255u);
-            uint32_t peers = __match_any_sync(FULL_MASK, d);
-            uint32_t rank = __popc(peers & lt);
-            uint32_t before = wc[w][d];
+            const uint64_t e = base + (uint64_t)i * 32;
+            v[i] = e < n ? in[e] : SENTINEL_PAIR;
+        }
+#pragma unroll
+        for (int i = 0; i < RS_ITEMS; ++i) {
+            const uint64_t e = base + (uint64_t)i * 32;
+            const bool ok = e < n;
+            const uint32_t d = (!ok || (filter && v[i] == SENTINEL_PAIR)) ? 256u : ((uint32_t)(v[i] >> shift) & 255u);
+            const uint32_t peers = __match_any_sync(FULL_MASK, d);
+            const uint32_t rank = __popc(peers & lt);
+            const uint32_t before = wc[w][d];
             __syncwarp();
             if (rank == 0) wc[w][d] = before + __popc(peers);
             __syncwarp();
             dr[i] = (d << 16) | (before + rank);
         }
         __syncthreads();
-        {
-            uint32_t run = 0;
+        // per digit: exclusive prefix over warps, then digit starts in the tile
+        uint32_t run = 0;
 #pragma unroll
-            for (int i = 0; i < NWARP; ++i) {
-                uint32_t c = wc[i][threadIdx.x];
-                wc[i][threadIdx.x] = run;
-                run += c;
-            }
+        for (int i = 0; i < NWARP; ++i) {
+            const uint32_t c = wc[i][threadIdx.x];
+            wc[i][threadIdx.x] = run;
+            run += c;
         }
+        uint64_t tot;
+        const uint32_t ds = (uint32_t)block_exclusive((uint64_t)run, (uint64_t)0, OpSum(), sm, &tot);
+        dstart[threadIdx.x] = ds;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; ++i) {
-            uint32_t d = dr[i] >> 16;
-            if (d < 256u) {
-                uint64_t pos = offs[(uint64_t)d * n_tiles + tile] + wc[w][d] + (dr[i] & 0xFFFFu);
-                out[pos] = v[i];
-            }
+            const uint32_t d = dr[i] >> 16;
+            if (d < 256u) staged[dstart[d] + wc[w][d] + (dr[i] & 0xFFFFu)] = v[i];
+        }
+        __syncthreads();
+        const uint32_t count = (uint32_t)tot;
+        for (uint32_t j = threadIdx.x; j < count; j += BT) {
+            const uint64_t x = staged[j];
+            const uint32_t d = (uint32_t)(x >> shift) & 255u;
+            out[gbase[d] + (j - dstart[d])] = x;
         }
         __syncthreads();
     }
@@ -375,45 +418,146 @@ cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_tota
 // --------------------------------------------------------------- finalize
 namespace {
 constexpr int FIN_ITEMS = 8;
-constexpr uint64_t FIN_TILE = (uint64_t)BT * FIN_ITEMS;  // element = base + i*BT + t
+constexpr uint64_t FIN_TILE = (uint64_t)BT * FIN_ITEMS;  // warp w: [base + 256 w, base + 256 (w+1))
+constexpr uint32_t WBASE_SMEM = 12288;                   // targets whose window bases fit shared memory
 
 __device__ __forceinline__ uint32_t hk_of(uint64_t v) { return (uint32_t)(v >> 32); }
 
-__device__ __forceinline__ bool run_start(const uint64_t* __restrict__ a, uint64_t e, uint64_t v) {
-    return e == 0 || hk_of(a[e - 1]) != hk_of(v);
+// In the sorted pair array, e starts a feature's run if its predecessor has
+// another feature; e is kept (rank in its run < cap) unless the pair cap
+// places earlier has the same feature (runs are contiguous).
+__device__ __forceinline__ void fin_flags(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap, uint64_t e,
+                                          uint64_t& v, bool& st, bool& kept, bool& over) {
+    st = kept = over = false;
+    if (e >= n) return;
+    v = a[e];
+    const uint32_t hk = hk_of(v);
+    st = e == 0 || hk_of(a[e - 1]) != hk;
+    const bool dropped = e >= cap && hk_of(a[e - cap]) == hk;
+    kept = !dropped;
+    // the first dropped pair of an overflowing run: the pair cap earlier starts the run
+    over = dropped && (e == cap || hk_of(a[e - cap - 1]) != hk);
 }
 
-// Tile maximum of run-start indices.
-__global__ void __launch_bounds__(BT) k_fin_runmax(const uint64_t* __restrict__ a, uint64_t n,
-                                                   uint64_t* __restrict__ tmax, uint64_t n_tiles) {
+// Tile sums of kept pairs and run starts.
+__global__ void __launch_bounds__(BT) k_fin_count(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
+                                                  uint64_t* __restrict__ tkept, uint64_t* __restrict__ tkeys,
+                                                  uint64_t n_tiles) {
     __shared__ uint64_t sm[NWARP];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        uint64_t base = tile * FIN_TILE, m = 0;
+        const uint64_t base = tile * FIN_TILE + (uint64_t)w * 32 * FIN_ITEMS + lane;
+        uint32_t nk = 0, ns = 0;
 #pragma unroll
         for (int i = 0; i < FIN_ITEMS; ++i) {
-            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
-            if (e < n && run_start(a, e, a[e])) m = max(m, e);
+            uint64_t v;
+            bool st, kept, over;
+            fin_flags(a, n, cap, base + (uint64_t)i * 32, v, st, kept, over);
+            nk += kept;
+            ns += st;
         }
-        uint64_t tot = block_reduce(m, (uint64_t)0, OpMaxU(), sm);
-        if (threadIdx.x == 0) tmax[tile] = tot;
+        const uint64_t both = block_reduce(((uint64_t)ns << 32) | nk, (uint64_t)0, OpSum(), sm);
+        if (threadIdx.x == 0) {
+            tkept[tile] = both & 0xFFFFFFFFull;
+            tkeys[tile] = both >> 32;
+        }
     }
 }
 
-// Exclusive max-scan of tile maxima (single block; tiles fit comfortably).
-__global__ void __launch_bounds__(BT) k_exclusive_max_u64(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                          uint64_t n) {
-    __shared__ uint64_t sm[NWARP];
-    uint64_t carry = 0;
-    for (uint64_t base = 0; base < n; base += BT) {
-        uint64_t e = base + threadIdx.x;
-        uint64_t v = e < n ? in[e] : 0;
-        uint64_t tot;
-        uint64_t ex = block_exclusive(v, (uint64_t)0, OpMaxU(), sm, &tot);
-        if (e < n) out[e] = max(carry, ex);
-        carry = max(carry, tot);
+// Writes the condensed outputs at the scanned positions: locations of kept
+// pairs (global window -> (target, window)), and per feature its h2 value,
+// the position of its first location and the index of its first pair.
+__global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
+                                                 const uint64_t* __restrict__ tkept, const uint64_t* __restrict__ tkeys,
+                                                 uint64_t n_tiles, const uint32_t* __restrict__ wbase,
+                                                 uint32_t n_targets, uint64_t* __restrict__ locs,
+                                                 uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
+                                                 uint64_t* __restrict__ kstart, unsigned long long* overflow) {
+    extern __shared__ uint32_t wb_sm[];
+    __shared__ uint32_t wk[NWARP], wsx[NWARP];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    const bool wb_in_smem = n_targets + 1 <= WBASE_SMEM;
+    if (wb_in_smem)
+        for (uint32_t i = threadIdx.x; i <= n_targets; i += BT) wb_sm[i] = wbase[i];
+    __syncthreads();
+    const uint32_t* wb = wb_in_smem ? wb_sm : wbase;
+    unsigned long long n_over = 0;
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint64_t base = tile * FIN_TILE + (uint64_t)w * 32 * FIN_ITEMS + lane;
+        uint64_t v[FIN_ITEMS];
+        uint32_t kmask = 0, smask = 0;  // per item: kept / run start
+        uint32_t nk = 0, ns = 0;
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            bool st, kept, over;
+            fin_flags(a, n, cap, base + (uint64_t)i * 32, v[i], st, kept, over);
+            kmask |= (kept ? 1u : 0u) << i;
+            smask |= (st ? 1u : 0u) << i;
+            nk += __popc(__ballot_sync(FULL_MASK, kept));
+            ns += __popc(__ballot_sync(FULL_MASK, st));
+            n_over += over;
+        }
+        if (lane == 0) {
+            wk[w] = nk;
+            wsx[w] = ns;
+        }
+        __syncthreads();
+        uint64_t kpos = tkept[tile], kidx = tkeys[tile];
+        for (int i = 0; i < w; ++i) {
+            kpos += wk[i];
+            kidx += wsx[i];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            const bool kept = (kmask >> i) & 1u, st = (smask >> i) & 1u;
+            const uint32_t bk = __ballot_sync(FULL_MASK, kept);
+            const uint32_t bs = __ballot_sync(FULL_MASK, st);
+            const uint64_t my_k = kpos + __popc(bk & lt);
+            if (kept) {
+                const uint32_t gw = (uint32_t)v[i];
+                uint32_t lo = 0, hi = n_targets;  // last t with wb[t] <= gw
+                while (hi - lo > 1) {
+                    const uint32_t mid = (lo + hi) >> 1;
+                    if (wb[mid] <= gw) lo = mid; else hi = mid;
+                }
+                locs[my_k] = ((uint64_t)lo << 32) | (gw - wb[lo]);
+            }
+            if (st) {
+                const uint64_t my_s = kidx + __popc(bs & lt);
+                khk[my_s] = hk_of(v[i]);
+                koff[my_s] = my_k;
+                kstart[my_s] = base + (uint64_t)i * 32;
+            }
+            kpos += __popc(bk);
+            kidx += __popc(bs);
+        }
+    }
+    for (int o = 16; o >= 1; o >>= 1) n_over += __shfl_xor_sync(FULL_MASK, n_over, o);
+    if (lane == 0 && n_over) atomicAdd(overflow, n_over);
+}
+
+// Pairs (h2 << 32 | global window) of a finalized layout, in layout order:
+// the input of the next finalize after an extension.
+__global__ void k_reconstruct_pairs(const uint4* __restrict__ table, uint64_t table_len,
+                                    const uint64_t* __restrict__ locs, const uint32_t* __restrict__ wbase,
+                                    uint64_t* __restrict__ out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < table_len;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint4 e = table[i];
+        if (e.y == 0) continue;
+        const uint64_t off = (uint64_t)e.z | ((uint64_t)e.w << 32);
+        for (uint32_t j = 0; j < e.y; ++j) {
+            const uint64_t loc = locs[off + j];
+            out[off + j] = ((uint64_t)e.x << 32) | (uint32_t)(wbase[(uint32_t)(loc >> 32)] + (uint32_t)loc);
+        }
     }
 }
 
+// Exclusive max-scan of the tile maxima (one block; the tiles are few).
 __global__ void __launch_bounds__(BT) k_exclusive_max_i64(const int64_t* __restrict__ in, int64_t* __restrict__ out,
                                                           uint64_t n, int64_t* total) {
     __shared__ int64_t sm[NWARP];
@@ -427,73 +571,6 @@ __global__ void __launch_bounds__(BT) k_exclusive_max_i64(const int64_t* __restr
         carry = max(carry, tot);
     }
     if (threadIdx.x == 0) *total = carry;
-}
-
-// Per element: run start, kept (rank in run < cap).  MODE 0: tile sums of
-// kept and run starts.  MODE 1: emit outputs at the scanned positions.
-template <int MODE>
-__global__ void __launch_bounds__(BT) k_fin_pass(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
-                                                 const uint64_t* __restrict__ tpre_max, uint64_t n_tiles,
-                                                 uint64_t* __restrict__ tkept, uint64_t* __restrict__ tkeys,
-                                                 const uint32_t* __restrict__ wbase, uint32_t n_targets,
-                                                 uint64_t* __restrict__ locs, uint64_t* __restrict__ kept_pairs,
-                                                 uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
-                                                 uint64_t* __restrict__ kstart, unsigned long long* overflow) {
-    __shared__ uint64_t sm[NWARP];
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        uint64_t base = tile * FIN_TILE;
-        uint64_t rs_carry = tpre_max[tile];
-        uint64_t kept_carry = MODE == 1 ? tkept[tile] : 0;
-        uint64_t key_carry = MODE == 1 ? tkeys[tile] : 0;
-        uint64_t n_over = 0;
-        for (int i = 0; i < FIN_ITEMS; ++i) {
-            uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
-            bool in_range = e < n;
-            uint64_t v = in_range ? a[e] : 0;
-            bool st = in_range && run_start(a, e, v);
-            uint64_t tot;
-            // inclusive max-scan of start indices = exclusive scan combined with own
-            uint64_t ex = block_exclusive(st ? e : (uint64_t)0, (uint64_t)0, OpMaxU(), sm, &tot);
-            uint64_t rstart = max(rs_carry, st ? e : ex);
-            rs_carry = max(rs_carry, tot);
-            bool kept = in_range && (e - rstart) < cap;
-            if (in_range && (e - rstart) == cap) ++n_over;
-            uint64_t kt, nt;
-            uint64_t kex = block_exclusive((uint64_t)kept, (uint64_t)0, OpSum(), sm, &kt);
-            uint64_t sex = block_exclusive((uint64_t)st, (uint64_t)0, OpSum(), sm, &nt);
-            if (MODE == 1) {
-                uint64_t kpos = kept_carry + kex;
-                if (kept) {
-                    uint32_t gw = (uint32_t)v;
-                    // target of the global window: last t with wbase[t] <= gw
-                    uint32_t lo = 0, hi = n_targets;
-                    while (hi - lo > 1) {
-                        uint32_t mid = (lo + hi) >> 1;
-                        if (wbase[mid] <= gw) lo = mid; else hi = mid;
-                    }
-                    locs[kpos] = ((uint64_t)lo << 32) | (gw - wbase[lo]);
-                    kept_pairs[kpos] = v;
-                }
-                if (st) {
-                    uint64_t kidx = key_carry + sex;
-                    khk[kidx] = hk_of(v);
-                    koff[kidx] = kpos;
-                    kstart[kidx] = e;
-                }
-            }
-            kept_carry += kt;
-            key_carry += nt;
-        }
-        if (MODE == 0) {
-            if (threadIdx.x == 0) {
-                tkept[tile] = kept_carry;
-                tkeys[tile] = key_carry;
-            }
-        } else {
-            uint64_t o = block_reduce(n_over, (uint64_t)0, OpSum(), sm);
-            if (threadIdx.x == 0 && o) atomicAdd(overflow, (unsigned long long)o);
-        }
-    }
 }
 
 __device__ __forceinline__ uint64_t home_slot(uint32_t hk, uint32_t log_t) {
@@ -553,25 +630,29 @@ __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ kh
 }
 }  // namespace
 
+cudaError_t reconstruct_pairs(const uint4* table, uint64_t table_len, const uint64_t* locs, const uint32_t* wbase,
+                              uint64_t* out, cudaStream_t s) {
+    if (table_len == 0) return cudaSuccess;
+    MC_LAUNCH("reconstruct_pairs", s,
+              k_reconstruct_pairs<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, locs, wbase, out));
+    return cudaGetLastError();
+}
+
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
                            uint32_t n_targets, FinalizeOut* out, cudaStream_t s) {
     cudaError_t e;
     *out = FinalizeOut();
-    uint64_t tiles = (n + FIN_TILE - 1) / FIN_TILE;
-    uint32_t g = grid_for(tiles ? tiles : 1);
+    const uint64_t tiles = (n + FIN_TILE - 1) / FIN_TILE;
+    const uint32_t g = grid_for(tiles ? tiles : 1);
     // counters: [0] overflow keys, [1] max displacement (u32 in low word)
     Tmp<unsigned long long> ctr(mem, 4, s);
     if (!ctr.ok()) return cudaErrorMemoryAllocation;
     if ((e = cudaMemsetAsync(ctr.ptr, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
     uint64_t host_tot[2] = {0, 0};
-    Tmp<uint64_t> tmax(mem, tiles + 1, s), tpre(mem, tiles + 1, s), tkept(mem, tiles + 1, s),
-        tkeys(mem, tiles + 1, s);
-    if (!tmax.ok() || !tpre.ok() || !tkept.ok() || !tkeys.ok()) return cudaErrorMemoryAllocation;
+    Tmp<uint64_t> tkept(mem, tiles + 1, s), tkeys(mem, tiles + 1, s);
+    if (!tkept.ok() || !tkeys.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
-        MC_LAUNCH("fin_runmax", s, k_fin_runmax<<<g, BT, 0, s>>>(sorted, n, tmax.ptr, tiles));
-        MC_LAUNCH("exclusive_max_u64", s, k_exclusive_max_u64<<<1, BT, 0, s>>>(tmax.ptr, tpre.ptr, tiles));
-        MC_LAUNCH("fin_count", s, k_fin_pass<0><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, nullptr, 0, nullptr,
-                                       nullptr, nullptr, nullptr, nullptr, nullptr));
+        MC_LAUNCH("fin_count", s, k_fin_count<<<g, BT, 0, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = scan_exclusive_sum(mem, tkept.ptr, tkept.ptr, tiles, s)) != cudaSuccess) return e;
         if ((e = scan_exclusive_sum(mem, tkeys.ptr, tkeys.ptr, tiles, s)) != cudaSuccess) return e;
@@ -580,38 +661,48 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     }
     const uint64_t n_kept = host_tot[0], n_keys = host_tot[1];
-    Tmp<uint64_t> locs(mem, n_kept, s), kpairs(mem, n_kept, s), koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
+    Tmp<uint64_t> locs(mem, n_kept, s), koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
     Tmp<uint32_t> khk(mem, n_keys, s);
-    if (!locs.ok() || !kpairs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
+    if (!locs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
-        MC_LAUNCH("fin_emit", s, k_fin_pass<1><<<g, BT, 0, s>>>(sorted, n, cap, tpre.ptr, tiles, tkept.ptr, tkeys.ptr, wbase, n_targets,
-                                       locs.ptr, kpairs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
+        const size_t wb_smem = n_targets + 1 <= WBASE_SMEM ? (size_t)(n_targets + 1) * 4 : 0;
+        if ((e = cudaFuncSetAttribute(k_fin_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(WBASE_SMEM * 4))) !=
+            cudaSuccess)
+            return e;
+        MC_LAUNCH("fin_emit", s,
+                  k_fin_emit<<<g, BT, wb_smem, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets,
+                                                     locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     }
-    // feature table: T = power of two >= 2 * n_keys (load factor <= 1/2)
+    // feature table: T = power of two >= 4 * n_keys (load factor <= 1/4, so
+    // almost every probe is answered by the home slot)
     uint32_t log_t = 1;
-    while ((1ull << log_t) < 2 * n_keys) ++log_t;
-    uint64_t T = 1ull << log_t;
-    uint64_t ktiles = (n_keys + FIN_TILE - 1) / FIN_TILE;
+    while ((1ull << log_t) < 4 * n_keys) ++log_t;
+    const uint64_t T = 1ull << log_t;
+    const uint64_t ktiles = (n_keys + FIN_TILE - 1) / FIN_TILE;
     int64_t host_maxa = INT64_MIN;
     Tmp<int64_t> kt_max(mem, ktiles + 1, s), kt_pre(mem, ktiles + 1, s);
     if (!kt_max.ok() || !kt_pre.ok()) return cudaErrorMemoryAllocation;
     if (n_keys > 0) {
-        MC_LAUNCH("tab_dispmax", s, k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles));
-        MC_LAUNCH("exclusive_max_i64", s, k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles));
+        MC_LAUNCH("tab_dispmax", s,
+                  k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles));
+        MC_LAUNCH("exclusive_max_i64", s,
+                  k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(&host_maxa, kt_pre.ptr + ktiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     }
-    uint64_t last_slot = n_keys ? (uint64_t)((int64_t)(n_keys - 1) + host_maxa) : 0;
-    uint64_t table_len = (last_slot + 1 > T ? last_slot + 1 : T) + 2;
+    const uint64_t last_slot = n_keys ? (uint64_t)((int64_t)(n_keys - 1) + host_maxa) : 0;
+    const uint64_t table_len = (last_slot + 1 > T ? last_slot + 1 : T) + 2;
     Tmp<uint4> table(mem, table_len, s);
     if (!table.ok()) return cudaErrorMemoryAllocation;
     if ((e = cudaMemsetAsync(table.ptr, 0, table_len * sizeof(uint4), s)) != cudaSuccess) return e;
     if (n_keys > 0) {
-        MC_LAUNCH("tab_emit", s, k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t, kt_pre.ptr,
-                                                   ktiles, table.ptr, (unsigned int*)(ctr.ptr + 1)));
+        MC_LAUNCH("tab_emit", s,
+                  k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t,
+                                                             kt_pre.ptr, ktiles, table.ptr,
+                                                             (unsigned int*)(ctr.ptr + 1)));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     unsigned long long host_ctr[2] = {0, 0};
@@ -625,7 +716,6 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     out->table_len = table_len;
     out->table_bytes = table_len * sizeof(uint4);
     out->locs = locs.release();
-    out->kept_pairs = kpairs.release();
     out->table = table.release();
     return cudaSuccess;
 }

@@ -21,6 +21,8 @@
 // queued and processed by a second kernel whose warps use a larger table in
 // global scratch memory.  Both paths run the same code, so the result does
 // not depend on the path.
+#include <algorithm>
+
 #include "mc_internal.h"
 #include "mc_sketch.cuh"
 
@@ -28,11 +30,13 @@ namespace mc {
 
 namespace {
 
-constexpr int CLS_WARPS = 8;                 // warps per CTA
+constexpr int CLS_WARPS = 4;                 // warps per CTA (score and large paths)
+constexpr int LK_WARPS = 8;                  // warps per CTA (lookup path)
 constexpr int WIN_A = 8;                     // windows per query on the shared-memory path
 constexpr uint32_t KB_SLOTS = 1u << 16;      // large-path histogram slots per warp
 constexpr uint32_t LIST_B = MC_MAX_QUERY_WINDOWS * MAX_S;
 constexpr int B_WARPS_PER_SM = 2;
+constexpr int SK_NW = 2;  // windows sketched together
 
 struct Cand {
     uint32_t score, t, j0, j1;
@@ -46,46 +50,20 @@ __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
     return a.j0 < b.j0;
 }
 
-__device__ __forceinline__ Cand shfl_cand(const Cand& c, int lane_mask) {
-    Cand o;
-    o.score = __shfl_xor_sync(FULL_MASK, c.score, lane_mask);
-    o.t = __shfl_xor_sync(FULL_MASK, c.t, lane_mask);
-    o.j0 = __shfl_xor_sync(FULL_MASK, c.j0, lane_mask);
-    o.j1 = __shfl_xor_sync(FULL_MASK, c.j1, lane_mask);
-    return o;
-}
-
-// Feature table lookup: ordered linear probing from the home slot; entries
-// are in ascending h2 order along the table, so the probe stops at an empty
-// slot or a larger key.  Returns the bucket size (0 if absent).
-__device__ __forceinline__ uint32_t table_find(const uint4* __restrict__ tab, uint32_t log_t, uint32_t max_probe,
-                                               uint32_t hk, uint64_t& off) {
-    uint64_t pos = log_t >= 32 ? hk : (hk >> (32 - log_t));
-    for (uint32_t d = 0; d <= max_probe; ++d) {
-        uint4 e = __ldg(tab + pos + d);
-        if (e.y == 0 || e.x > hk) return 0;
-        if (e.x == hk) {
-            off = (uint64_t)e.z | ((uint64_t)e.w << 32);
-            return e.y;
-        }
-    }
-    return 0;
-}
-
 __device__ __forceinline__ uint32_t loc_slot(uint64_t loc, uint32_t mask) {
     uint64_t h = (loc ^ (loc >> 29)) * 0x9E3779B97F4A7C15ull;
     return (uint32_t)(h >> 32) & mask;
 }
 
-// Histogram insert (count + 1).  Returns false if the table is full.
+// Histogram insert (count + 1).  `fresh_slot` receives the slot if the
+// location was new, else stays -1.  Returns false if the table is full.
 __device__ __forceinline__ bool hist_insert(uint64_t* keys, uint32_t* cnts, uint32_t mask, uint64_t loc,
-                                            bool& fresh) {
+                                            int& fresh_slot) {
     uint32_t slot = loc_slot(loc, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         uint64_t k = *(volatile uint64_t*)(keys + slot);
         if (k == loc) {
             atomicAdd(cnts + slot, 1u);
-            fresh = false;
             return true;
         }
         if (k == EMPTY_LOC) {
@@ -93,13 +71,12 @@ __device__ __forceinline__ bool hist_insert(uint64_t* keys, uint32_t* cnts, uint
                 atomicCAS((unsigned long long*)(keys + slot), (unsigned long long)EMPTY_LOC, (unsigned long long)loc);
             if (prev == EMPTY_LOC || prev == loc) {
                 atomicAdd(cnts + slot, 1u);
-                fresh = prev == EMPTY_LOC;
+                if (prev == EMPTY_LOC) fresh_slot = (int)slot;
                 return true;
             }
         }
         slot = (slot + 1) & mask;
     }
-    fresh = false;
     return false;
 }
 
@@ -115,70 +92,6 @@ __device__ __forceinline__ uint32_t hist_count(const uint64_t* keys, const uint3
     return 0;
 }
 
-// Per-lane top-m list with at most one candidate per target.
-struct TopList {
-    Cand c[MAX_M];
-    int n;
-    __device__ __forceinline__ void init() {
-        n = 0;
-#pragma unroll
-        for (int i = 0; i < MAX_M; ++i) c[i] = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
-    }
-    __device__ __forceinline__ void remove_at(int idx) {
-#pragma unroll
-        for (int i = 0; i < MAX_M - 1; ++i)
-            if (i >= idx) c[i] = c[i + 1];
-        c[MAX_M - 1] = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
-        --n;
-    }
-    __device__ __forceinline__ void insert(const Cand& x, int m) {
-        if (n == m) {
-            Cand last = c[0];
-#pragma unroll
-            for (int i = 0; i < MAX_M; ++i)
-                if (i == m - 1) last = c[i];
-            if (!better(x, last)) return;
-        }
-        int same = -1;
-#pragma unroll
-        for (int i = 0; i < MAX_M; ++i)
-            if (i < n && c[i].t == x.t) same = i;
-        if (same >= 0) {
-            Cand old = c[0];
-#pragma unroll
-            for (int i = 0; i < MAX_M; ++i)
-                if (i == same) old = c[i];
-            if (!better(x, old)) return;
-            remove_at(same);
-        }
-        if (n == m) {  // drop the last
-#pragma unroll
-            for (int i = 0; i < MAX_M; ++i)
-                if (i == m - 1) c[i] = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
-            --n;
-        }
-#pragma unroll
-        for (int i = 0; i < MAX_M; ++i)
-            if (i == n) c[i] = x;
-        ++n;
-#pragma unroll
-        for (int i = MAX_M - 1; i >= 1; --i) {
-            if (i < n && better(c[i], c[i - 1])) {
-                Cand t = c[i];
-                c[i] = c[i - 1];
-                c[i - 1] = t;
-            }
-        }
-    }
-    __device__ __forceinline__ void remove_target(uint32_t t) {
-        int idx = -1;
-#pragma unroll
-        for (int i = 0; i < MAX_M; ++i)
-            if (i < n && c[i].t == t) idx = i;
-        if (idx >= 0) remove_at(idx);
-    }
-};
-
 __device__ __forceinline__ uint32_t lca2(const ClassifyDb& db, uint32_t a, uint32_t b) {
     if (a >= db.n_taxa || b >= db.n_taxa) return NO_TAXON;
     uint32_t da = db.depth[a], dbb = db.depth[b];
@@ -192,15 +105,57 @@ __device__ __forceinline__ uint32_t lca2(const ClassifyDb& db, uint32_t a, uint3
 
 enum { Q_DONE = 0, Q_ESCALATE = 1, Q_TOO_LARGE = 2 };
 
+constexpr uint32_t MAX_MATES = MC_MAX_QUERY_MATES;  // mates per query (lane i holds mate i)
+constexpr int LB = 4;               // feature-table probes in flight per lane
+constexpr int GB = 8;               // bucket loads in flight per lane
+
+// Per-warp working memory (shared memory on the main path, global scratch
+// on the large path).
 struct Scratch {
-    uint64_t* keys;
-    uint32_t* cnts;
-    uint32_t kcap;  // power of two
-    uint64_t* l_off;
+    uint64_t* keys;   // histogram keys (location), kcap
+    uint32_t* cnts;   // histogram counts, kcap
+    uint32_t* score;  // sliding-window scores of the dense entries, kcap
+    uint32_t* dense;  // slots of the distinct locations, kcap
+    uint32_t kcap;    // power of two
+    uint32_t* feat;   // features of all windows, list_cap
+    uint64_t* l_off;  // found buckets: offset, size, exclusive prefix (list_cap + 1)
     uint32_t* l_cnt;
-    uint32_t* l_pre;  // list_cap + 1
+    uint32_t* l_pre;
     uint32_t list_cap;
+    uint32_t* cand;   // sketch selection scratch, SK_NW * 32
+    uint8_t* buf;     // the query's bases
+    uint32_t buf_cap;
     uint32_t win_cap;
+};
+
+__host__ __device__ constexpr size_t scratch_bytes(uint32_t kcap, uint32_t list_cap, uint32_t buf_cap) {
+    return (size_t)kcap * 20 + (size_t)list_cap * 20 + 16 + 4 * 32 * SK_NW + buf_cap;
+}
+
+// Carves a Scratch out of `base` (16-byte aligned).
+__device__ __forceinline__ Scratch carve(unsigned char* base, uint32_t kcap, uint32_t list_cap, uint32_t buf_cap,
+                                         uint32_t win_cap) {
+    Scratch S;
+    S.keys = reinterpret_cast<uint64_t*>(base);
+    S.l_off = reinterpret_cast<uint64_t*>(base + (size_t)kcap * 8);
+    uint32_t* u = reinterpret_cast<uint32_t*>(base + (size_t)kcap * 8 + (size_t)list_cap * 8);
+    S.cnts = u;
+    S.score = u + kcap;
+    S.dense = S.score + kcap;
+    S.feat = S.dense + kcap;
+    S.l_cnt = S.feat + list_cap;
+    S.l_pre = S.l_cnt + list_cap;
+    S.cand = S.l_pre + list_cap + 4;
+    S.buf = reinterpret_cast<uint8_t*>(S.cand + 32 * SK_NW);
+    S.kcap = kcap;
+    S.list_cap = list_cap;
+    S.buf_cap = buf_cap;
+    S.win_cap = win_cap;
+    return S;
+}
+
+struct Counters {
+    unsigned long long features = 0, locations = 0, distinct = 0, found = 0, sectors = 0;
 };
 
 // Lane i (< m) writes candidate slot i; `mine` is the lane's candidate.
@@ -225,60 +180,163 @@ __device__ __forceinline__ void write_unclassified(const ClassifyQuery& Q, uint3
     write_result(Q, q, NO_TAXON, 0, 0xFFFFFFFFu, Cand{0, 0xFFFFFFFFu, 0, 0});
 }
 
-template <int R>
-__device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
-                             unsigned long long (&ctr)[5]) {
+__device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Query steps 1-4 of Section 4.2 on one warp (sketch every window of every
+// mate, look every feature up): the found buckets are written as a list of
+// (offset, size), to the working memory (l_off / l_cnt) or, packed as
+// offset << 16 | size, to `glist`.  Also returns the sliding-window size.
+// Returns Q_DONE, Q_ESCALATE (needs the large path) or Q_TOO_LARGE.
+// Also returns the number of features and the 32-byte sectors of the found
+// buckets (warp totals) for the counters.
+template <int R, bool TO_GLOBAL>
+__device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
+                                            uint64_t* __restrict__ glist, uint32_t& n_list_out, uint32_t& sws_out,
+                                            uint32_t& n_feat_out, uint32_t& n_sect_out) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     const SketchParams& p = db.sp;
     const uint32_t m0 = Q.qoffs[q], m1 = Q.qoffs[q + 1];
+    if (m1 < m0 || m1 - m0 > MAX_MATES) return Q_TOO_LARGE;
+    const uint32_t nm = m1 - m0;
 
-    uint64_t span_sum = 0, n_win = 0;
-    for (uint32_t i = m0; i < m1; ++i) {
-        uint64_t L = Q.offs[i + 1] - Q.offs[i];
-        span_sum += L;
-        n_win += num_windows(L, p.k, p.stride);
-    }
+    // mates: lane i holds mate i's offset, length and window count
+    const uint64_t o = lane <= nm ? Q.offs[m0 + lane] : 0;
+    const uint64_t o_next = __shfl_down_sync(FULL_MASK, o, 1);
+    const uint64_t L = (lane < nm && o_next > o) ? o_next - o : 0;
+    const uint64_t nw = lane < nm ? num_windows(L, p.k, p.stride) : 0;
+    const uint64_t span_sum = warp_sum_u64(L);
+    const uint64_t n_win = warp_sum_u64(nw);
     if (n_win > MC_MAX_QUERY_WINDOWS) return Q_TOO_LARGE;
-    if (n_win > S.win_cap) return Q_ESCALATE;
+    if (n_win > S.win_cap || span_sum > S.buf_cap) return Q_ESCALATE;
+    uint64_t boff = L;  // exclusive prefix of mate lengths
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        uint64_t x = __shfl_up_sync(FULL_MASK, boff, d);
+        if ((int)lane >= d) boff += x;
+    }
+    boff -= L;
 
-    // 1. sketch + lookup: list of (bucket offset, size) of found features
+    // 1a. stage the query's bases in working memory (all loads in flight)
+    for (uint32_t i = 0; i < nm; ++i) {
+        const uint64_t oi = __shfl_sync(FULL_MASK, o, i);
+        const uint64_t Li = __shfl_sync(FULL_MASK, L, i);
+        const uint64_t bi = __shfl_sync(FULL_MASK, boff, i);
+        const uint8_t* src = Q.seq + oi;
+#pragma unroll 4
+        for (uint64_t b = lane; b < Li; b += 32) S.buf[bi + b] = __ldg(src + b);
+    }
+    __syncwarp();
+
+    // 1b. sketch every window of every mate (Section 3.2: reads are windowed
+    // like the targets), SK_NW windows at a time; feat[] gets the features
+    // in window order
+    uint32_t F = 0;
+    {
+        uint32_t mi = 0;          // mate of the next window
+        uint64_t jn = 0;          // its window index
+        uint64_t nw_mi = __shfl_sync(FULL_MASK, nw, 0);
+        for (uint64_t done = 0; done < n_win; done += SK_NW) {
+            const uint8_t* sq[SK_NW];
+            uint64_t Ls[SK_NW], wss[SK_NW];
+            bool act[SK_NW];
+#pragma unroll
+            for (int i = 0; i < SK_NW; ++i) {
+                act[i] = done + i < n_win;
+                while (act[i] && jn >= nw_mi) {  // skip to the mate of this window
+                    ++mi;
+                    jn = 0;
+                    nw_mi = __shfl_sync(FULL_MASK, nw, mi & 31);
+                }
+                sq[i] = S.buf + __shfl_sync(FULL_MASK, boff, mi & 31);
+                Ls[i] = act[i] ? __shfl_sync(FULL_MASK, L, mi & 31) : 0;
+                wss[i] = jn * p.stride;
+                if (act[i]) ++jn;
+            }
+            uint32_t f[SK_NW], cnt[SK_NW];
+            warp_sketch_multi<R, SK_NW, false>(sq, Ls, wss, act, p, S.cand, f, cnt);
+#pragma unroll
+            for (int i = 0; i < SK_NW; ++i) {
+                if (lane < cnt[i]) S.feat[F + lane] = f[i];
+                F += cnt[i];
+            }
+        }
+    }
+    __syncwarp();
+
+    // 1c. feature table probes, LB per lane in flight
     uint32_t n_list = 0;
-    uint64_t n_feat = 0, n_sect = 0;
-    for (uint32_t i = m0; i < m1; ++i) {
-        uint64_t L = Q.offs[i + 1] - Q.offs[i];
-        uint64_t nw = num_windows(L, p.k, p.stride);
-        const uint8_t* s = Q.seq + Q.offs[i];
-        for (uint64_t j = 0; j < nw; ++j) {
-            uint32_t f;
-            uint32_t cnt = warp_sketch<R>(s, L, j * p.stride, p, f);
-            n_feat += cnt;
-            uint64_t off = 0;
+    unsigned long long n_sect = 0;
+    for (uint32_t base = 0; base < F; base += 32 * LB) {
+        uint32_t hk[LB];
+        uint64_t pos[LB];
+        uint4 e[LB];
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const uint32_t idx = base + b * 32 + lane;
+            hk[b] = idx < F ? hash_h2(S.feat[idx]) : 0u;
+            pos[b] = db.log_t >= 32 ? hk[b] : (hk[b] >> (32 - db.log_t));
+            e[b] = idx < F ? __ldg(db.table + pos[b]) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int b = 0; b < LB; ++b) {
+            const uint32_t idx = base + b * 32 + lane;
             uint32_t c = 0;
-            if (lane < cnt) c = table_find(db.table, db.log_t, db.max_probe, hash_h2(f), off);
-            uint32_t found = __ballot_sync(FULL_MASK, c > 0);
+            uint64_t off = 0;
+            if (idx < F) {
+                uint4 x = e[b];
+                for (uint32_t d = 1; x.y != 0 && x.x < hk[b] && d <= db.max_probe; ++d) x = __ldg(db.table + pos[b] + d);
+                if (x.y != 0 && x.x == hk[b]) {
+                    c = x.y;
+                    off = (uint64_t)x.z | ((uint64_t)x.w << 32);
+                }
+            }
+            const uint32_t found = __ballot_sync(FULL_MASK, c > 0);
             if (c > 0) {
-                uint32_t idx = n_list + __popc(found & lt);
-                S.l_off[idx] = off;
-                S.l_cnt[idx] = c;
-                // 32-byte sectors the bucket occupies (for the roofline counters)
+                const uint32_t li = n_list + __popc(found & lt);
+                if (TO_GLOBAL) {
+                    glist[li] = (off << 16) | c;
+                } else {
+                    S.l_off[li] = off;
+                    S.l_cnt[li] = c;
+                }
                 n_sect += ((off * 8 + (uint64_t)c * 8 - 1) >> 5) - ((off * 8) >> 5) + 1;
             }
             n_list += __popc(found);
         }
     }
     __syncwarp();
+    n_feat_out = F;
+    n_sect_out = (uint32_t)warp_sum_u64(n_sect);
+    const uint64_t span = (nm <= 1) ? span_sum : (span_sum > Q.max_insert ? span_sum : (uint64_t)Q.max_insert);
+    sws_out = span >= p.k ? (uint32_t)((span - p.k + p.stride - 1) / p.stride + 1) : 0;
+    n_list_out = n_list;
+    return Q_DONE;
+}
+
+// Query steps 5-8 of Section 4.2 on one warp, from the bucket list in
+// working memory: gather, window count statistic, sliding-window scores,
+// top m, label.  Writes the outputs and returns Q_DONE, or Q_ESCALATE if the
+// histogram does not fit the working memory.
+__device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
+                                           uint32_t n_list, uint32_t sws, Counters& ctr) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
 
     // 2. exclusive prefix of bucket sizes; H = locations to gather
     uint32_t H = 0;
     for (uint32_t base = 0; base < n_list; base += 32) {
-        uint32_t idx = base + lane;
-        uint32_t c = idx < n_list ? S.l_cnt[idx] : 0;
+        const uint32_t idx = base + lane;
+        const uint32_t c = idx < n_list ? S.l_cnt[idx] : 0;
         uint32_t inc = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            uint32_t o = __shfl_up_sync(FULL_MASK, inc, d);
-            if ((int)lane >= d) inc += o;
+            uint32_t x = __shfl_up_sync(FULL_MASK, inc, d);
+            if ((int)lane >= d) inc += x;
         }
         if (idx < n_list) S.l_pre[idx] = H + inc - c;
         H += __shfl_sync(FULL_MASK, inc, 31);
@@ -293,78 +351,105 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
     }
     __syncwarp();
 
-    // gather into the histogram
+    // 3. gather the buckets into the hit histogram (window count statistic,
+    // Section 3.2), GB loads per lane in flight; the slots of new locations
+    // are appended to a dense list
     const uint32_t limit = kq - kq / 8;
-    uint32_t distinct = 0;
-    uint32_t b = 0;
-    for (uint32_t base = 0; base < H; base += 32) {
-        uint32_t x = base + lane;
-        bool fresh = false, ok = true;
-        if (x < H) {
-            while (S.l_pre[b + 1] <= x) ++b;
-            uint64_t loc = db.locs[S.l_off[b] + (x - S.l_pre[b])];
-            ok = hist_insert(S.keys, S.cnts, mask, loc, fresh);
-        }
-        distinct += __popc(__ballot_sync(FULL_MASK, fresh));
-        if (__any_sync(FULL_MASK, !ok) || distinct > limit) return Q_ESCALATE;
-    }
-    __syncwarp();
-    ctr[0] += n_feat;
-    ctr[1] += H;
-    ctr[2] += distinct;
-    ctr[3] += n_list;
-    ctr[4] += n_sect;  // per lane; summed over the warp at flush
-
-    // 3. sliding-window scores (Section 4.6)
-    uint64_t span = (m1 - m0 <= 1) ? span_sum : (span_sum > Q.max_insert ? span_sum : (uint64_t)Q.max_insert);
-    uint32_t sws = span >= p.k ? (uint32_t)((span - p.k + p.stride - 1) / p.stride + 1) : 0;
-    TopList tl;
-    tl.init();
-    const int m = (int)Q.m;
-    for (uint32_t s = lane; s < kq; s += 32) {
-        uint64_t loc = S.keys[s];
-        if (loc == EMPTY_LOC) continue;
-        Cand c;
-        c.score = S.cnts[s];
-        c.t = (uint32_t)(loc >> 32);
-        c.j0 = (uint32_t)loc;
-        c.j1 = c.j0;
-        for (uint32_t d = 1; d < sws; ++d) {
-            uint32_t n = hist_count(S.keys, S.cnts, mask, loc + d);
-            if (n) {
-                c.score += n;
-                c.j1 = c.j0 + d;
+    uint32_t D = 0;
+    uint32_t bkt = 0;
+    for (uint32_t base = 0; base < H; base += 32 * GB) {
+        uint64_t v[GB];
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            const uint32_t x = base + g * 32 + lane;
+            v[g] = EMPTY_LOC;
+            if (x < H) {
+                while (S.l_pre[bkt + 1] <= x) ++bkt;
+                v[g] = __ldg(db.locs + S.l_off[bkt] + (x - S.l_pre[bkt]));
             }
         }
-        tl.insert(c, m);
+        bool ok = true;
+#pragma unroll
+        for (int g = 0; g < GB; ++g) {
+            int slot = -1;
+            if (v[g] != EMPTY_LOC) ok &= hist_insert(S.keys, S.cnts, mask, v[g], slot);
+            const uint32_t fresh = __ballot_sync(FULL_MASK, slot >= 0);
+            if (slot >= 0) S.dense[D + __popc(fresh & lt)] = (uint32_t)slot;
+            D += __popc(fresh);
+        }
+        if (__any_sync(FULL_MASK, !ok) || D > limit) return Q_ESCALATE;
     }
+    __syncwarp();
+    ctr.locations += H;
+    ctr.distinct += D;
 
-    // 4. warp merge of the lane lists: m rounds of arg-max, removing the
-    // winner's target from every list.  Round r's winner is kept by lane r;
-    // the close candidates' taxa are folded into the label as they come.
+    // 4. sliding-window scores (Section 4.6): score(t, j0) = sum of the
+    // counts of (t, j0 .. j0+sws-1), for the distinct locations
+    for (uint32_t i = lane; i < D; i += 32) {
+        const uint32_t slot = S.dense[i];
+        const uint64_t key = S.keys[slot];
+        uint32_t sc = S.cnts[slot];
+        const uint32_t room = 0xFFFFFFFFu - (uint32_t)key;  // windows left before the id wraps
+        for (uint32_t d = 1; d < sws && d <= room; ++d) sc += hist_count(S.keys, S.cnts, mask, key + d);
+        S.score[i] = sc;
+    }
+    __syncwarp();
+
+    // 5. top m with one candidate per target (Section 3.2 / 4.6): m rounds
+    // of warp arg-max, excluding the targets already chosen; the label is
+    // folded as the candidates come (hit threshold of Section 5.6, LCA of
+    // the close candidates of Section 3.2)
+    const int m = (int)Q.m;
     Cand mine = Cand{0, 0xFFFFFFFFu, 0, 0};
     uint32_t label = NO_TAXON, hits = 0, top = 0xFFFFFFFFu;
     uint64_t bar = 0;
+    uint32_t won[MAX_M];
+#pragma unroll
+    for (int i = 0; i < MAX_M; ++i) won[i] = 0xFFFFFFFFu;
 #pragma unroll
     for (int r = 0; r < MAX_M; ++r) {
         if (r >= m) break;
-        Cand h = tl.n > 0 ? tl.c[0] : Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
+        Cand best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
+        for (uint32_t i = lane; i < D; i += 32) {
+            const uint64_t key = S.keys[S.dense[i]];
+            const uint32_t t = (uint32_t)(key >> 32);
+            bool excl = false;
+#pragma unroll
+            for (int x = 0; x < MAX_M; ++x)
+                if (x < r && won[x] == t) excl = true;
+            const Cand c = Cand{S.score[i], t, (uint32_t)key, 0};
+            if (!excl && better(c, best)) best = c;
+        }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
-            Cand x = shfl_cand(h, o);
-            if (better(x, h)) h = x;
+            Cand x;
+            x.score = __shfl_xor_sync(FULL_MASK, best.score, o);
+            x.t = __shfl_xor_sync(FULL_MASK, best.t, o);
+            x.j0 = __shfl_xor_sync(FULL_MASK, best.j0, o);
+            if (better(x, best)) best = x;
         }
-        if (h.score == 0) break;
-        if ((int)lane == r) mine = h;
-        tl.remove_target(h.t);
-        // 5. label (Section 3.2; hit threshold of Section 5.6)
+        if (best.score == 0) break;
+        won[r] = best.t;
+        if (Q.cands) {
+            // last window of the range present in the histogram
+            uint32_t j1 = best.j0;
+            for (uint32_t i = lane; i < D; i += 32) {
+                const uint64_t key = S.keys[S.dense[i]];
+                const uint32_t j = (uint32_t)key;
+                if ((uint32_t)(key >> 32) == best.t && j >= best.j0 && (uint64_t)j < (uint64_t)best.j0 + sws && j > j1)
+                    j1 = j;
+            }
+            j1 = __reduce_max_sync(FULL_MASK, j1);
+            best.j1 = j1;
+        }
+        if ((int)lane == r) mine = best;
         if (r == 0) {
-            hits = h.score;
-            top = h.t;
+            hits = best.score;
+            top = best.t;
             bar = (uint64_t)(100 - Q.band) * hits;
             if (hits >= Q.hits_min) label = top < db.n_targets ? db.taxon_of_target[top] : NO_TAXON;
-        } else if (hits >= Q.hits_min && 100ull * h.score >= bar) {
-            uint32_t tx = h.t < db.n_targets ? db.taxon_of_target[h.t] : NO_TAXON;
+        } else if (hits >= Q.hits_min && 100ull * best.score >= bar) {
+            const uint32_t tx = best.t < db.n_targets ? db.taxon_of_target[best.t] : NO_TAXON;
             label = lca2(db, label, tx);
         }
     }
@@ -372,50 +457,115 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
     return Q_DONE;
 }
 
+// Whole query on one warp with the bucket list in working memory.
+template <int R>
+__device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
+                                             Counters& ctr) {
+    uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
+    int r = query_lookup<R, false>(db, Q, q, S, nullptr, n_list, sws, n_feat, n_sect);
+    if (r != Q_DONE) return r;
+    r = query_score(db, Q, q, S, n_list, sws, ctr);
+    if (r == Q_DONE) {
+        ctr.features += n_feat;
+        ctr.found += n_list;
+        ctr.sectors += n_sect;
+    }
+    return r;
+}
+
 // counters: [0] features looked up, [1] locations gathered, [2] distinct
 // locations, [3] queries on the large path, [4] features found, [5] 32-byte
 // sectors of the gathered buckets.
-__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, unsigned long long (&ctr)[5]) {
-    unsigned long long sect = ctr[4];
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) sect += __shfl_xor_sync(FULL_MASK, sect, o);
+__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, const Counters& c) {
+    const unsigned long long sect = c.sectors;
     if (Q.counters && lane_id() == 0) {
-        atomicAdd(Q.counters + 0, ctr[0]);
-        atomicAdd(Q.counters + 1, ctr[1]);
-        atomicAdd(Q.counters + 2, ctr[2]);
-        atomicAdd(Q.counters + 4, ctr[3]);
+        atomicAdd(Q.counters + 0, c.features);
+        atomicAdd(Q.counters + 1, c.locations);
+        atomicAdd(Q.counters + 2, c.distinct);
+        atomicAdd(Q.counters + 4, c.found);
         atomicAdd(Q.counters + 5, sect);
     }
 }
 
-// Shared-memory path: one warp per query, KA histogram slots per warp.
-template <int R, int KA>
-__global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_smem(ClassifyDb db, ClassifyQuery Q, uint32_t list_cap,
+constexpr uint32_t BUF_A = 1024;   // bases per query on the shared-memory path
+constexpr uint32_t BUF_B = 16384;  // bases per query on the large path
+
+constexpr uint32_t ESCALATED = 0xFFFFFFFFu;
+
+// Main path, part 1 (sketch + lookup): one warp per query of the chunk
+// [q0, q0 + nq), shared memory for the query's bases and features only, so
+// many warps fit on an SM.  Writes each query's bucket list to
+// glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
+// meta; queries that need the large path are queued.
+template <int R>
+__global__ void __launch_bounds__(LK_WARPS * 32) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+                                                                  uint32_t nq, uint32_t list_cap,
+                                                                  uint64_t* __restrict__ glist,
+                                                                  uint4* __restrict__ meta,
                                                                   uint32_t* __restrict__ ovf_list,
                                                                   uint32_t* __restrict__ ovf_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
-    const size_t per_warp = (size_t)KA * 12 + (size_t)list_cap * 12 + (list_cap + 1) * 4 + 16;
-    unsigned char* base = smem + w * ((per_warp + 15) & ~(size_t)15);
-    Scratch S;
-    S.keys = reinterpret_cast<uint64_t*>(base);
-    S.l_off = reinterpret_cast<uint64_t*>(base + (size_t)KA * 8);
-    S.cnts = reinterpret_cast<uint32_t*>(base + (size_t)KA * 8 + (size_t)list_cap * 8);
-    S.l_cnt = S.cnts + KA;
-    S.l_pre = S.l_cnt + list_cap;
-    S.kcap = KA;
-    S.list_cap = list_cap;
-    S.win_cap = WIN_A;
-    unsigned long long ctr[5] = {0, 0, 0, 0, 0};
+    const size_t per_warp = (scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15;
+    const Scratch S = carve(smem + w * per_warp, 0, list_cap, BUF_A, WIN_A);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t q = gw; q < Q.n_q; q += nw) {
-        int r = process_query<R>(db, Q, q, S, ctr);
+    const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < nq; i += nwarp) {
+        const uint32_t q = q0 + i;
+        uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
+        int r = query_lookup<R, true>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
         if (r == Q_ESCALATE) {
-            if (lane_id() == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
+            if (lane_id() == 0) {
+                ovf_list[atomicAdd(ovf_n, 1u)] = q;
+                meta[i] = make_uint4(ESCALATED, 0, 0, 0);
+            }
         } else if (r == Q_TOO_LARGE) {
             write_unclassified(Q, q);
-            if (lane_id() == 0) atomicMax(Q.status, DEV_ERR_CAPACITY);
+            if (lane_id() == 0) {
+                atomicMax(Q.status, DEV_ERR_CAPACITY);
+                meta[i] = make_uint4(ESCALATED, 0, 0, 0);
+            }
+        } else if (lane_id() == 0) {
+            meta[i] = make_uint4(n_list, sws, n_feat, n_sect);
+        }
+        __syncwarp();
+    }
+}
+
+// Main path, part 2 (gather + score + label): one warp per query of the
+// chunk, KA histogram slots per warp in shared memory.
+template <int KA>
+__global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+                                                                     uint32_t nq, uint32_t list_cap,
+                                                                     const uint64_t* __restrict__ glist,
+                                                                     const uint4* __restrict__ meta,
+                                                                     uint32_t* __restrict__ ovf_list,
+                                                                     uint32_t* __restrict__ ovf_n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const size_t per_warp = (scratch_bytes(KA, list_cap, 0) + 15) & ~(size_t)15;
+    const Scratch S = carve(smem + w * per_warp, KA, list_cap, 0, WIN_A);
+    Counters ctr;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < nq; i += nwarp) {
+        const uint4 mt = meta[i];
+        if (mt.x == ESCALATED) continue;
+        const uint64_t* src = glist + (uint64_t)i * list_cap;
+        for (uint32_t j = lane; j < mt.x; j += 32) {
+            const uint64_t e = __ldg(src + j);
+            S.l_off[j] = e >> 16;
+            S.l_cnt[j] = (uint32_t)(e & 0xFFFFu);
+        }
+        __syncwarp();
+        const uint32_t q = q0 + i;
+        if (query_score(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
+            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
+        } else {
+            ctr.features += mt.z;
+            ctr.found += mt.x;
+            ctr.sectors += mt.w;
         }
         __syncwarp();
     }
@@ -423,25 +573,17 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_smem(ClassifyDb 
 }
 
 // Large path: queries queued by the shared-memory path, one warp each, with
-// a KB_SLOTS histogram in global scratch memory.
+// working memory in global scratch.
 template <int R>
-__global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_large(ClassifyDb db, ClassifyQuery Q,
+__global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb db, ClassifyQuery Q,
                                                                    const uint32_t* __restrict__ ovf_list,
                                                                    const uint32_t* __restrict__ ovf_n,
-                                                                   uint32_t* __restrict__ work, uint64_t* gkeys,
-                                                                   uint32_t* gcnts, uint64_t* gloff, uint32_t* glcnt,
-                                                                   uint32_t* glpre) {
+                                                                   uint32_t* __restrict__ work,
+                                                                   unsigned char* __restrict__ scratch,
+                                                                   size_t per_warp) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    Scratch S;
-    S.keys = gkeys + (uint64_t)gw * KB_SLOTS;
-    S.cnts = gcnts + (uint64_t)gw * KB_SLOTS;
-    S.kcap = KB_SLOTS;
-    S.l_off = gloff + (uint64_t)gw * LIST_B;
-    S.l_cnt = glcnt + (uint64_t)gw * LIST_B;
-    S.l_pre = glpre + (uint64_t)gw * (LIST_B + 1);
-    S.list_cap = LIST_B;
-    S.win_cap = MC_MAX_QUERY_WINDOWS;
-    unsigned long long ctr[5] = {0, 0, 0, 0, 0};
+    const Scratch S = carve(scratch + gw * per_warp, KB_SLOTS, LIST_B, BUF_B, MC_MAX_QUERY_WINDOWS);
+    Counters ctr;
     const uint32_t n = *ovf_n;
     unsigned long long n_large = 0;
     for (;;) {
@@ -449,7 +591,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_large(ClassifyDb
         if (lane_id() == 0) i = atomicAdd(work, 1u);
         i = __shfl_sync(FULL_MASK, i, 0);
         if (i >= n) break;
-        uint32_t q = ovf_list[i];
+        const uint32_t q = ovf_list[i];
         ++n_large;
         int r = process_query<R>(db, Q, q, S, ctr);
         if (r != Q_DONE) {
@@ -463,45 +605,60 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 1) k_classify_large(ClassifyDb
 }
 
 constexpr int KA_DEFAULT = 512;
+constexpr uint32_t CHUNK = 1u << 20;  // queries per lookup/score round
 
 template <int R>
 cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
     cudaError_t e;
     const uint32_t list_cap = WIN_A * db.sp.s;
-    const size_t per_warp = (size_t)KA_DEFAULT * 12 + (size_t)list_cap * 12 + (list_cap + 1) * 4 + 16;
-    const size_t smem = CLS_WARPS * ((per_warp + 15) & ~(size_t)15);
-    auto ka = k_classify_smem<R, KA_DEFAULT>;
-    if ((e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-        return e;
-    int dev = 0, sms = NUM_SMS_HINT, occ = 1;
+    int dev = 0, sms = NUM_SMS_HINT;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ka, CLS_WARPS * 32, smem)) != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
 
-    // scratch: overflow queue + counters
+    const size_t smem_l = LK_WARPS * ((scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15);
+    const size_t smem_s = CLS_WARPS * ((scratch_bytes(KA_DEFAULT, list_cap, 0) + 15) & ~(size_t)15);
+    auto kl = k_classify_lookup<R>;
+    auto ks = k_classify_score<KA_DEFAULT>;
+    if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s)) != cudaSuccess)
+        return e;
+    int occ_l = 1, occ_s = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, kl, LK_WARPS * 32, smem_l)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, CLS_WARPS * 32, smem_s)) != cudaSuccess) return e;
+    occ_l = std::max(occ_l, 1);
+    occ_s = std::max(occ_s, 1);
+
+    // scratch: overflow queue + counters, bucket lists and metadata of a chunk
+    const uint32_t chunk = std::min<uint32_t>(Q.n_q, CHUNK);
     Tmp<uint32_t> ovf(mem, (size_t)Q.n_q + 4, s);
-    if (!ovf.ok()) return cudaErrorMemoryAllocation;
+    Tmp<uint64_t> glist(mem, (size_t)chunk * list_cap, s);
+    Tmp<uint4> meta(mem, chunk, s);
+    if (!ovf.ok() || !glist.ok() || !meta.ok()) return cudaErrorMemoryAllocation;
     uint32_t* ovf_n = ovf.ptr + Q.n_q;
     uint32_t* work = ovf_n + 1;
     if ((e = cudaMemsetAsync(ovf_n, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
 
-    uint64_t blocks = ((uint64_t)Q.n_q + CLS_WARPS - 1) / CLS_WARPS;
-    uint64_t cap_blocks = (uint64_t)sms * occ * 8;
-    uint32_t g = (uint32_t)(blocks < cap_blocks ? blocks : cap_blocks);
-    if (g == 0) return cudaSuccess;
-    MC_LAUNCH("classify_smem", s, ka<<<g, CLS_WARPS * 32, smem, s>>>(db, Q, list_cap, ovf.ptr, ovf_n));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (uint32_t q0 = 0; q0 < Q.n_q; q0 += chunk) {
+        const uint32_t nq = std::min(chunk, Q.n_q - q0);
+        const uint32_t gl = (uint32_t)std::min<uint64_t>(((uint64_t)nq + LK_WARPS - 1) / LK_WARPS, (uint64_t)sms * occ_l);
+        const uint32_t gs = (uint32_t)std::min<uint64_t>(((uint64_t)nq + CLS_WARPS - 1) / CLS_WARPS, (uint64_t)sms * occ_s);
+        MC_LAUNCH("classify_lookup", s,
+                  kl<<<gl, LK_WARPS * 32, smem_l, s>>>(db, Q, q0, nq, list_cap, glist.ptr, meta.ptr, ovf.ptr, ovf_n));
+        MC_LAUNCH("classify_score", s,
+                  ks<<<gs, CLS_WARPS * 32, smem_s, s>>>(db, Q, q0, nq, list_cap, glist.ptr, meta.ptr, ovf.ptr, ovf_n));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
 
-    // large path (persistent warps, exits at once if nothing was queued)
-    const uint32_t b_blocks = (uint32_t)sms * B_WARPS_PER_SM / CLS_WARPS > 0 ? (uint32_t)sms * B_WARPS_PER_SM / CLS_WARPS : 1;
+    // large path (persistent warps; exits at once if nothing was queued)
+    const uint32_t b_blocks = std::max(1u, (uint32_t)(sms * B_WARPS_PER_SM / CLS_WARPS));
     const uint64_t b_warps = (uint64_t)b_blocks * CLS_WARPS;
-    Tmp<uint64_t> gkeys(mem, b_warps * KB_SLOTS, s), gloff(mem, b_warps * LIST_B, s);
-    Tmp<uint32_t> gcnts(mem, b_warps * KB_SLOTS, s), glcnt(mem, b_warps * LIST_B, s),
-        glpre(mem, b_warps * (LIST_B + 1), s);
-    if (!gkeys.ok() || !gloff.ok() || !gcnts.ok() || !glcnt.ok() || !glpre.ok()) return cudaErrorMemoryAllocation;
-    MC_LAUNCH("classify_large", s, k_classify_large<R><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, gkeys.ptr, gcnts.ptr,
-                                                           gloff.ptr, glcnt.ptr, glpre.ptr));
+    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    Tmp<unsigned char> scratch(mem, b_warps * per_warp_b, s);
+    if (!scratch.ok()) return cudaErrorMemoryAllocation;
+    MC_LAUNCH("classify_large", s,
+              k_classify_large<R><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, scratch.ptr,
+                                                                     per_warp_b));
     return cudaGetLastError();
 }
 

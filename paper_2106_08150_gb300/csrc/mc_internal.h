@@ -87,8 +87,7 @@ struct FinalizeOut {
     uint64_t n_keys = 0;
     uint64_t n_kept = 0;
     uint64_t overflow_keys = 0;
-    uint64_t* locs = nullptr;      // n_kept, (target << 32) | window
-    uint64_t* kept_pairs = nullptr; // n_kept, (h2 << 32) | global window
+    uint64_t* locs = nullptr;  // n_kept, (target << 32) | window
     uint4* table = nullptr;         // table_len entries {h2, count, offset lo, offset hi}
     uint64_t table_len = 0;
     uint64_t table_bytes = 0;
@@ -101,6 +100,11 @@ struct FinalizeOut {
 // linear-probing feature table.  wbase: n_targets+1 global window bases.
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
                            uint32_t n_targets, FinalizeOut* out, cudaStream_t s);
+
+// The (h2 << 32 | global window) pairs of a finalized layout, in layout
+// order (out has n_kept entries).
+cudaError_t reconstruct_pairs(const uint4* table, uint64_t table_len, const uint64_t* locs, const uint32_t* wbase,
+                              uint64_t* out, cudaStream_t s);
 
 // Taxonomy: depth per node and lineage rows lin[x * stride + d].
 cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* depth, uint32_t* max_depth,

@@ -11,11 +11,11 @@
 //     4-base loads and sub-warp shuffles; here the window start is any base,
 //     the stride need not be a multiple of 4);
 //  3. canonical code = min(forward, reverse complement), hashed by h1;
-//  4. the s smallest distinct hashes are extracted with s rounds of a warp
-//     min-reduction (redux.sync) over the lanes' locally sorted, locally
-//     de-duplicated lists: each round pops the minimum from every lane that
-//     holds it, so repeated k-mers count once (Section 2).
-// Lane i (< count) ends up holding the i-th smallest feature.
+//  4. the s smallest distinct hashes (Section 2: repeated k-mers count
+//     once) are selected by a cutoff + warp bitonic sort, with an exact
+//     min-reduction fallback (see warp_sketch_multi).
+// Lane i (< count) ends up holding the i-th smallest feature.  Several
+// windows can be sketched together so that their dependency chains overlap.
 #pragma once
 
 #include "mc_common.cuh"
@@ -43,91 +43,181 @@ __device__ __forceinline__ uint32_t window_kmers(uint64_t L, uint64_t ws, const 
     return (uint32_t)(last - ws + 1);
 }
 
-// Computes the sketch of the window starting at base `ws` of `seq` (length
-// L).  Returns the number of features (warp-uniform); lane i < count holds
-// feature i (ascending) in `feature`.  Requires 32*R >= w.
-template <int R>
-__device__ __forceinline__ uint32_t warp_sketch(const uint8_t* __restrict__ seq, uint64_t L, uint64_t ws,
-                                                const SketchParams& p, uint32_t& feature) {
-    constexpr int E_MAX = (15 + R - 1) / R;  // neighbours for k <= 16
+// Bitonic sort of one value per lane across the warp (ascending by lane).
+__device__ __forceinline__ uint32_t warp_sort32(uint32_t v) {
     const uint32_t lane = lane_id();
-    const uint32_t n_k = window_kmers(L, ws, p);
-    uint64_t lim = ws + p.w;
-    if (lim > L) lim = L;
-
-    // 1. load and encode R bases
-    uint32_t code = 0, inv = 0;
-    const uint64_t b0 = ws + (uint64_t)R * lane;
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        uint64_t b = b0 + i;
-        uint32_t c = (b < lim) ? (uint32_t)__ldg(seq + b) : 0u;
-        uint32_t ok = (b < lim) ? base_valid(c) : 0u;
-        code = (code << 2) | base_code(c);
-        inv = (inv << 1) | (ok ^ 1u);
-    }
-
-    // 2. bases of the following lanes
-    uint64_t comb = code, combinv = inv;
+    for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-    for (int e = 1; e <= E_MAX; ++e) {
-        uint32_t c2 = __shfl_down_sync(FULL_MASK, code, e);
-        uint32_t i2 = __shfl_down_sync(FULL_MASK, inv, e);
-        comb = (comb << (2 * R)) | c2;
-        combinv = (combinv << R) | i2;
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const uint32_t u = __shfl_xor_sync(FULL_MASK, v, j);
+            const bool up = (lane & k) == 0;
+            const bool lower = (lane & j) == 0;
+            v = (lower == up) ? min(v, u) : max(v, u);
+        }
     }
-    constexpr int T = R * (1 + E_MAX);  // bases held by this lane
+    return v;
+}
 
-    // 3. canonical k-mers and h1
-    uint32_t h[R];
-    int nv = 0;
+// Computes the sketches of NW windows at once (independent dependency
+// chains interleave).  Window w starts at base ws[w] of seq[w] (length
+// L[w]; global memory, or shared memory when GLOBAL_SEQ is false); inactive
+// windows yield count 0.  count[w] is warp-uniform; lane i < count[w] holds
+// feature i of window w (ascending) in feature[w].  Requires 32*R >= w.
+// cand: per-warp shared scratch of NW*32 words.
+//
+// Selection of the s smallest distinct hashes: a cutoff tau is chosen so
+// that about 24 of the window's n_k hashes fall below it (all of them when
+// n_k <= 32).  The hashes <= tau (at most 32 of them) are gathered one per
+// lane, sorted by a warp bitonic network and de-duplicated.  If that gives
+// at least s distinct values, or no valid hash lies above tau, they are
+// exactly the s smallest distinct hashes.  Otherwise (a few percent of
+// windows, and low-complexity windows) the exact fallback runs: s rounds of
+// a warp min-reduction over locally sorted, de-duplicated lane lists.
+template <int R, int NW, bool GLOBAL_SEQ = true>
+__device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW], const uint64_t (&L)[NW],
+                                                  const uint64_t (&ws)[NW], const bool (&active)[NW],
+                                                  const SketchParams& p, uint32_t* cand, uint32_t (&feature)[NW],
+                                                  uint32_t (&count)[NW]) {
+    constexpr int E_MAX = (15 + R - 1) / R;  // neighbours for k <= 16
+    constexpr int T = R * (1 + E_MAX);       // bases held by a lane
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
     const uint32_t kmask_bits = 2 * p.k;
     const uint64_t cmask = (kmask_bits == 32) ? 0xFFFFFFFFull : ((1ull << kmask_bits) - 1);
     const uint64_t imask = (1ull << p.k) - 1;
+    uint32_t h[NW][R];
+    uint32_t vmask[NW];  // bit r: h[w][r] is a valid k-mer's hash
+    bool fast[NW];
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const uint32_t shift = (uint32_t)(T - r) - p.k;  // T - r - k >= 0 since T >= R + k - 1
-        uint32_t fwd = (uint32_t)((comb >> (2 * shift)) & cmask);
-        bool bad = ((combinv >> shift) & imask) != 0;
-        uint32_t pos = (uint32_t)R * lane + r;
-        bool ok = (pos < n_k) && !bad;
-        uint32_t rc = revcomp_code(fwd, p.k);
-        uint32_t canon = fwd < rc ? fwd : rc;
-        h[r] = ok ? hash_h1(canon) : 0xFFFFFFFFu;
-        nv += ok ? 1 : 0;
+    for (int w = 0; w < NW; ++w) {
+        const uint32_t n_k = active[w] ? window_kmers(L[w], ws[w], p) : 0u;
+        uint64_t lim = ws[w] + p.w;
+        if (lim > L[w]) lim = L[w];
+        if (!active[w]) lim = 0;
+        // 1. load and encode R bases
+        uint32_t code = 0, inv = 0;
+        const uint64_t b0 = ws[w] + (uint64_t)R * lane;
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            const uint64_t b = b0 + i;
+            const bool in = b < lim;
+            const uint32_t c = in ? (GLOBAL_SEQ ? (uint32_t)__ldg(seq[w] + b) : (uint32_t)seq[w][b]) : 0u;
+            const uint32_t ok = in ? base_valid(c) : 0u;
+            code = (code << 2) | base_code(c);
+            inv = (inv << 1) | (ok ^ 1u);
+        }
+        // 2. bases of the following lanes
+        uint64_t comb = code, combinv = inv;
+#pragma unroll
+        for (int e = 1; e <= E_MAX; ++e) {
+            comb = (comb << (2 * R)) | __shfl_down_sync(FULL_MASK, code, e);
+            combinv = (combinv << R) | __shfl_down_sync(FULL_MASK, inv, e);
+        }
+        // 3. canonical k-mers and h1
+        vmask[w] = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const uint32_t shift = (uint32_t)(T - r) - p.k;  // >= 0 since T >= R + k - 1
+            const uint32_t fwd = (uint32_t)((comb >> (2 * shift)) & cmask);
+            const bool bad = ((combinv >> shift) & imask) != 0;
+            const bool ok = ((uint32_t)R * lane + r < n_k) && !bad;
+            const uint32_t rc = revcomp_code(fwd, p.k);
+            h[w][r] = ok ? hash_h1(fwd < rc ? fwd : rc) : 0xFFFFFFFFu;
+            vmask[w] |= (ok ? 1u : 0u) << r;
+        }
+        // 4. candidates below the cutoff, one per lane in cand[]
+        const uint32_t tau = n_k <= 32 ? 0xFFFFFFFFu : (uint32_t)min((24ull << 32) / n_k, 0xFFFFFFFFull);
+        uint32_t cmine = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) cmine += (((vmask[w] >> r) & 1u) && h[w][r] <= tau) ? 1u : 0u;
+        uint32_t pre = cmine;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL_MASK, pre, d);
+            if ((int)lane >= d) pre += x;
+        }
+        const uint32_t C = __shfl_sync(FULL_MASK, pre, 31);
+        const uint32_t Nv = __reduce_add_sync(FULL_MASK, (uint32_t)__popc(vmask[w]));
+        pre -= cmine;
+        fast[w] = C <= 32;
+        if (fast[w]) {
+            uint32_t o = pre;
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                if (((vmask[w] >> r) & 1u) && h[w][r] <= tau) cand[w * 32 + o++] = h[w][r];
+        }
+        __syncwarp();
+        if (fast[w]) {
+            uint32_t v = lane < C ? cand[w * 32 + lane] : 0xFFFFFFFFu;
+            v = warp_sort32(v);
+            const uint32_t prev = __shfl_up_sync(FULL_MASK, v, 1);
+            const bool fresh = lane < C && (lane == 0 || v != prev);
+            const uint32_t nd = __ballot_sync(FULL_MASK, fresh);
+            const uint32_t D = __popc(nd);
+            fast[w] = D >= p.s || C == Nv;
+            if (fast[w]) {
+                __syncwarp();
+                if (fresh) cand[w * 32 + __popc(nd & lt)] = v;
+                __syncwarp();
+                count[w] = D < p.s ? D : p.s;
+                feature[w] = lane < count[w] ? cand[w * 32 + lane] : 0u;
+            }
+        }
     }
 
-    // 4. local sort + local de-duplication (valid entries are the first nv)
-    sort_small<R>(h);
-    int ndup = 0;
+    // exact fallback for the windows the cutoff did not settle
+    uint32_t need = 0;
 #pragma unroll
-    for (int r = R - 1; r >= 1; --r) {
-        bool dup = (r < nv) && (h[r] == h[r - 1]);
-        if (dup) { h[r] = 0xFFFFFFFFu; ++ndup; }
+    for (int w = 0; w < NW; ++w) need |= (fast[w] ? 0u : 1u) << w;
+    if (need == 0) return;
+    int nv[NW];
+    bool any_dup = false;
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        nv[w] = 0;
+        if (fast[w]) continue;
+        // local sort + local de-duplication (valid entries become the first nv)
+        nv[w] = __popc(vmask[w]);
+        sort_small<R>(h[w]);
+#pragma unroll
+        for (int r = R - 1; r >= 1; --r) {
+            if ((r < nv[w]) && (h[w][r] == h[w][r - 1])) {
+                h[w][r] = 0xFFFFFFFFu;
+                nv[w] -= 1;
+                any_dup = true;
+            }
+        }
+        count[w] = 0;
+        feature[w] = 0;
     }
-    if (__any_sync(FULL_MASK, ndup > 0)) {
-        sort_small<R>(h);
-        nv -= ndup;
+    if (__any_sync(FULL_MASK, any_dup)) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w)
+            if (!fast[w]) sort_small<R>(h[w]);
     }
-
-    // s rounds of warp-wide minimum extraction
-    uint32_t cnt = 0;
-    feature = 0;
     for (uint32_t it = 0; it < p.s; ++it) {
-        bool has = nv > 0;
-        if (!__any_sync(FULL_MASK, has)) break;
-        uint32_t head = has ? h[0] : 0xFFFFFFFFu;
-        uint32_t m = __reduce_min_sync(FULL_MASK, head);
-        bool pop = has && (h[0] == m);
+        uint32_t mine = 0;
 #pragma unroll
-        for (int r = 0; r < R - 1; ++r) h[r] = pop ? h[r + 1] : h[r];
-        h[R - 1] = pop ? 0xFFFFFFFFu : h[R - 1];
-        nv -= pop ? 1 : 0;
-        if (lane == it) feature = m;
-        ++cnt;
+        for (int w = 0; w < NW; ++w) mine |= (nv[w] > 0 ? 1u : 0u) << w;
+        const uint32_t live = __reduce_or_sync(FULL_MASK, mine);
+        if (live == 0) break;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (!((live >> w) & 1u)) continue;
+            const bool has = nv[w] > 0;
+            const uint32_t m = __reduce_min_sync(FULL_MASK, has ? h[w][0] : 0xFFFFFFFFu);
+            const bool pop = has && (h[w][0] == m);
+#pragma unroll
+            for (int r = 0; r < R - 1; ++r) h[w][r] = pop ? h[w][r + 1] : h[w][r];
+            h[w][R - 1] = pop ? 0xFFFFFFFFu : h[w][R - 1];
+            nv[w] -= pop ? 1 : 0;
+            if (lane == it) feature[w] = m;
+            count[w] += 1;
+        }
     }
-    return cnt;
 }
+
 
 // R for a window length: the warp covers 32*R >= w bases.
 __host__ __device__ inline int sketch_r_for(uint32_t w) { return w <= 128 ? 4 : (w <= 256 ? 8 : 16); }

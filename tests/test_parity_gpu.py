@@ -355,3 +355,26 @@ def test_batch_invariance(mc, tiny):
         for x, y in zip(full[:3], part[:3]):
             assert (x[a:b] == y).all()
     db.free()
+
+
+def test_query_mate_and_insert_limits(mc, tiny):
+    """More than MC_MAX_QUERY_MATES mates leave the query unclassified with a
+    capacity status; max_insert beyond MC_MAX_INSERT is rejected."""
+    import torch
+    w = tiny
+    db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **w.db_params)
+    g = bytes(w.genomes).decode()
+    mates = [g[0:100]] + [g[1000 + 40 * i: 1030 + 40 * i] for i in range(40)]
+    roffs = offsets([len(x) for x in mates])
+    qoffs = np.array([0, 1, 41], dtype=np.uint32)
+    label = torch.zeros(2, dtype=torch.int32, device="cuda")
+    hits = torch.zeros(2, dtype=torch.int32, device="cuda")
+    db.classify(dev(u8("".join(mates))), dev(roffs), dev(qoffs), label=label, hits=hits, **w.cls_params)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_classify_status(db.handle)
+    assert e.value.code == mc.MC_ERR_CAPACITY
+    assert host_u32(label)[1] == mc.MC_NO_TAXON and host_u32(label)[0] == w.taxon_of_target[0]
+    with pytest.raises(mc.McError) as e:
+        db.classify(dev(u8("".join(mates))), dev(roffs), dev(qoffs), **dict(w.cls_params, max_insert=70000))
+    assert e.value.code == mc.MC_ERR_ARG
+    db.free()
