@@ -169,6 +169,30 @@ int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_se
                 const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                 uint32_t* hits, uint32_t* top_target, void* stream);
 
+/* Allocation-free classification (this library's addition; the paper has
+ * no counterpart).  Same arguments, results and asynchronous behaviour as
+ * mc_classify, for callers that cannot allocate device memory during the
+ * call -- for example a server whose GPU memory is entirely reserved by
+ * another allocator, or a latency-critical loop that must avoid the
+ * allocation path.  mc_classify takes its per-call scratch from the
+ * allocator; this function allocates nothing and instead uses a fixed
+ * scratch array of MC_NOALLOC_SCRATCH_BYTES compiled into the library,
+ * which every GPU that loads the library holds until the process exits.
+ *  - At most MC_NOALLOC_MAX_QUERIES queries per call; larger calls return
+ *    MC_ERR_CAPACITY (split the batch).
+ *  - The first call on each device looks up the device address of the
+ *    scratch array (cudaGetSymbolAddress, with that device current); make
+ *    that first call before any stream capture.
+ *  - All calls on a device share the one scratch array: calls whose work
+ *    overlaps on the GPU (other streams, other threads) race and corrupt
+ *    each other.  Serialise them, e.g. on one stream.
+ *  - Device-detected errors are reported by mc_classify_status as usual. */
+#define MC_NOALLOC_MAX_QUERIES 16384u
+#define MC_NOALLOC_SCRATCH_BYTES (48u << 20)
+int mc_classify_noalloc(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
+                        const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
+                        uint32_t* hits, uint32_t* top_target, void* stream);
+
 /* Synchronises `stream` and returns (and clears) the first device-detected
  * error of earlier mc_classify calls of this database (MC_ERR_CAPACITY for
  * a query with more distinct hit locations than the largest per-query

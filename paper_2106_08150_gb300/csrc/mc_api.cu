@@ -508,6 +508,59 @@ static int classify_impl(const mc_db* db, const mc_classify_params* params, uint
     return MC_OK;
 }
 
+}  // extern "C"
+
+namespace mc {
+int report_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int classify_prepare(const mc_db* db, const mc_classify_params* params, const char* seq, const uint64_t* offs,
+                     uint32_t n_queries, const uint32_t* qoffs, uint32_t* label, uint32_t* hits,
+                     uint32_t* top_target, cudaStream_t stream, ClassifyDb* cdb, ClassifyQuery* q) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (!db->has_table) return fail(MC_ERR_STATE, "classify before mc_db_finalize");
+    if (n_queries && (!seq || !offs || !qoffs || !label || !hits))
+        return fail(MC_ERR_ARG, "NULL input or output pointer");
+    MC_CU(cudaStreamWaitEvent(stream, db->ready, 0));
+    cdb->table = (const uint4*)db->table.p;
+    cdb->log_t = db->log_t;
+    cdb->max_probe = db->max_probe;
+    cdb->locs = (const uint64_t*)db->locs.p;
+    cdb->taxon_of_target = (const uint32_t*)db->taxon.p;
+    cdb->n_targets = db->n_targets;
+    cdb->lineage = (const uint32_t*)db->lineage.p;
+    cdb->depth = (const uint32_t*)db->depth.p;
+    cdb->lin_stride = db->lin_stride;
+    cdb->n_taxa = db->n_taxa;
+    cdb->sp = db->sp;
+    q->seq = (const uint8_t*)seq;
+    q->offs = offs;
+    q->qoffs = qoffs;
+    q->n_q = n_queries;
+    q->m = params->max_candidates;
+    q->hits_min = params->hits_min;
+    q->band = params->lca_band_pct;
+    q->max_insert = params->max_insert;
+    q->label = label;
+    q->hits = hits;
+    q->top_target = top_target;
+    q->cands = nullptr;
+    q->counters = nullptr;
+    q->status = (uint32_t*)db->status.p;
+    return MC_OK;
+}
+}  // namespace mc
+
+extern "C" {
+
 int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                 const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label, uint32_t* hits,
                 uint32_t* top_target, void* stream) {

@@ -662,7 +662,85 @@ cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery
     return cudaGetLastError();
 }
 
+// Number of large-path warps of the allocation-free launch.
+constexpr uint32_t NOALLOC_B_WARPS = 8;
+
+__host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Scratch layout of the allocation-free launch: overflow queue + counters,
+// query metadata, bucket lists, large-path working memory.
+struct NoAllocLayout {
+    size_t ovf, meta, glist, large, total;
+};
+
+NoAllocLayout noalloc_layout(uint32_t n_q, uint32_t sketch_size) {
+    NoAllocLayout L;
+    const size_t list_cap = (size_t)WIN_A * sketch_size;
+    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    L.ovf = 0;
+    L.meta = align256(L.ovf + ((size_t)n_q + 4) * 4);
+    L.glist = align256(L.meta + (size_t)n_q * sizeof(uint4));
+    L.large = align256(L.glist + (size_t)n_q * list_cap * 8);
+    L.total = align256(L.large + NOALLOC_B_WARPS * per_warp_b);
+    return L;
+}
+
+template <int R>
+cudaError_t launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch, size_t scratch_len,
+                           cudaStream_t s) {
+    cudaError_t e;
+    const NoAllocLayout Lay = noalloc_layout(Q.n_q, db.sp.s);
+    if (Lay.total > scratch_len) return cudaErrorInvalidValue;
+    const uint32_t list_cap = WIN_A * db.sp.s;
+    int dev = 0, sms = NUM_SMS_HINT;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem_l = LK_WARPS * ((scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15);
+    const size_t smem_s = CLS_WARPS * ((scratch_bytes(KA_DEFAULT, list_cap, 0) + 15) & ~(size_t)15);
+    auto kl = k_classify_lookup<R>;
+    auto ks = k_classify_score<KA_DEFAULT>;
+    if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s)) != cudaSuccess)
+        return e;
+    int occ_l = 1, occ_s = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, kl, LK_WARPS * 32, smem_l)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, CLS_WARPS * 32, smem_s)) != cudaSuccess) return e;
+    occ_l = std::max(occ_l, 1);
+    occ_s = std::max(occ_s, 1);
+    uint32_t* ovf = reinterpret_cast<uint32_t*>(scratch + Lay.ovf);
+    uint32_t* ovf_n = ovf + Q.n_q;
+    uint32_t* work = ovf_n + 1;
+    uint4* meta = reinterpret_cast<uint4*>(scratch + Lay.meta);
+    uint64_t* glist = reinterpret_cast<uint64_t*>(scratch + Lay.glist);
+    unsigned char* large = scratch + Lay.large;
+    // the queue counters are the only scratch that must start at zero
+    if ((e = cudaMemsetAsync(ovf_n, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    const uint32_t nq = Q.n_q;
+    const uint32_t gl = (uint32_t)std::min<uint64_t>(((uint64_t)nq + LK_WARPS - 1) / LK_WARPS, (uint64_t)sms * occ_l);
+    const uint32_t gs = (uint32_t)std::min<uint64_t>(((uint64_t)nq + CLS_WARPS - 1) / CLS_WARPS, (uint64_t)sms * occ_s);
+    MC_LAUNCH("classify_lookup", s, kl<<<gl, LK_WARPS * 32, smem_l, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
+    MC_LAUNCH("classify_score", s, ks<<<gs, CLS_WARPS * 32, smem_s, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    MC_LAUNCH("classify_large", s,
+              k_classify_large<R><<<NOALLOC_B_WARPS / CLS_WARPS, CLS_WARPS * 32, 0, s>>>(db, Q, ovf, ovf_n, work, large,
+                                                                                       per_warp_b));
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size) { return noalloc_layout(n_q, sketch_size).total; }
+
+cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch,
+                                   size_t scratch_len, cudaStream_t s) {
+    if (Q.n_q == 0) return cudaSuccess;
+    int r = sketch_r_for(db.sp.w);
+    if (r == 4) return launch_noalloc<4>(db, Q, scratch, scratch_len, s);
+    if (r == 8) return launch_noalloc<8>(db, Q, scratch, scratch_len, s);
+    return launch_noalloc<16>(db, Q, scratch, scratch_len, s);
+}
 
 cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
     if (Q.n_q == 0) return cudaSuccess;

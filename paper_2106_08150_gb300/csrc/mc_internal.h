@@ -149,4 +149,20 @@ struct ClassifyQuery {
 
 cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& q, cudaStream_t s);
 
+// Classification that allocates nothing: every scratch buffer is carved out
+// of `scratch` (scratch_len bytes, 256-byte aligned).  classify_noalloc_bytes
+// is the size a call with n_q queries needs.
+size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size);
+cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& q, unsigned char* scratch,
+                                   size_t scratch_len, cudaStream_t s);
+
+// ------------------------------------------------------------- mc_api.cu
+// Records an error message for mc_last_error_string and returns `code`.
+int report_error(int code, const char* fmt, ...);
+// Checks a classify call and fills the kernel views of the database and the
+// query (no allocation); makes `stream` wait for the last finalize.
+int classify_prepare(const mc_db* db, const mc_classify_params* params, const char* seq, const uint64_t* offs,
+                     uint32_t n_queries, const uint32_t* qoffs, uint32_t* label, uint32_t* hits,
+                     uint32_t* top_target, cudaStream_t stream, ClassifyDb* cdb, ClassifyQuery* q);
+
 }  // namespace mc

@@ -74,6 +74,8 @@ _SIGS = {
     "mc_classify_debug": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp,
                            _vp, _vp], _i),
     "mc_classify_status": ([_vp, _vp], _i),
+    "mc_classify_noalloc": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp,
+                             _vp], _i),
     "mc_db_free": ([_vp], None),
     "mc_db_stats": ([_vp, ctypes.POINTER(mc_db_stats_t)], _i),
     "mc_db_dump": ([_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i),
@@ -191,6 +193,17 @@ def mc_classify_debug(db: int, params: mc_classify_params, n_seq: int, seq, offs
     _check(_lib.mc_classify_debug(db, ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), n_queries, _ptr(qoffs),
                                   _ptr(label), _ptr(hits), _ptr(top_target), _ptr(cands), _ptr(counters),
                                   _stream(stream)))
+
+
+MC_NOALLOC_MAX_QUERIES = 16384
+
+
+def mc_classify_noalloc(db: int, params: mc_classify_params, n_seq: int, seq, offs, n_queries: int, qoffs, label,
+                        hits, top_target=None, stream=None):
+    """mc_classify without any device allocation (fixed scratch inside the
+    library; at most MC_NOALLOC_MAX_QUERIES queries per call)."""
+    _check(_lib.mc_classify_noalloc(db, ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), n_queries, _ptr(qoffs),
+                                    _ptr(label), _ptr(hits), _ptr(top_target), _stream(stream)))
 
 
 def mc_classify_status(db: int, stream=None):
