@@ -4,7 +4,7 @@
 One step = the whole hot path over one batch of synthetic input: build the
 database from the reference genomes (sketch, sort, cap, condensed layout)
 and classify every read pair against it (the paper's on-the-fly mode,
-Section 5.4).  The default workload is the mid-size configuration: 1,000
+Section 5.3).  The default workload is the mid-size configuration: 1,000
 genomes (~3.4 Gbp) in 100 genera, 10M paired-end 2x150 bp reads.
 
 Prints one JSON line.  `value` is read pairs classified per second over the
@@ -86,6 +86,24 @@ def workload_config(w, args, n_gpus):
         "l2": "inputs larger than L2 (genomes 3.4 GB, reads 3 GB)" if args.workload == "mid" else "small workload",
         "recipe": w.recipe,
     }
+
+
+# ------------------------------------------------------------- ranks
+def max_over_ranks(vals, world: int, device=None) -> list:
+    """Element-wise maximum over all ranks (the timed region's slowest rank)."""
+    if world <= 1:
+        return [float(v) for v in vals]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_rate(units_per_rank: float, world: int, steps: int, total_ms: float, scale: float = 1e6) -> float:
+    """Units processed by all ranks per second (weak scaling: every rank does
+    the same per-rank work), in units of `scale`."""
+    return world * units_per_rank * steps / (total_ms * 1e-3) / scale
 
 
 # ------------------------------------------------------------- clocks
@@ -289,11 +307,7 @@ def run_gpu(args, rank, world, local_rank):
     ends = starts[1:] + [ev_end]
     cls_ms = sum(a.elapsed_time(b) for a, b in zip(mids, ends))
 
-    # max over ranks
-    t = torch.tensor([total_ms, build_ms, cls_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms, build_ms, cls_ms = t.tolist()
+    total_ms, build_ms, cls_ms = max_over_ranks([total_ms, build_ms, cls_ms], world, dev)
 
     # end-to-end through the public API with host buffers (pinned), copies timed
     e2e = None
@@ -325,12 +339,8 @@ def run_gpu(args, rank, world, local_rank):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize()
-        e2e_ms = (time.perf_counter() - t0) * 1e3
-        te = torch.tensor([e2e_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e_ms = te.item()
-        e2e = {"value": world * nq * args.steps / (e2e_ms * 1e-3) / 1e6, "unit": UNIT,
+        e2e_ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, dev)[0]
+        e2e = {"value": whole_job_rate(nq, world, args.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": e2e_ms / args.steps}
 
@@ -345,16 +355,20 @@ def run_gpu(args, rank, world, local_rank):
         traffic_db = load_traffic()
         traffic = None
         tinfo = traffic_db.get(dom)
-        if tinfo and tinfo.get("src_sha") == kernel_source_hash() and tinfo.get("workload") == args.workload:
-            traffic = tinfo.get("bytes_per_launch")
         if per_step_bytes is not None:
             per_launch_bytes = per_step_bytes / per_launch_count
+            if tinfo and tinfo.get("src_sha") == kernel_source_hash():
+                # DRAM bytes of one ncu capture (profiles/), scaled to this
+                # launch by the ratio of algorithmic bytes; null once the
+                # kernel sources changed after the capture
+                ratio = tinfo["dram_bytes_per_launch_captured"] / tinfo["algorithmic_bytes_per_launch_captured"]
+                traffic = round(ratio * per_launch_bytes)
             achieved = per_launch_bytes / (kernels[dom]["avg_ms"] * 1e-3) / 1e9
             roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                     "frac": round(achieved / peak, 4), "traffic": traffic,
                     "algorithmic_bytes_per_launch": per_launch_bytes, "peak_source": peak_src + " (burst)"}
 
-    value = world * nq * args.steps / (total_ms * 1e-3) / 1e6
+    value = whole_job_rate(nq, world, args.steps, total_ms)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,

@@ -85,7 +85,7 @@ typedef struct mc_db_params {
 /* Classification parameters, per mc_classify call (Section 3.2). */
 typedef struct mc_classify_params {
     uint32_t max_candidates; /* m: top hits kept, 1..8 (Section 3.2: usually 2..4) */
-    uint32_t hits_min;       /* minimum top score to classify (Section 5.6: hit threshold) */
+    uint32_t hits_min;       /* minimum top score to classify (Section 5.5: hit threshold) */
     uint32_t lca_band_pct;   /* 0..100: candidates with score >= (100-band)% of the top score
                                 are "close"; one close candidate -> its taxon, several -> LCA */
     uint32_t max_insert;     /* read pairs: sliding-window span is max(len1+len2, max_insert);
@@ -264,7 +264,7 @@ int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_
 
 /* ---------------------------------------------------------------------
  * Tracing and launch accounting (no counterpart in the paper beyond its
- * per-stage breakdown, Section 5.5).
+ * per-stage breakdown, Section 5.4).
  * ------------------------------------------------------------------- */
 
 /* Enables (1) or disables (0) tracing: each kernel launch of the library is

@@ -358,7 +358,7 @@ uint64_t oracle_sws(uint32_t n_mates, uint64_t span_sum, uint32_t max_insert, ui
 //     + 1, the most windows a fragment of that span can touch;
 //  5. top m (Section 3.2): one candidate per target (its best range; ties ->
 //     smaller j0), ordered by score descending then target ascending;
-//  6. label (Section 3.2 and Section 5.6 hit threshold): no candidate or
+//  6. label (Section 3.2 and Section 5.5 hit threshold): no candidate or
 //     top score < hits_min -> unclassified.  Otherwise the candidates whose
 //     score is within lca_band_pct percent of the top score are "close"; one
 //     close candidate -> its target's taxon ("difference above a

@@ -3,7 +3,7 @@
 //
 // GB300 design.  The paper runs the query as a pipeline of kernels with
 // global-memory hand-offs: sketch+lookup, compaction, a segmented sort
-// (about half of its query time, Section 5.5) and a top-candidate kernel.
+// (about half of its query time, Section 5.4) and a top-candidate kernel.
 // Here one warp carries a whole query (a read or a read pair) through all
 // steps without leaving the SM:
 //   1. sketch every window of every mate (mc_sketch.cuh) and look each
@@ -397,7 +397,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
 
     // 5. top m with one candidate per target (Section 3.2 / 4.6): m rounds
     // of warp arg-max, excluding the targets already chosen; the label is
-    // folded as the candidates come (hit threshold of Section 5.6, LCA of
+    // folded as the candidates come (hit threshold of Section 5.5, LCA of
     // the close candidates of Section 3.2)
     const int m = (int)Q.m;
     Cand mine = Cand{0, 0xFFFFFFFFu, 0, 0};
