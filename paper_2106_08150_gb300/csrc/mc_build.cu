@@ -184,7 +184,7 @@ constexpr int SK_NW = 2;  // windows sketched together by a warp
 // One warp per window; a warp takes WINDOWS_PER_TASK consecutive windows
 // and walks the sequences they belong to.  EMIT = build pairs, else the
 // debug sketch export.
-template <int R, bool EMIT>
+template <int R, int KC, bool EMIT>
 __global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, const uint8_t* __restrict__ seq,
                                                const uint64_t* __restrict__ offs,
                                                const uint64_t* __restrict__ win_offs, uint64_t n_windows,
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, c
                 }
             }
             uint32_t f[SK_NW], cnt[SK_NW];
-            warp_sketch_multi<R, SK_NW>(sq, Ls, wss, act, p, cand, f, cnt);
+            warp_sketch_multi<R, SK_NW, KC>(sq, Ls, wss, act, p, cand, f, cnt);
 #pragma unroll
             for (int i = 0; i < SK_NW; ++i) {
                 if (!act[i]) continue;
@@ -258,14 +258,18 @@ cudaError_t launch_sketch(const SketchParams& p, uint32_t n_seq, const uint8_t* 
     uint64_t tasks = (n_windows + WINDOWS_PER_TASK - 1) / WINDOWS_PER_TASK;
     uint64_t blocks = (tasks + NWARP - 1) / NWARP;
     uint32_t g = grid_for(blocks, 16);
-    int r = sketch_r_for(p.w);
-    if (r == 4)
-        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<4, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real));
-    else if (r == 8)
-        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<8, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real));
-    else
-        MC_LAUNCH(EMIT ? "sketch_emit" : "sketch", s, k_sketch<16, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts,
-                                            real));
+    const int r = sketch_r_for(p.w);
+    const char* name = EMIT ? "sketch_emit" : "sketch";
+#define MC_SK(RR, KK) \
+    MC_LAUNCH(name, s, k_sketch<RR, KK, EMIT><<<g, BT, 0, s>>>(p, n_seq, seq, offs, win_offs, n_windows, gw_base, pairs, sketch, counts, real))
+    if (r == 4) {
+        if (p.k == 16) MC_SK(4, 16); else MC_SK(4, 0);
+    } else if (r == 8) {
+        if (p.k == 16) MC_SK(8, 16); else MC_SK(8, 0);
+    } else {
+        if (p.k == 16) MC_SK(16, 16); else MC_SK(16, 0);
+    }
+#undef MC_SK
     return cudaGetLastError();
 }
 }  // namespace

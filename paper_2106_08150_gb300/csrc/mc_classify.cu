@@ -55,22 +55,30 @@ __device__ __forceinline__ uint32_t loc_slot(uint64_t loc, uint32_t mask) {
     return (uint32_t)(h >> 32) & mask;
 }
 
+// Histogram count increment: 32-bit counts use atomicAdd directly; 16-bit
+// counts add 1 << 16*(slot&1) to the aligned 32-bit word holding them (a
+// count never passes 65535 there, so the neighbour is not disturbed).
+__device__ __forceinline__ void count_inc(uint32_t* cnts, uint32_t slot) { atomicAdd(cnts + slot, 1u); }
+__device__ __forceinline__ void count_inc(uint16_t* cnts, uint32_t slot) {
+    atomicAdd(reinterpret_cast<uint32_t*>(cnts) + (slot >> 1), 1u << ((slot & 1u) * 16));
+}
+
 // Histogram insert (count + 1).  `fresh_slot` receives the slot if the
 // location was new, else stays -1.  Returns false if the table is full.
-__device__ __forceinline__ bool hist_insert(uint64_t* keys, uint32_t* cnts, uint32_t mask, uint64_t loc,
-                                            int& fresh_slot) {
+template <class CntT>
+__device__ __forceinline__ bool hist_insert(uint64_t* keys, CntT* cnts, uint32_t mask, uint64_t loc, int& fresh_slot) {
     uint32_t slot = loc_slot(loc, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         uint64_t k = *(volatile uint64_t*)(keys + slot);
         if (k == loc) {
-            atomicAdd(cnts + slot, 1u);
+            count_inc(cnts, slot);
             return true;
         }
         if (k == EMPTY_LOC) {
             unsigned long long prev =
                 atomicCAS((unsigned long long*)(keys + slot), (unsigned long long)EMPTY_LOC, (unsigned long long)loc);
             if (prev == EMPTY_LOC || prev == loc) {
-                atomicAdd(cnts + slot, 1u);
+                count_inc(cnts, slot);
                 if (prev == EMPTY_LOC) fresh_slot = (int)slot;
                 return true;
             }
@@ -80,8 +88,8 @@ __device__ __forceinline__ bool hist_insert(uint64_t* keys, uint32_t* cnts, uint
     return false;
 }
 
-__device__ __forceinline__ uint32_t hist_count(const uint64_t* keys, const uint32_t* cnts, uint32_t mask,
-                                               uint64_t loc) {
+template <class CntT>
+__device__ __forceinline__ uint32_t hist_count(const uint64_t* keys, const CntT* cnts, uint32_t mask, uint64_t loc) {
     uint32_t slot = loc_slot(loc, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
         uint64_t k = keys[slot];
@@ -109,48 +117,66 @@ constexpr uint32_t MAX_MATES = MC_MAX_QUERY_MATES;  // mates per query (lane i h
 constexpr int LB = 4;               // feature-table probes in flight per lane
 constexpr int GB = 8;               // bucket loads in flight per lane
 
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
 // Per-warp working memory (shared memory on the main path, global scratch
-// on the large path).
+// on the large path).  CntT is the histogram count type: 16 bits on the
+// shared-memory path (whose queries gather at most 65,535 locations), 32
+// bits on the large path.  Unused regions have size 0.
+template <class CntT>
 struct Scratch {
-    uint64_t* keys;   // histogram keys (location), kcap
-    uint32_t* cnts;   // histogram counts, kcap
-    uint32_t* score;  // sliding-window scores of the dense entries, kcap
-    uint32_t* dense;  // slots of the distinct locations, kcap
-    uint32_t kcap;    // power of two
-    uint32_t* feat;   // features of all windows, list_cap
-    uint64_t* l_off;  // found buckets: offset, size, exclusive prefix (list_cap + 1)
-    uint32_t* l_cnt;
-    uint32_t* l_pre;
+    uint64_t* keys;    // histogram keys (location), kcap
+    CntT* cnts;        // histogram counts, kcap
+    CntT* score;       // sliding-window scores of the dense entries, kcap
+    uint16_t* dense;   // slots of the distinct locations, kcap
+    uint32_t kcap;     // power of two, <= 65536
+    uint64_t* list;    // found buckets, offset << 16 | size, list_cap
+    uint32_t* l_pre;   // exclusive prefix of bucket sizes, list_cap + 1
     uint32_t list_cap;
-    uint32_t* cand;   // sketch selection scratch, SK_NW * 32
-    uint8_t* buf;     // the query's bases
+    uint32_t* feat;    // features of all windows, feat_cap
+    uint32_t* cand;    // sketch selection scratch, SK_NW * 32
+    uint8_t* buf;      // the query's bases, buf_cap
     uint32_t buf_cap;
-    uint32_t win_cap;
+    uint32_t win_cap;  // windows per query
+    uint32_t max_locs; // locations per query
 };
 
-__host__ __device__ constexpr size_t scratch_bytes(uint32_t kcap, uint32_t list_cap, uint32_t buf_cap) {
-    return (size_t)kcap * 20 + (size_t)list_cap * 20 + 16 + 4 * 32 * SK_NW + buf_cap;
+template <class CntT>
+__host__ __device__ constexpr size_t scratch_bytes(uint32_t kcap, uint32_t list_cap, uint32_t feat_cap,
+                                                   uint32_t buf_cap) {
+    return align16((size_t)kcap * 8) + 2 * align16((size_t)kcap * sizeof(CntT)) + align16((size_t)kcap * 2) +
+           align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + align16((size_t)feat_cap * 4) +
+           (feat_cap ? align16(4 * 32 * SK_NW) : 0) + align16(buf_cap);
 }
 
-// Carves a Scratch out of `base` (16-byte aligned).
-__device__ __forceinline__ Scratch carve(unsigned char* base, uint32_t kcap, uint32_t list_cap, uint32_t buf_cap,
-                                         uint32_t win_cap) {
-    Scratch S;
-    S.keys = reinterpret_cast<uint64_t*>(base);
-    S.l_off = reinterpret_cast<uint64_t*>(base + (size_t)kcap * 8);
-    uint32_t* u = reinterpret_cast<uint32_t*>(base + (size_t)kcap * 8 + (size_t)list_cap * 8);
-    S.cnts = u;
-    S.score = u + kcap;
-    S.dense = S.score + kcap;
-    S.feat = S.dense + kcap;
-    S.l_cnt = S.feat + list_cap;
-    S.l_pre = S.l_cnt + list_cap;
-    S.cand = S.l_pre + list_cap + 4;
-    S.buf = reinterpret_cast<uint8_t*>(S.cand + 32 * SK_NW);
+// Carves a Scratch out of `base` (16-byte aligned), in scratch_bytes order.
+template <class CntT>
+__device__ __forceinline__ Scratch<CntT> carve(unsigned char* base, uint32_t kcap, uint32_t list_cap,
+                                               uint32_t feat_cap, uint32_t buf_cap, uint32_t win_cap) {
+    Scratch<CntT> S;
+    unsigned char* p = base;
+    S.keys = reinterpret_cast<uint64_t*>(p);
+    p += align16((size_t)kcap * 8);
+    S.cnts = reinterpret_cast<CntT*>(p);
+    p += align16((size_t)kcap * sizeof(CntT));
+    S.score = reinterpret_cast<CntT*>(p);
+    p += align16((size_t)kcap * sizeof(CntT));
+    S.dense = reinterpret_cast<uint16_t*>(p);
+    p += align16((size_t)kcap * 2);
+    S.list = reinterpret_cast<uint64_t*>(p);
+    p += align16((size_t)list_cap * 8);
+    S.l_pre = reinterpret_cast<uint32_t*>(p);
+    p += align16(((size_t)list_cap + 4) * 4);
+    S.feat = reinterpret_cast<uint32_t*>(p);
+    p += align16((size_t)feat_cap * 4);
+    S.cand = reinterpret_cast<uint32_t*>(p);
+    p += feat_cap ? align16(4 * 32 * SK_NW) : 0;
+    S.buf = p;
     S.kcap = kcap;
     S.list_cap = list_cap;
     S.buf_cap = buf_cap;
     S.win_cap = win_cap;
+    S.max_locs = sizeof(CntT) == 2 ? 0xFFFFu : 0xFFFFFFFFu;
     return S;
 }
 
@@ -187,15 +213,15 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
 }
 
 // Query steps 1-4 of Section 4.2 on one warp (sketch every window of every
-// mate, look every feature up): the found buckets are written as a list of
-// (offset, size), to the working memory (l_off / l_cnt) or, packed as
-// offset << 16 | size, to `glist`.  Also returns the sliding-window size.
+// mate, look every feature up): the found buckets are written to `list`
+// (working memory or global scratch), packed as offset << 16 | size.  Also
+// returns the sliding-window size.
 // Returns Q_DONE, Q_ESCALATE (needs the large path) or Q_TOO_LARGE.
 // Also returns the number of features and the 32-byte sectors of the found
 // buckets (warp totals) for the counters.
-template <int R, bool TO_GLOBAL>
-__device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
-                                            uint64_t* __restrict__ glist, uint32_t& n_list_out, uint32_t& sws_out,
+template <int R, int KC, class CntT>
+__device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                            const Scratch<CntT>& S, uint64_t* __restrict__ list, uint32_t& n_list_out, uint32_t& sws_out,
                                             uint32_t& n_feat_out, uint32_t& n_sect_out) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
@@ -258,7 +284,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
                 if (act[i]) ++jn;
             }
             uint32_t f[SK_NW], cnt[SK_NW];
-            warp_sketch_multi<R, SK_NW, false>(sq, Ls, wss, act, p, S.cand, f, cnt);
+            warp_sketch_multi<R, SK_NW, KC, false>(sq, Ls, wss, act, p, S.cand, f, cnt);
 #pragma unroll
             for (int i = 0; i < SK_NW; ++i) {
                 if (lane < cnt[i]) S.feat[F + lane] = f[i];
@@ -297,13 +323,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
             }
             const uint32_t found = __ballot_sync(FULL_MASK, c > 0);
             if (c > 0) {
-                const uint32_t li = n_list + __popc(found & lt);
-                if (TO_GLOBAL) {
-                    glist[li] = (off << 16) | c;
-                } else {
-                    S.l_off[li] = off;
-                    S.l_cnt[li] = c;
-                }
+                list[n_list + __popc(found & lt)] = (off << 16) | c;
                 n_sect += ((off * 8 + (uint64_t)c * 8 - 1) >> 5) - ((off * 8) >> 5) + 1;
             }
             n_list += __popc(found);
@@ -322,8 +342,9 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
 // working memory: gather, window count statistic, sliding-window scores,
 // top m, label.  Writes the outputs and returns Q_DONE, or Q_ESCALATE if the
 // histogram does not fit the working memory.
-__device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
-                                           uint32_t n_list, uint32_t sws, Counters& ctr) {
+template <class CntT>
+__device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                           const Scratch<CntT>& S, uint32_t n_list, uint32_t sws, Counters& ctr) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
 
@@ -331,7 +352,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     uint32_t H = 0;
     for (uint32_t base = 0; base < n_list; base += 32) {
         const uint32_t idx = base + lane;
-        const uint32_t c = idx < n_list ? S.l_cnt[idx] : 0;
+        const uint32_t c = idx < n_list ? (uint32_t)(S.list[idx] & 0xFFFFu) : 0;
         uint32_t inc = c;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -342,6 +363,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
         H += __shfl_sync(FULL_MASK, inc, 31);
     }
     if (lane == 0) S.l_pre[n_list] = H;
+    if (H > S.max_locs) return Q_ESCALATE;
     uint32_t kq = 32;
     while (kq < 2 * H && kq < S.kcap) kq <<= 1;
     const uint32_t mask = kq - 1;
@@ -352,20 +374,28 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     __syncwarp();
 
     // 3. gather the buckets into the hit histogram (window count statistic,
-    // Section 3.2), GB loads per lane in flight; the slots of new locations
+    // Section 3.2): each lane loads GB consecutive locations of the flat
+    // list (all in flight), then inserts them; the slots of new locations
     // are appended to a dense list
     const uint32_t limit = kq - kq / 8;
     uint32_t D = 0;
-    uint32_t bkt = 0;
     for (uint32_t base = 0; base < H; base += 32 * GB) {
+        const uint32_t x0 = base + lane * GB;
+        // bucket of x0: last b with l_pre[b] <= x0
+        uint32_t lo = 0, hi = n_list;
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (S.l_pre[mid] <= x0) lo = mid; else hi = mid;
+        }
+        uint32_t bkt = lo;
         uint64_t v[GB];
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
-            const uint32_t x = base + g * 32 + lane;
+            const uint32_t x = x0 + g;
             v[g] = EMPTY_LOC;
             if (x < H) {
                 while (S.l_pre[bkt + 1] <= x) ++bkt;
-                v[g] = __ldg(db.locs + S.l_off[bkt] + (x - S.l_pre[bkt]));
+                v[g] = __ldg(db.locs + (S.list[bkt] >> 16) + (x - S.l_pre[bkt]));
             }
         }
         bool ok = true;
@@ -374,7 +404,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             int slot = -1;
             if (v[g] != EMPTY_LOC) ok &= hist_insert(S.keys, S.cnts, mask, v[g], slot);
             const uint32_t fresh = __ballot_sync(FULL_MASK, slot >= 0);
-            if (slot >= 0) S.dense[D + __popc(fresh & lt)] = (uint32_t)slot;
+            if (slot >= 0) S.dense[D + __popc(fresh & lt)] = (uint16_t)slot;
             D += __popc(fresh);
         }
         if (__any_sync(FULL_MASK, !ok) || D > limit) return Q_ESCALATE;
@@ -391,7 +421,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
         uint32_t sc = S.cnts[slot];
         const uint32_t room = 0xFFFFFFFFu - (uint32_t)key;  // windows left before the id wraps
         for (uint32_t d = 1; d < sws && d <= room; ++d) sc += hist_count(S.keys, S.cnts, mask, key + d);
-        S.score[i] = sc;
+        S.score[i] = (CntT)sc;
     }
     __syncwarp();
 
@@ -458,11 +488,11 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
 }
 
 // Whole query on one warp with the bucket list in working memory.
-template <int R>
-__device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, const Scratch& S,
-                                             Counters& ctr) {
+template <int R, int KC, class CntT>
+__device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                             const Scratch<CntT>& S, Counters& ctr) {
     uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
-    int r = query_lookup<R, false>(db, Q, q, S, nullptr, n_list, sws, n_feat, n_sect);
+    int r = query_lookup<R, KC>(db, Q, q, S, S.list, n_list, sws, n_feat, n_sect);
     if (r != Q_DONE) return r;
     r = query_score(db, Q, q, S, n_list, sws, ctr);
     if (r == Q_DONE) {
@@ -497,7 +527,7 @@ constexpr uint32_t ESCALATED = 0xFFFFFFFFu;
 // many warps fit on an SM.  Writes each query's bucket list to
 // glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
 // meta; queries that need the large path are queued.
-template <int R>
+template <int R, int KC>
 __global__ void __launch_bounds__(LK_WARPS * 32) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                   uint32_t nq, uint32_t list_cap,
                                                                   uint64_t* __restrict__ glist,
@@ -506,14 +536,14 @@ __global__ void __launch_bounds__(LK_WARPS * 32) k_classify_lookup(ClassifyDb db
                                                                   uint32_t* __restrict__ ovf_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
-    const size_t per_warp = (scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15;
-    const Scratch S = carve(smem + w * per_warp, 0, list_cap, BUF_A, WIN_A);
+    const size_t per_warp = scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
+    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, 0, 0, list_cap, BUF_A, WIN_A);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = gw; i < nq; i += nwarp) {
         const uint32_t q = q0 + i;
         uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
-        int r = query_lookup<R, true>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
+        int r = query_lookup<R, KC>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
         if (r == Q_ESCALATE) {
             if (lane_id() == 0) {
                 ovf_list[atomicAdd(ovf_n, 1u)] = q;
@@ -535,7 +565,7 @@ __global__ void __launch_bounds__(LK_WARPS * 32) k_classify_lookup(ClassifyDb db
 // Main path, part 2 (gather + score + label): one warp per query of the
 // chunk, KA histogram slots per warp in shared memory.
 template <int KA>
-__global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+__global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                      uint32_t nq, uint32_t list_cap,
                                                                      const uint64_t* __restrict__ glist,
                                                                      const uint4* __restrict__ meta,
@@ -544,8 +574,8 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_score(ClassifyDb
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    const size_t per_warp = (scratch_bytes(KA, list_cap, 0) + 15) & ~(size_t)15;
-    const Scratch S = carve(smem + w * per_warp, KA, list_cap, 0, WIN_A);
+    const size_t per_warp = scratch_bytes<uint16_t>(KA, list_cap, 0, 0);
+    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, KA, list_cap, 0, 0, WIN_A);
     Counters ctr;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
@@ -553,11 +583,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_score(ClassifyDb
         const uint4 mt = meta[i];
         if (mt.x == ESCALATED) continue;
         const uint64_t* src = glist + (uint64_t)i * list_cap;
-        for (uint32_t j = lane; j < mt.x; j += 32) {
-            const uint64_t e = __ldg(src + j);
-            S.l_off[j] = e >> 16;
-            S.l_cnt[j] = (uint32_t)(e & 0xFFFFu);
-        }
+        for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
         __syncwarp();
         const uint32_t q = q0 + i;
         if (query_score(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
@@ -574,7 +600,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_score(ClassifyDb
 
 // Large path: queries queued by the shared-memory path, one warp each, with
 // working memory in global scratch.
-template <int R>
+template <int R, int KC>
 __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb db, ClassifyQuery Q,
                                                                    const uint32_t* __restrict__ ovf_list,
                                                                    const uint32_t* __restrict__ ovf_n,
@@ -582,7 +608,8 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
                                                                    unsigned char* __restrict__ scratch,
                                                                    size_t per_warp) {
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const Scratch S = carve(scratch + gw * per_warp, KB_SLOTS, LIST_B, BUF_B, MC_MAX_QUERY_WINDOWS);
+    const Scratch<uint32_t> S =
+        carve<uint32_t>(scratch + gw * per_warp, KB_SLOTS, LIST_B, LIST_B, BUF_B, MC_MAX_QUERY_WINDOWS);
     Counters ctr;
     const uint32_t n = *ovf_n;
     unsigned long long n_large = 0;
@@ -593,7 +620,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
         if (i >= n) break;
         const uint32_t q = ovf_list[i];
         ++n_large;
-        int r = process_query<R>(db, Q, q, S, ctr);
+        int r = process_query<R, KC>(db, Q, q, S, ctr);
         if (r != Q_DONE) {
             write_unclassified(Q, q);
             if (lane_id() == 0) atomicMax(Q.status, DEV_ERR_CAPACITY);
@@ -607,7 +634,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
 constexpr int KA_DEFAULT = 512;
 constexpr uint32_t CHUNK = 1u << 20;  // queries per lookup/score round
 
-template <int R>
+template <int R, int KC>
 cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
     cudaError_t e;
     const uint32_t list_cap = WIN_A * db.sp.s;
@@ -615,9 +642,9 @@ cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
 
-    const size_t smem_l = LK_WARPS * ((scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15);
-    const size_t smem_s = CLS_WARPS * ((scratch_bytes(KA_DEFAULT, list_cap, 0) + 15) & ~(size_t)15);
-    auto kl = k_classify_lookup<R>;
+    const size_t smem_l = LK_WARPS * scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
+    const size_t smem_s = CLS_WARPS * scratch_bytes<uint16_t>(KA_DEFAULT, list_cap, 0, 0);
+    auto kl = k_classify_lookup<R, KC>;
     auto ks = k_classify_score<KA_DEFAULT>;
     if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
         return e;
@@ -653,11 +680,11 @@ cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery
     // large path (persistent warps; exits at once if nothing was queued)
     const uint32_t b_blocks = std::max(1u, (uint32_t)(sms * B_WARPS_PER_SM / CLS_WARPS));
     const uint64_t b_warps = (uint64_t)b_blocks * CLS_WARPS;
-    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     Tmp<unsigned char> scratch(mem, b_warps * per_warp_b, s);
     if (!scratch.ok()) return cudaErrorMemoryAllocation;
     MC_LAUNCH("classify_large", s,
-              k_classify_large<R><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, scratch.ptr,
+              k_classify_large<R, KC><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, scratch.ptr,
                                                                      per_warp_b));
     return cudaGetLastError();
 }
@@ -676,7 +703,7 @@ struct NoAllocLayout {
 NoAllocLayout noalloc_layout(uint32_t n_q, uint32_t sketch_size) {
     NoAllocLayout L;
     const size_t list_cap = (size_t)WIN_A * sketch_size;
-    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     L.ovf = 0;
     L.meta = align256(L.ovf + ((size_t)n_q + 4) * 4);
     L.glist = align256(L.meta + (size_t)n_q * sizeof(uint4));
@@ -685,7 +712,7 @@ NoAllocLayout noalloc_layout(uint32_t n_q, uint32_t sketch_size) {
     return L;
 }
 
-template <int R>
+template <int R, int KC>
 cudaError_t launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch, size_t scratch_len,
                            cudaStream_t s) {
     cudaError_t e;
@@ -695,9 +722,9 @@ cudaError_t launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigne
     int dev = 0, sms = NUM_SMS_HINT;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem_l = LK_WARPS * ((scratch_bytes(0, list_cap, BUF_A) + 15) & ~(size_t)15);
-    const size_t smem_s = CLS_WARPS * ((scratch_bytes(KA_DEFAULT, list_cap, 0) + 15) & ~(size_t)15);
-    auto kl = k_classify_lookup<R>;
+    const size_t smem_l = LK_WARPS * scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
+    const size_t smem_s = CLS_WARPS * scratch_bytes<uint16_t>(KA_DEFAULT, list_cap, 0, 0);
+    auto kl = k_classify_lookup<R, KC>;
     auto ks = k_classify_score<KA_DEFAULT>;
     if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
         return e;
@@ -722,9 +749,9 @@ cudaError_t launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigne
     MC_LAUNCH("classify_lookup", s, kl<<<gl, LK_WARPS * 32, smem_l, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
     MC_LAUNCH("classify_score", s, ks<<<gs, CLS_WARPS * 32, smem_s, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t per_warp_b = (scratch_bytes(KB_SLOTS, LIST_B, BUF_B) + 15) & ~(size_t)15;
+    const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     MC_LAUNCH("classify_large", s,
-              k_classify_large<R><<<NOALLOC_B_WARPS / CLS_WARPS, CLS_WARPS * 32, 0, s>>>(db, Q, ovf, ovf_n, work, large,
+              k_classify_large<R, KC><<<NOALLOC_B_WARPS / CLS_WARPS, CLS_WARPS * 32, 0, s>>>(db, Q, ovf, ovf_n, work, large,
                                                                                        per_warp_b));
     return cudaGetLastError();
 }
@@ -736,18 +763,20 @@ size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size) { return noall
 cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch,
                                    size_t scratch_len, cudaStream_t s) {
     if (Q.n_q == 0) return cudaSuccess;
-    int r = sketch_r_for(db.sp.w);
-    if (r == 4) return launch_noalloc<4>(db, Q, scratch, scratch_len, s);
-    if (r == 8) return launch_noalloc<8>(db, Q, scratch, scratch_len, s);
-    return launch_noalloc<16>(db, Q, scratch, scratch_len, s);
+    const int r = sketch_r_for(db.sp.w);
+    const bool k16 = db.sp.k == 16;
+    if (r == 4) return k16 ? launch_noalloc<4, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<4, 0>(db, Q, scratch, scratch_len, s);
+    if (r == 8) return k16 ? launch_noalloc<8, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<8, 0>(db, Q, scratch, scratch_len, s);
+    return k16 ? launch_noalloc<16, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<16, 0>(db, Q, scratch, scratch_len, s);
 }
 
 cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
     if (Q.n_q == 0) return cudaSuccess;
-    int r = sketch_r_for(db.sp.w);
-    if (r == 4) return launch_all<4>(mem, db, Q, s);
-    if (r == 8) return launch_all<8>(mem, db, Q, s);
-    return launch_all<16>(mem, db, Q, s);
+    const int r = sketch_r_for(db.sp.w);
+    const bool k16 = db.sp.k == 16;
+    if (r == 4) return k16 ? launch_all<4, 16>(mem, db, Q, s) : launch_all<4, 0>(mem, db, Q, s);
+    if (r == 8) return k16 ? launch_all<8, 16>(mem, db, Q, s) : launch_all<8, 0>(mem, db, Q, s);
+    return k16 ? launch_all<16, 16>(mem, db, Q, s) : launch_all<16, 0>(mem, db, Q, s);
 }
 
 }  // namespace mc

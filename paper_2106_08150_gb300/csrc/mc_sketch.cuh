@@ -43,6 +43,24 @@ __device__ __forceinline__ uint32_t window_kmers(uint64_t L, uint64_t ws, const 
     return (uint32_t)(last - ws + 1);
 }
 
+// Encodes 4 bases packed little-endian in x (byte 0 = first base): code8 =
+// their 2-bit codes, first base most significant; inv4 = 1 bit per invalid
+// base, first base most significant.  A byte is a base iff (byte | 0x20)
+// is one of a, c, g, t; each check is done on all four bytes at once.
+__device__ __forceinline__ void encode4(uint32_t x, uint32_t& code8, uint32_t& inv4) {
+    const uint32_t c = ((x >> 1) ^ (x >> 2)) & 0x03030303u;  // code of every byte
+    code8 = (c * 0x40100401u) >> 24;                        // b0<<6 | b1<<4 | b2<<2 | b3
+    // the only letter (lower case) with code c: 'a' + {0, 2, 6, 19}[c]
+    const uint32_t hi = (c >> 1) & 0x01010101u;
+    const uint32_t both = c & (c >> 1) & 0x01010101u;
+    const uint32_t expect = 0x61616161u + (c << 1) + (hi << 1) + both * 11u;
+    const uint32_t d = (x | 0x20202020u) ^ expect;            // zero byte <=> valid base
+    uint32_t z = (d & 0x7F7F7F7Fu) + 0x7F7F7F7Fu;
+    z = ~(z | d | 0x7F7F7F7Fu);                               // bit 7 of each zero byte
+    const uint32_t valid = (((z >> 7) & 0x01010101u) * 0x08040201u) >> 24;  // b0<<3 | ... | b3
+    inv4 = ~valid & 0xFu;
+}
+
 // Bitonic sort of one value per lane across the warp (ascending by lane).
 __device__ __forceinline__ uint32_t warp_sort32(uint32_t v) {
     const uint32_t lane = lane_id();
@@ -74,7 +92,7 @@ __device__ __forceinline__ uint32_t warp_sort32(uint32_t v) {
 // exactly the s smallest distinct hashes.  Otherwise (a few percent of
 // windows, and low-complexity windows) the exact fallback runs: s rounds of
 // a warp min-reduction over locally sorted, de-duplicated lane lists.
-template <int R, int NW, bool GLOBAL_SEQ = true>
+template <int R, int NW, int KC = 0, bool GLOBAL_SEQ = true>
 __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW], const uint64_t (&L)[NW],
                                                   const uint64_t (&ws)[NW], const bool (&active)[NW],
                                                   const SketchParams& p, uint32_t* cand, uint32_t (&feature)[NW],
@@ -83,9 +101,10 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
     constexpr int T = R * (1 + E_MAX);       // bases held by a lane
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
-    const uint32_t kmask_bits = 2 * p.k;
+    const uint32_t k = KC ? (uint32_t)KC : p.k;  // k-mer length (compile-time when KC != 0)
+    const uint32_t kmask_bits = 2 * k;
     const uint64_t cmask = (kmask_bits == 32) ? 0xFFFFFFFFull : ((1ull << kmask_bits) - 1);
-    const uint64_t imask = (1ull << p.k) - 1;
+    const uint64_t imask = (1ull << k) - 1;
     uint32_t h[NW][R];
     uint32_t vmask[NW];  // bit r: h[w][r] is a valid k-mer's hash
     bool fast[NW];
@@ -95,17 +114,23 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
         uint64_t lim = ws[w] + p.w;
         if (lim > L[w]) lim = L[w];
         if (!active[w]) lim = 0;
-        // 1. load and encode R bases
+        // 1. load and encode R bases (bytes past the window's end read as 0,
+        // an invalid base), four at a time
         uint32_t code = 0, inv = 0;
         const uint64_t b0 = ws[w] + (uint64_t)R * lane;
 #pragma unroll
-        for (int i = 0; i < R; ++i) {
-            const uint64_t b = b0 + i;
-            const bool in = b < lim;
-            const uint32_t c = in ? (GLOBAL_SEQ ? (uint32_t)__ldg(seq[w] + b) : (uint32_t)seq[w][b]) : 0u;
-            const uint32_t ok = in ? base_valid(c) : 0u;
-            code = (code << 2) | base_code(c);
-            inv = (inv << 1) | (ok ^ 1u);
+        for (int g = 0; g < R / 4; ++g) {
+            uint32_t x = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const uint64_t b = b0 + 4 * g + i;
+                const uint32_t c = b < lim ? (GLOBAL_SEQ ? (uint32_t)__ldg(seq[w] + b) : (uint32_t)seq[w][b]) : 0u;
+                x |= c << (8 * i);
+            }
+            uint32_t c8, i4;
+            encode4(x, c8, i4);
+            code = (code << 8) | c8;
+            inv = (inv << 4) | i4;
         }
         // 2. bases of the following lanes
         uint64_t comb = code, combinv = inv;
@@ -118,16 +143,17 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
         vmask[w] = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            const uint32_t shift = (uint32_t)(T - r) - p.k;  // >= 0 since T >= R + k - 1
+            const uint32_t shift = (uint32_t)(T - r) - k;  // >= 0 since T >= R + k - 1
             const uint32_t fwd = (uint32_t)((comb >> (2 * shift)) & cmask);
             const bool bad = ((combinv >> shift) & imask) != 0;
             const bool ok = ((uint32_t)R * lane + r < n_k) && !bad;
-            const uint32_t rc = revcomp_code(fwd, p.k);
+            const uint32_t rc = revcomp_code(fwd, k);
             h[w][r] = ok ? hash_h1(fwd < rc ? fwd : rc) : 0xFFFFFFFFu;
             vmask[w] |= (ok ? 1u : 0u) << r;
         }
         // 4. candidates below the cutoff, one per lane in cand[]
-        const uint32_t tau = n_k <= 32 ? 0xFFFFFFFFu : (uint32_t)min((24ull << 32) / n_k, 0xFFFFFFFFull);
+        // (any cutoff is correct; a fast reciprocal is plenty for aiming at ~24)
+        const uint32_t tau = n_k <= 32 ? 0xFFFFFFFFu : __float2uint_rz(__fdividef(24.0f, (float)n_k) * 4294967296.0f);
         uint32_t cmine = 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) cmine += (((vmask[w] >> r) & 1u) && h[w][r] <= tau) ? 1u : 0u;
