@@ -309,25 +309,57 @@ def run_gpu(args, rank, world, local_rank):
 
     total_ms, build_ms, cls_ms = max_over_ranks([total_ms, build_ms, cls_ms], world, dev)
 
-    # end-to-end through the public API with host buffers (pinned), copies timed
+    # end-to-end through the public API with host buffers (pinned), copies
+    # timed every step.  The genome copy is split into chunks on a copy
+    # stream so that adding chunk i overlaps copying chunk i+1, and the
+    # reads are copied while the database is built.
     e2e = None
     if not args.no_e2e:
-        hg, hgo = torch.from_numpy(w.genomes).pin_memory(), torch.from_numpy(w.goffs.view(np.int64)).pin_memory()
+        n_chunks = 8
+        cut = np.searchsorted(w.goffs, np.linspace(0, w.n_bp, n_chunks + 1)).clip(0, w.n_targets)
+        cut[0], cut[-1] = 0, w.n_targets
+        cut = np.unique(cut)
+        chunks = [(int(a), int(b)) for a, b in zip(cut[:-1], cut[1:]) if b > a]
+        hg = torch.from_numpy(w.genomes).pin_memory()
+        hgo = [torch.from_numpy((w.goffs[a:b + 1] - w.goffs[a]).view(np.int64)).pin_memory() for a, b in chunks]
         hr, hro = torch.from_numpy(w.reads).pin_memory(), torch.from_numpy(w.roffs.view(np.int64)).pin_memory()
         hqo = torch.from_numpy(w.qoffs.view(np.int32)).pin_memory()
         hl = torch.empty(nq, dtype=torch.int32).pin_memory()
         hh = torch.empty(nq, dtype=torch.int32).pin_memory()
-        h2d = sum(x.numel() * x.element_size() for x in (hg, hgo, hr, hro, hqo))
+        dg = torch.empty_like(hg, device=dev)
+        dgo = [torch.empty_like(x, device=dev) for x in hgo]
+        dr, dro, dqo = torch.empty_like(hr, device=dev), torch.empty_like(hro, device=dev), torch.empty_like(hqo, device=dev)
+        h2d = sum(x.numel() * x.element_size() for x in [hg, hr, hro, hqo] + hgo)
         d2h = 2 * nq * 4
+        copy_stream = torch.cuda.Stream(device=dev)
 
         def e2e_step():
-            with torch.cuda.stream(stream):
-                dg, dgo = hg.to(dev, non_blocking=True), hgo.to(dev, non_blocking=True)
-                dr, dro, dqo = hr.to(dev, non_blocking=True), hro.to(dev, non_blocking=True), hqo.to(dev, non_blocking=True)
-            step(dg, dgo, dr, dro, dqo)
+            evs = []
+            with torch.cuda.stream(copy_stream):
+                for (a, b), ho, do in zip(chunks, hgo, dgo):
+                    lo, hi = int(w.goffs[a]), int(w.goffs[b])
+                    dg[lo:hi].copy_(hg[lo:hi], non_blocking=True)
+                    do.copy_(ho, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                    evs.append(ev)
+                dr.copy_(hr, non_blocking=True)
+                dro.copy_(hro, non_blocking=True)
+                dqo.copy_(hqo, non_blocking=True)
+                ev_reads = torch.cuda.Event()
+                ev_reads.record(copy_stream)
+            db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+            for (a, b), do, ev in zip(chunks, dgo, evs):
+                stream.wait_event(ev)
+                lo = int(w.goffs[a])
+                db.add_targets(dg[lo:], do, w.taxon_of_target[a:b])
+            db.finalize()
+            stream.wait_event(ev_reads)
+            mc.mc_classify(db.handle, cp, w.n_seq, dr, dro, nq, dqo, label, hits, top, stream=stream)
             with torch.cuda.stream(stream):
                 hl.copy_(label, non_blocking=True)
                 hh.copy_(hits, non_blocking=True)
+            db.free()
             stream.synchronize()
 
         for _ in range(args.warmup):

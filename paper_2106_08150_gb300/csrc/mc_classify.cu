@@ -146,7 +146,7 @@ __host__ __device__ constexpr size_t scratch_bytes(uint32_t kcap, uint32_t list_
                                                    uint32_t buf_cap) {
     return align16((size_t)kcap * 8) + 2 * align16((size_t)kcap * sizeof(CntT)) + align16((size_t)kcap * 2) +
            align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + align16((size_t)feat_cap * 4) +
-           (feat_cap ? align16(4 * 32 * SK_NW) : 0) + align16(buf_cap);
+           (feat_cap ? align16(4 * 32 * SK_NW) : 0) + (buf_cap ? align16(buf_cap + 16) : 0);
 }
 
 // Carves a Scratch out of `base` (16-byte aligned), in scratch_bytes order.
@@ -247,14 +247,27 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     }
     boff -= L;
 
-    // 1a. stage the query's bases in working memory (all loads in flight)
-    for (uint32_t i = 0; i < nm; ++i) {
-        const uint64_t oi = __shfl_sync(FULL_MASK, o, i);
-        const uint64_t Li = __shfl_sync(FULL_MASK, L, i);
-        const uint64_t bi = __shfl_sync(FULL_MASK, boff, i);
-        const uint8_t* src = Q.seq + oi;
-#pragma unroll 4
-        for (uint64_t b = lane; b < Li; b += 32) S.buf[bi + b] = __ldg(src + b);
+    // 1a. stage the query's bases in working memory.  The mates of a query
+    // are consecutive sequences, so this is one contiguous range; it is
+    // copied in 16-byte chunks aligned in memory (one vector load per chunk,
+    // all in flight), placed at the same offset mod 16 in the buffer, with
+    // the partial chunks at both ends copied byte by byte.
+    const uint64_t start = __shfl_sync(FULL_MASK, o, 0);
+    const uintptr_t first = (uintptr_t)(Q.seq + start);
+    const uint32_t shift = (uint32_t)(first & 15u);
+    {
+        const uintptr_t a0 = first - shift;
+        const uint64_t n_chunks = (shift + span_sum + 15) / 16;
+        for (uint64_t c = lane; c < n_chunks; c += 32) {
+            const uintptr_t cs = a0 + 16 * c;
+            if (cs >= first && cs + 16 <= first + span_sum) {
+                *reinterpret_cast<uint4*>(S.buf + 16 * c) = __ldg(reinterpret_cast<const uint4*>(cs));
+            } else {
+                const uintptr_t lo = cs > first ? cs : first;
+                const uintptr_t hi = cs + 16 < first + span_sum ? cs + 16 : first + span_sum;
+                for (uintptr_t b = lo; b < hi; ++b) S.buf[b - a0] = __ldg(reinterpret_cast<const uint8_t*>(b));
+            }
+        }
     }
     __syncwarp();
 
@@ -278,7 +291,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
                     jn = 0;
                     nw_mi = __shfl_sync(FULL_MASK, nw, mi & 31);
                 }
-                sq[i] = S.buf + __shfl_sync(FULL_MASK, boff, mi & 31);
+                sq[i] = S.buf + shift + __shfl_sync(FULL_MASK, boff, mi & 31);
                 Ls[i] = act[i] ? __shfl_sync(FULL_MASK, L, mi & 31) : 0;
                 wss[i] = jn * p.stride;
                 if (act[i]) ++jn;
@@ -301,12 +314,15 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
         uint32_t hk[LB];
         uint64_t pos[LB];
         uint4 e[LB];
+        uint4 e2[LB];
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
             const uint32_t idx = base + b * 32 + lane;
             hk[b] = idx < F ? hash_h2(S.feat[idx]) : 0u;
             pos[b] = db.log_t >= 32 ? hk[b] : (hk[b] >> (32 - db.log_t));
+            // the home slot and the next one (the table has 2 slots of padding)
             e[b] = idx < F ? __ldg(db.table + pos[b]) : make_uint4(0, 0, 0, 0);
+            e2[b] = idx < F ? __ldg(db.table + pos[b] + 1) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
@@ -315,7 +331,8 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
             uint64_t off = 0;
             if (idx < F) {
                 uint4 x = e[b];
-                for (uint32_t d = 1; x.y != 0 && x.x < hk[b] && d <= db.max_probe; ++d) x = __ldg(db.table + pos[b] + d);
+                if (x.y != 0 && x.x < hk[b] && db.max_probe >= 1) x = e2[b];
+                for (uint32_t d = 2; x.y != 0 && x.x < hk[b] && d <= db.max_probe; ++d) x = __ldg(db.table + pos[b] + d);
                 if (x.y != 0 && x.x == hk[b]) {
                     c = x.y;
                     off = (uint64_t)x.z | ((uint64_t)x.w << 32);
@@ -425,30 +442,31 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     }
     __syncwarp();
 
-    // 5. top m with one candidate per target (Section 3.2 / 4.6): m rounds
-    // of warp arg-max, excluding the targets already chosen; the label is
-    // folded as the candidates come (hit threshold of Section 5.5, LCA of
-    // the close candidates of Section 3.2)
+    // 5. top m with one candidate per target (Section 3.2 / 4.6): rounds of
+    // warp arg-max; the winner's target is excluded from later rounds by
+    // zeroing the scores of its entries.  The label is folded as the
+    // candidates come (hit threshold of Section 5.5, LCA of the close
+    // candidates of Section 3.2).  Later rounds only give lower scores, so
+    // unless the full top-m list is requested the rounds stop once the
+    // query is unclassified or the best remaining score is not close.
     const int m = (int)Q.m;
     Cand mine = Cand{0, 0xFFFFFFFFu, 0, 0};
     uint32_t label = NO_TAXON, hits = 0, top = 0xFFFFFFFFu;
     uint64_t bar = 0;
-    uint32_t won[MAX_M];
-#pragma unroll
-    for (int i = 0; i < MAX_M; ++i) won[i] = 0xFFFFFFFFu;
-#pragma unroll
-    for (int r = 0; r < MAX_M; ++r) {
-        if (r >= m) break;
+    uint32_t prev_t = 0xFFFFFFFFu;
+    for (int r = 0; r < m; ++r) {
         Cand best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
         for (uint32_t i = lane; i < D; i += 32) {
+            uint32_t sc = S.score[i];
+            if (sc == 0) continue;
             const uint64_t key = S.keys[S.dense[i]];
             const uint32_t t = (uint32_t)(key >> 32);
-            bool excl = false;
-#pragma unroll
-            for (int x = 0; x < MAX_M; ++x)
-                if (x < r && won[x] == t) excl = true;
-            const Cand c = Cand{S.score[i], t, (uint32_t)key, 0};
-            if (!excl && better(c, best)) best = c;
+            if (t == prev_t) {
+                S.score[i] = 0;
+                continue;
+            }
+            const Cand c = Cand{sc, t, (uint32_t)key, 0};
+            if (better(c, best)) best = c;
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) {
@@ -459,7 +477,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             if (better(x, best)) best = x;
         }
         if (best.score == 0) break;
-        won[r] = best.t;
+        prev_t = best.t;
         if (Q.cands) {
             // last window of the range present in the histogram
             uint32_t j1 = best.j0;
@@ -469,8 +487,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
                 if ((uint32_t)(key >> 32) == best.t && j >= best.j0 && (uint64_t)j < (uint64_t)best.j0 + sws && j > j1)
                     j1 = j;
             }
-            j1 = __reduce_max_sync(FULL_MASK, j1);
-            best.j1 = j1;
+            best.j1 = __reduce_max_sync(FULL_MASK, j1);
         }
         if ((int)lane == r) mine = best;
         if (r == 0) {
@@ -478,10 +495,14 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             top = best.t;
             bar = (uint64_t)(100 - Q.band) * hits;
             if (hits >= Q.hits_min) label = top < db.n_targets ? db.taxon_of_target[top] : NO_TAXON;
+            else if (!Q.cands) break;
         } else if (hits >= Q.hits_min && 100ull * best.score >= bar) {
             const uint32_t tx = best.t < db.n_targets ? db.taxon_of_target[best.t] : NO_TAXON;
             label = lca2(db, label, tx);
+        } else if (!Q.cands) {
+            break;
         }
+        __syncwarp();
     }
     write_result(Q, q, label, hits, top, mine);
     return Q_DONE;
@@ -528,7 +549,7 @@ constexpr uint32_t ESCALATED = 0xFFFFFFFFu;
 // glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
 // meta; queries that need the large path are queued.
 template <int R, int KC>
-__global__ void __launch_bounds__(LK_WARPS * 32) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+__global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                   uint32_t nq, uint32_t list_cap,
                                                                   uint64_t* __restrict__ glist,
                                                                   uint4* __restrict__ meta,
