@@ -4,7 +4,7 @@
 One step = the whole hot path over one batch of synthetic input: build the
 database from the reference genomes (sketch, sort, cap, condensed layout)
 and classify every read pair against it (the paper's on-the-fly mode,
-Section 5.3).  The default workload is the mid-size configuration: 1,000
+Section 6.3).  The default workload is the mid-size configuration: 1,000
 genomes (~3.4 Gbp) in 100 genera, 10M paired-end 2x150 bp reads.
 
 Prints one JSON line.  `value` is read pairs classified per second over the
@@ -49,6 +49,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-genera", type=int, default=2)
     ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
+    ap.add_argument("--batches", type=int, default=256,
+                    help="mixed-length query batches of the batched-classification section (0 = skip)")
     return ap.parse_args()
 
 
@@ -56,11 +58,11 @@ def parse_args():
 def make_workload(name: str, rank: int):
     import synth
     if name == "mid":
-        w = synth.config1(seed=1001)
+        w = synth.mid_workload(seed=1001)
     elif name == "small":
-        w = synth.config1(seed=1001, n_families=1, genera_per_family=10, n_pairs=1_000_000)
+        w = synth.mid_workload(seed=1001, n_families=1, genera_per_family=10, n_pairs=1_000_000)
     else:
-        w = synth.config1(seed=1001, n_families=1, genera_per_family=2, len_scale=0.1, n_pairs=50_000)
+        w = synth.mid_workload(seed=1001, n_families=1, genera_per_family=2, len_scale=0.1, n_pairs=50_000)
     if rank:
         # replicas classify their own reads against the same database
         reads, roffs, qoffs, truth = synth.simulate_reads(
@@ -422,7 +424,107 @@ def run_gpu(args, rank, world, local_rank):
         "clocks": clk,
         "generation_s": round(t_gen, 1),
     }
+    if args.batches and world == 1:
+        out["batched"] = run_batched(args, w, dev, stream)
     return out, w
+
+
+# ------------------------------------------------------ batched queries
+def run_batched(args, w, dev, stream):
+    """Mixed-length query batches against the resident database: one
+    mc_classify call per batch, one launch set over all batches
+    (mc_classify_batches), a CUDA-graph plan, and the plan with the
+    autotuner's launch shape.  All four must give identical outputs."""
+    import torch
+    import synth
+    from paper_2106_08150_gb300 import mc
+
+    t0 = time.time()
+    batches = synth.mixed_batches(1003, w.genomes, w.goffs, n_batches=args.batches)
+    gen_s = time.time() - t0
+    db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+    db.add_targets(torch.from_numpy(w.genomes).to(dev), torch.from_numpy(w.goffs.view(np.int64)).to(dev),
+                   w.taxon_of_target)
+    db.finalize()
+    cp = mc.classify_params(**dict(w.cls_params, max_insert=0))
+
+    def t(a):
+        a = np.ascontiguousarray(a)
+        a = a.view(np.int64) if a.dtype == np.uint64 else a.view(np.int32) if a.dtype == np.uint32 else a
+        return torch.from_numpy(a).to(dev)
+
+    ins, ref, out = [], [], []
+    for reads, roffs, qoffs, _ in batches:
+        nq = len(qoffs) - 1
+        ins.append((len(roffs) - 1, nq, t(reads) if len(reads) else torch.zeros(1, dtype=torch.uint8, device=dev),
+                    t(roffs), t(qoffs)))
+        ref.append([torch.empty(max(1, nq), dtype=torch.int32, device=dev) for _ in range(3)])
+        out.append([torch.empty(max(1, nq), dtype=torch.int32, device=dev) for _ in range(3)])
+    descs = [mc.batch(n_seq, seq, offs, qo, *o) for (n_seq, nq, seq, offs, qo), o in zip(ins, out)]
+    total_q = sum(x[1] for x in ins)
+    total_mates = sum(x[0] for x in ins)
+    total_bp = sum(int(b[1][-1]) for b in batches)
+    torch.cuda.synchronize()
+
+    def per_batch(outs):
+        for (n_seq, nq, seq, offs, qo), o in zip(ins, outs):
+            if nq:
+                mc.mc_classify(db.handle, cp, n_seq, seq, offs, nq, qo, *o, stream=stream)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        n0 = mc.mc_kernel_launches()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / args.steps
+        return {"mreads_s": round(total_q / (ms * 1e-3) / 1e6, 3), "ms": round(ms, 3),
+                "launches": (mc.mc_kernel_launches() - n0) // args.steps}
+
+    def same():
+        mc.mc_classify_status(db.handle, stream)
+        return all(bool(torch.equal(x[:n], y[:n])) for (_, n, *_r), rx, ox in zip(ins, ref, out)
+                   for x, y in zip(rx, ox))
+
+    res = {}
+    res["per_batch"] = timed(lambda: per_batch(ref))
+    res["one_launch_set"] = timed(lambda: mc.mc_classify_batches(db.handle, cp, descs, stream=stream))
+    ok = same()
+    plan = mc.Plan(db.handle, cp, len(descs), total_q)
+    res["graph"] = timed(lambda: plan.run(descs, stream))
+    ok = ok and same()
+    plan.free()
+    # autotune on the leading batches (up to 2^20 queries)
+    sample, n = [], 0
+    for d, x in zip(descs, ins):
+        if n + x[1] > (1 << 20):
+            break
+        sample.append(d)
+        n += x[1]
+    t0 = time.time()
+    best, rec = mc.mc_autotune(db.handle, cp, sample, reps=3)
+    tune_s = time.time() - t0
+    plan = mc.Plan(db.handle, cp, len(descs), total_q, best)
+    res["graph_tuned"] = timed(lambda: plan.run(descs, stream))
+    ok = ok and same()
+    plan.free()
+    db.free()
+    sizes = [x[1] for x in ins]
+    return {
+        "workload": f"{len(batches)} batches, sizes lognormal(median 5e4, sigma 1) in [1e3, 2e6], read length "
+                    f"U(50,300), half single-end half pairs, against the {w.name} database",
+        "batches": len(batches), "queries": total_q, "mates": total_mates, "bases": total_bp,
+        "batch_size_min": int(min(sizes)), "batch_size_max": int(max(sizes)),
+        "unit": "Mreads/s", **res, "identical_results": bool(ok), "tuning": best.as_dict(),
+        "autotune_s": round(tune_s, 2), "autotune_sample_queries": n,
+        "autotune_times_ms": [[r[0], r[1], round(r[2], 4)] for r in rec],
+        "generation_s": round(gen_s, 1),
+    }
 
 
 # ------------------------------------------------------------ CPU arms

@@ -4,10 +4,10 @@
  * MetaCache-GPU (Kobus et al., arXiv 2106.08150) classifies short DNA reads
  * against a database of reference genomes ("targets").  The database maps
  * minhash features of reference windows to the locations (target, window)
- * they occur in (Section 3.1); classification sketches each read, looks its
+ * they occur in (Section 4.1); classification sketches each read, looks its
  * features up, accumulates the hit locations and labels the read by its top
  * candidate or by the lowest common ancestor (LCA) of the close candidates
- * in a taxonomy (Section 3.2).  Every step of both halves runs in CUDA
+ * in a taxonomy (Section 4.2).  Every step of both halves runs in CUDA
  * kernels of this library.
  *
  * Conventions for every function:
@@ -20,7 +20,7 @@
  *    the caller and only read during the call (stream-ordered for device
  *    inputs); outputs are caller-allocated.
  *  - Sequences are ASCII bytes; A/C/G/T in either case are bases, every
- *    other byte is an invalid base (Section 4.2 step 1: "N" and friends).
+ *    other byte is an invalid base (Section 5.2 step 1: "N" and friends).
  *  - Streams are cudaStream_t values passed as void* (NULL = legacy stream).
  *
  * Build and query order: mc_db_create -> mc_db_add_targets (one or more
@@ -67,25 +67,25 @@ typedef enum mc_status {
 
 typedef struct mc_db mc_db; /* opaque; owns every device allocation it makes */
 
-/* Database parameters, fixed at mc_db_create (Section 4.2: defaults k = 16,
+/* Database parameters, fixed at mc_db_create (Section 5.2: defaults k = 16,
  * s = 16, window 127 with overlap k-1; the paper's GPU kernels also require
  * stride % 4 == 0 and w <= 128, which this library does not). */
 typedef struct mc_db_params {
     uint32_t k;             /* k-mer length, 1..16 */
-    uint32_t sketch_size;   /* s: features per window, 1..32 (Section 3.1) */
-    uint32_t window_len;    /* w: bases per window, k..k+511 (Section 3.1) */
-    uint32_t window_stride; /* distance of window starts, 1..w-k+1 (Section 3.1: w-k+1) */
-    uint32_t bucket_cap;    /* locations kept per feature, 1..65535 (Section 3.1: 254);
+    uint32_t sketch_size;   /* s: features per window, 1..32 (Section 4.1) */
+    uint32_t window_len;    /* w: bases per window, k..k+511 (Section 4.1) */
+    uint32_t window_stride; /* distance of window starts, 1..w-k+1 (Section 4.1: w-k+1) */
+    uint32_t bucket_cap;    /* locations kept per feature, 1..65535 (Section 4.1: 254);
                                the smallest (target, window) pairs are kept */
     uint32_t reserved;      /* must be 0 */
     uint64_t max_locations; /* optional capacity hint (0 = none) */
     uint64_t hbm_budget;    /* bytes the database may hold on the device (0 = no limit) */
 } mc_db_params;
 
-/* Classification parameters, per mc_classify call (Section 3.2). */
+/* Classification parameters, per mc_classify call (Section 4.2). */
 typedef struct mc_classify_params {
-    uint32_t max_candidates; /* m: top hits kept, 1..8 (Section 3.2: usually 2..4) */
-    uint32_t hits_min;       /* minimum top score to classify (Section 5.5: hit threshold) */
+    uint32_t max_candidates; /* m: top hits kept, 1..8 (Section 4.2: usually 2..4) */
+    uint32_t hits_min;       /* minimum top score to classify (Section 6.5: hit threshold) */
     uint32_t lca_band_pct;   /* 0..100: candidates with score >= (100-band)% of the top score
                                 are "close"; one close candidate -> its taxon, several -> LCA */
     uint32_t max_insert;     /* read pairs: sliding-window span is max(len1+len2, max_insert);
@@ -111,17 +111,17 @@ int mc_set_allocator(const mc_allocator* allocator);
  *  params : host; validated as documented in mc_db_params.
  *  n_taxa : number of taxonomy nodes (>= 1); taxon ids are 0..n_taxa-1.
  *  parent : host, n_taxa entries; parent[x] is x's parent, a root has
- *           parent[x] == x (NCBI-style tree, Section 3.1).  Cycles are
+ *           parent[x] == x (NCBI-style tree, Section 4.1).  Cycles are
  *           rejected with MC_ERR_ARG.
  *  stream : stream for every build-side call of this database.
  *  out    : host; receives the handle.
- * The per-taxon lineage table used for constant-time LCA (Section 3.2) is
+ * The per-taxon lineage table used for constant-time LCA (Section 4.2) is
  * built on the device here.  Synchronises `stream`. */
 int mc_db_create(const mc_db_params* params, uint32_t n_taxa, const uint32_t* parent, void* stream,
                  mc_db** out);
 
-/* Adds targets (reference sequences) to the database (Section 3.1 build
- * phase, Section 4.2 build pipeline: encode, canonical k-mers, h1, sketch,
+/* Adds targets (reference sequences) to the database (Section 4.1 build
+ * phase, Section 5.2 build pipeline: encode, canonical k-mers, h1, sketch,
  * insert).
  *  n_targets : number of sequences in this call (may be 0).
  *  seq       : device, ASCII bases of all targets back to back.
@@ -139,13 +139,13 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
                       const uint32_t* taxon, uint32_t* first_target_id);
 
 /* Publishes everything added so far in the condensed query layout
- * (Section 3.2 / 4.1: all buckets in one contiguous array, a single-value
+ * (Section 4.2 / 5.1: all buckets in one contiguous array, a single-value
  * hash table from feature to bucket).  Each feature keeps its bucket_cap
  * smallest locations, sorted ascending.  Idempotent; required before
  * mc_classify.  Synchronises the database stream. */
 int mc_db_finalize(mc_db* db);
 
-/* Classifies queries (Section 3.2 query phase, Section 4.2 query steps 1-8).
+/* Classifies queries (Section 4.2 query phase, Section 5.2 query steps 1-8).
  *  params    : host.
  *  n_seq     : number of sequences (mates) in seq.
  *  seq       : device, ASCII bases of all mates back to back.
@@ -193,6 +193,95 @@ int mc_classify_noalloc(const mc_db* db, const mc_classify_params* params, uint3
                         const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                         uint32_t* hits, uint32_t* top_target, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batched classification of mixed-length query batches.
+ *
+ * The paper pushes reads through its GPU pipeline one batch at a time,
+ * with memory allocated for one batch (Section 5.2), and bundles the
+ * kernels of its segmented sort in a CUDA graph (Section 5.5).  Here a
+ * whole set of batches -- each with its own buffers, read
+ * lengths and single/paired mix -- goes through one set of kernel launches
+ * (lookup, score, large path), or through one replay of a CUDA graph of
+ * that launch set (mc_plan).  Results equal those of one mc_classify call
+ * per batch, bit for bit. */
+
+/* One batch of queries: the arguments of mc_classify for one call. */
+typedef struct mc_batch {
+    uint32_t n_seq;          /* sequences (mates) of the batch */
+    uint32_t n_queries;      /* queries of the batch */
+    const char* seq;         /* device, ASCII bases of all mates */
+    const uint64_t* offs;    /* device, n_seq+1 byte offsets into seq */
+    const uint32_t* qoffs;   /* device, n_queries+1 mate indices (as in mc_classify) */
+    uint32_t* label;         /* device out, n_queries */
+    uint32_t* hits;          /* device out, n_queries */
+    uint32_t* top_target;    /* device out, n_queries (nullable) */
+} mc_batch;
+
+/* Launch shape of the classification kernels.  Every setting gives the same
+ * results; only the speed differs.  Zero fields take the defaults.
+ *  hist_slots  : shared-memory histogram slots per query (the on-chip tile
+ *                that replaces the paper's sort tile): 256, 512 (default)
+ *                or 1024.  Queries whose distinct locations do not fit go
+ *                to the large path.
+ *  probe_batch : feature-table probes in flight per lane (32 lanes probe
+ *                together): 2, 4 (default) or 8.
+ *  gather_batch: bucket-location loads in flight per lane: 4, 8 (default)
+ *                or 16.
+ *  lookup_warps: warps per CTA of the lookup kernel: 4 or 8 (default).
+ *  score_warps : warps per CTA of the score kernel: 2 or 4 (default).
+ * One warp carries one query in every kernel. */
+typedef struct mc_tuning {
+    uint32_t hist_slots;
+    uint32_t probe_batch;
+    uint32_t gather_batch;
+    uint32_t lookup_warps;
+    uint32_t score_warps;
+} mc_tuning;
+
+/* Sets the launch shape used by later classify calls on this database that
+ * take no explicit tuning (mc_classify, mc_classify_batches with NULL).
+ * NULL restores the defaults.  MC_ERR_ARG for a value outside the sets
+ * above. */
+int mc_db_set_tuning(mc_db* db, const mc_tuning* tuning);
+
+/* Classifies n_batches batches (host array of descriptors; device buffers)
+ * in one launch set on `stream`.  tuning: NULL = the database's.  Per-batch
+ * limits as in mc_classify; the total query count must be below 2^32.
+ * Asynchronous; errors as mc_classify (mc_classify_status). */
+int mc_classify_batches(const mc_db* db, const mc_classify_params* params, const mc_tuning* tuning,
+                        uint32_t n_batches, const mc_batch* batches, void* stream);
+
+/* A reusable classification plan: scratch memory for up to max_queries
+ * queries in up to max_batches batches, and a CUDA graph of the whole
+ * launch set, captured once.  mc_plan_run replays the graph for a new set
+ * of batches: it copies the batch descriptors (host, n_batches) to the
+ * device and launches the graph on `stream`.  A plan is re-captured
+ * automatically when its database has been finalized again since.  Runs of
+ * one plan are serialised (a run waits on the host for the previous run's
+ * descriptor copy).  MC_ERR_CAPACITY if a run exceeds max_batches or
+ * max_queries.  mc_plan_free synchronises and releases the plan. */
+typedef struct mc_plan mc_plan;
+int mc_plan_create(const mc_db* db, const mc_classify_params* params, const mc_tuning* tuning,
+                   uint32_t max_batches, uint32_t max_queries, mc_plan** out);
+int mc_plan_run(mc_plan* plan, uint32_t n_batches, const mc_batch* batches, void* stream);
+int mc_plan_kernels(const mc_plan* plan);  /* kernel launches per run (graph kernel nodes) */
+void mc_plan_free(mc_plan* plan);
+
+/* Autotuner: times every lookup setting (probe_batch x lookup_warps) and
+ * every score setting (hist_slots x gather_batch x score_warps, with the
+ * large path it leaves) on the given sample batches (at most 2^20 queries
+ * in total), `reps` times each, and writes the fastest setting to *best.
+ * If `times` is not NULL it receives up to max_times records
+ * {setting, kernel ms (mean over reps)} in the order tried; *n_times (if
+ * not NULL) the number tried.  Synchronises the database stream. */
+typedef struct mc_tuning_time {
+    mc_tuning tuning;
+    uint32_t stage;  /* 0 = lookup setting, 1 = score setting */
+    float ms;
+} mc_tuning_time;
+int mc_autotune(const mc_db* db, const mc_classify_params* params, uint32_t n_batches, const mc_batch* batches,
+                uint32_t reps, mc_tuning* best, mc_tuning_time* times, uint32_t max_times, uint32_t* n_times);
+
 /* Synchronises `stream` and returns (and clears) the first device-detected
  * error of earlier mc_classify calls of this database (MC_ERR_CAPACITY for
  * a query with more distinct hit locations than the largest per-query
@@ -201,6 +290,22 @@ int mc_classify_status(const mc_db* db, void* stream);
 
 /* Releases the database and all its device memory (synchronises its stream). */
 void mc_db_free(mc_db* db);
+
+/* Writes the finalized database to a file (Section 4.1: the database and
+ * the taxonomy are written to the file system after the build; Section 4.2:
+ * a saved database is loaded in the condensed layout).  The file holds the
+ * parameters, the taxonomy (parent array), the targets' taxa and window
+ * bases, the location array and the feature table.  MC_ERR_STATE if
+ * additions are pending (call mc_db_finalize first); MC_ERR_ARG if the
+ * file cannot be written.  Synchronises the database stream. */
+int mc_db_save(const mc_db* db, const char* path);
+
+/* Reads a database written by mc_db_save into a new handle (device memory
+ * from the current allocator, build-side calls on `stream`).  The loaded
+ * database can be classified against at once and extended like any other.
+ * MC_ERR_ARG if the file is missing, truncated or not a database of this
+ * format version. */
+int mc_db_load(const char* path, void* stream, mc_db** out);
 
 /* ---------------------------------------------------------------------
  * Inspection and test exports.
@@ -212,7 +317,9 @@ typedef struct mc_db_stats_t {
     uint64_t n_pairs;           /* (feature, location) pairs offered */
     uint64_t n_keys;            /* distinct features */
     uint64_t n_locations;       /* locations stored after the cap */
-    uint64_t overflow_keys;     /* features that had more than bucket_cap locations */
+    uint64_t overflow_keys;     /* features that had more than bucket_cap locations (after a
+                                   live extension: counted over the kept locations of the
+                                   earlier targets plus those of the new ones) */
     uint64_t dropped_locations; /* n_pairs - n_locations */
     uint64_t table_slots;       /* slots of the feature table */
     uint64_t max_probe;         /* longest probe distance in the feature table */
@@ -235,13 +342,13 @@ int mc_db_stats(const mc_db* db, mc_db_stats_t* out);
 int mc_db_dump(const mc_db* db, uint64_t key_lo, uint64_t key_hi, uint64_t max_keys, uint64_t max_locs,
                uint32_t* keys, uint32_t* counts, uint64_t* locs, uint64_t* n_keys, uint64_t* n_locs);
 
-/* Window layout of sequences (Section 3.1): win_offs (device out, n_seq+1)
+/* Window layout of sequences (Section 4.1): win_offs (device out, n_seq+1)
  * receives the exclusive prefix sum of ceil((L-k+1)/stride) (0 if L < k).
  * Asynchronous on `stream`. */
 int mc_window_offsets(const mc_db_params* params, uint32_t n_seq, const uint64_t* offs, uint64_t* win_offs,
                       void* stream);
 
-/* Minhash sketches of every window (Section 2, Section 4.2 steps 1-3):
+/* Minhash sketches of every window (Section 2, Section 5.2 steps 1-3):
  * sketch[w * sketch_size + i] (device out) = i-th smallest distinct h1
  * value of window w's valid canonical k-mers, 0 past counts[w] (device
  * out, n_windows).  win_offs from mc_window_offsets; n_windows =
@@ -264,7 +371,7 @@ int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_
 
 /* ---------------------------------------------------------------------
  * Tracing and launch accounting (no counterpart in the paper beyond its
- * per-stage breakdown, Section 5.4).
+ * per-stage breakdown, Section 6.4).
  * ------------------------------------------------------------------- */
 
 /* Enables (1) or disables (0) tracing: each kernel launch of the library is

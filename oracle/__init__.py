@@ -1,7 +1,7 @@
 """CPU oracle for the MetaCache-GPU hot path -- TEST INFRASTRUCTURE ONLY.
 
 `oracle.cpp` states, in plain C++17, what database build and read
-classification compute (arXiv 2106.08150, Sections 2, 3.1, 3.2 and 4.2-4.6).
+classification compute (arXiv 2106.08150, Sections 2, 4.1, 4.2 and 5.2-5.6).
 Only the tests, `__graft_entry__.smoke()` and the CPU-baseline / reference
 legs of `bench.py` may use it.  The CUDA product path never imports it, and
 the two share no code.

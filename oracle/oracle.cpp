@@ -31,14 +31,14 @@ namespace {
 const uint32_t NO_TAXON = 0xFFFFFFFFu;
 
 struct Params {
-    uint32_t k;       // k-mer length (Section 4.2: default 16)
-    uint32_t s;       // sketch size (Section 4.2: default 16)
-    uint32_t w;       // window length (Section 3.1: windows of size w)
-    uint32_t stride;  // window stride (Section 3.1: overlap k-1, stride w-k+1)
-    uint32_t cap;     // locations kept per feature (Section 3.1: 254 by default)
+    uint32_t k;       // k-mer length (Section 5.2: default 16)
+    uint32_t s;       // sketch size (Section 5.2: default 16)
+    uint32_t w;       // window length (Section 4.1: windows of size w)
+    uint32_t stride;  // window stride (Section 4.1: overlap k-1, stride w-k+1)
+    uint32_t cap;     // locations kept per feature (Section 4.1: 254 by default)
 };
 
-// Section 4.2 step 1 / Section 4.3: the regular bases A, C, G, T get a
+// Section 5.2 step 1 / Section 5.3: the regular bases A, C, G, T get a
 // 2-bit code; everything else (N and other ambiguity letters) is invalid.
 // Lower case is treated like upper case.
 int base_code(uint8_t c) {
@@ -51,7 +51,7 @@ int base_code(uint8_t c) {
     }
 }
 
-// h1 (Section 3.1: "a hash function h1 is applied" to each canonical k-mer;
+// h1 (Section 4.1: "a hash function h1 is applied" to each canonical k-mer;
 // the paper does not name it).  Reading: the "lowbias32" 32-bit integer
 // mixer from C. Wellons' hash-prospector (public domain): two rounds of
 // xor-shift and odd multiply, a bijection on 32-bit words.
@@ -64,7 +64,7 @@ uint32_t h1(uint32_t x) {
     return x;
 }
 
-// Section 3.1: a sequence is divided into windows of w bases that overlap by
+// Section 4.1: a sequence is divided into windows of w bases that overlap by
 // k-1 bases, i.e. window j starts at j*stride.  Window j's k-mers start at
 // positions j*stride .. min(j*stride + w - k, L - k).  A window exists while
 // its first k-mer fits, so there are ceil((L-k+1)/stride) windows (none if
@@ -94,12 +94,12 @@ bool kmer_codes(const uint8_t* x, uint64_t pos, uint32_t k, uint32_t* fwd, uint3
     return true;
 }
 
-// Section 3.1 (canonical k-mers): the smaller of a k-mer's code and its
+// Section 4.1 (canonical k-mers): the smaller of a k-mer's code and its
 // reverse complement's code, so that a read and its reverse complement
 // produce the same k-mers.
 uint32_t canonical(uint32_t fwd, uint32_t rc) { return fwd < rc ? fwd : rc; }
 
-// Section 2 and Section 3.1: the minhash sketch of a window is the s smallest
+// Section 2 and Section 4.1: the minhash sketch of a window is the s smallest
 // distinct hash values of its valid canonical k-mers (repeated k-mers count
 // once, as in the Section 2 example where ACTG occurs twice).
 std::vector<uint32_t> sketch_window(const uint8_t* x, uint64_t L, uint64_t j, const Params& p) {
@@ -108,7 +108,7 @@ std::vector<uint32_t> sketch_window(const uint8_t* x, uint64_t L, uint64_t j, co
     uint64_t last = std::min<uint64_t>(first + p.w - p.k, L - p.k);
     for (uint64_t pos = first; pos <= last; ++pos) {
         uint32_t f, r;
-        if (!kmer_codes(x, pos, p.k, &f, &r)) continue;  // Section 4.2 step 2: valid k-mers only
+        if (!kmer_codes(x, pos, p.k, &f, &r)) continue;  // Section 5.2 step 2: valid k-mers only
         hashes.push_back(h1(canonical(f, r)));
     }
     std::sort(hashes.begin(), hashes.end());
@@ -127,7 +127,7 @@ struct DB {
     uint64_t n_windows = 0;
     uint64_t n_pairs = 0;       // (feature, location) pairs offered to the table
     uint64_t overflow_keys = 0; // features that had more than cap locations
-    // Section 3.1: each feature maps to a bucket of locations, limited to cap.
+    // Section 4.1: each feature maps to a bucket of locations, limited to cap.
     std::unordered_map<uint32_t, std::vector<uint64_t>> buckets;
 };
 
@@ -198,12 +198,12 @@ uint64_t oracle_sketch(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint
     return total;
 }
 
-// Database build (Section 3.1 build phase, Section 4.2 build pipeline):
+// Database build (Section 4.1 build phase, Section 5.2 build pipeline):
 // targets get ids in input order; for every target t, every window j and
 // every feature f of window j's sketch, the location (t, j) is added to f's
 // bucket.  Finally each bucket is sorted and cut to the cap, keeping the
 // smallest locations (the CPU version's behaviour, since it inserts in
-// ascending (target, window) order, Section 3.1).
+// ascending (target, window) order, Section 4.1).
 // key_filter (sorted, optional) restricts the stored features to a subset,
 // which lets tests check sampled keys of a large database.
 // Sketching may use n_threads threads (per-target work); the insertion is
@@ -304,7 +304,7 @@ uint64_t oracle_db_dump(void* h, uint64_t lo, uint64_t hi, uint32_t* keys, uint3
     return ks.size();
 }
 
-// Lowest common ancestor (Section 3.2: candidates close to the maximum are
+// Lowest common ancestor (Section 4.2: candidates close to the maximum are
 // labelled with the LCA of their taxa).  Plain walk: compute both depths by
 // following parents to the root (parent == self), lift the deeper node to
 // the same depth, then lift both until they meet.  Different roots, an
@@ -329,7 +329,7 @@ uint32_t oracle_lca(uint32_t n_taxa, const uint32_t* parent, uint32_t a, uint32_
 
 struct Cand { uint32_t score, t, j0, j1; };
 
-// Sliding-window size (Section 4.6: "determined by the length of the
+// Sliding-window size (Section 5.6: "determined by the length of the
 // respective read"; the formula is not given).  Reading: the number of
 // consecutive windows that the k-mer starts of a fragment spanning `span`
 // bases can touch, span = read length (single-end) or max(sum of mate
@@ -339,10 +339,10 @@ uint64_t oracle_sws(uint32_t n_mates, uint64_t span_sum, uint32_t max_insert, ui
     return span >= k ? (span - k + stride - 1) / stride + 1 : 0;
 }
 
-// Read classification (Section 3.2 query phase; Section 4.2 query steps 1-8).
+// Read classification (Section 4.2 query phase; Section 5.2 query steps 1-8).
 // Per query (one read or one read pair = consecutive mates qoffs[q] ..
 // qoffs[q+1]):
-//  1. every mate is cut into windows exactly like a target (Section 3.2:
+//  1. every mate is cut into windows exactly like a target (Section 4.2:
 //     "windows of the same length as used in the database") and each
 //     window is sketched;
 //  2. every feature of every window is looked up and its bucket appended
@@ -350,15 +350,15 @@ uint64_t oracle_sws(uint32_t n_mates, uint64_t span_sum, uint32_t max_insert, ui
 //     windows of one query contributes its bucket twice);
 //  3. the location list is sorted and identical locations are accumulated
 //     into the window count statistic (location -> hit count);
-//  4. sliding window (Section 3.2, Section 4.6): for every location (t, j0)
+//  4. sliding window (Section 4.2, Section 5.6): for every location (t, j0)
 //     of the statistic, score = sum of counts of (t, j) with
 //     j0 <= j <= j0 + sws - 1.  Reading for sws (the paper says only that it
 //     follows from the read length): span = read length (single-end) or
 //     max(sum of mate lengths, max_insert) (pairs); sws = ceil((span-k)/stride)
 //     + 1, the most windows a fragment of that span can touch;
-//  5. top m (Section 3.2): one candidate per target (its best range; ties ->
+//  5. top m (Section 4.2): one candidate per target (its best range; ties ->
 //     smaller j0), ordered by score descending then target ascending;
-//  6. label (Section 3.2 and Section 5.5 hit threshold): no candidate or
+//  6. label (Section 4.2 and Section 6.5 hit threshold): no candidate or
 //     top score < hits_min -> unclassified.  Otherwise the candidates whose
 //     score is within lca_band_pct percent of the top score are "close"; one
 //     close candidate -> its target's taxon ("difference above a

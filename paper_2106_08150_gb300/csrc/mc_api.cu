@@ -94,10 +94,23 @@ std::vector<std::pair<std::string, TraceAcc>> g_trace_acc;
 }  // namespace
 
 namespace mc {
-void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return st != cudaStreamCaptureStatusNone;
+}
+
+void note_launch(cudaStream_t s) {
+    if (!capturing(s)) g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+
+void note_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 TraceScope::TraceScope(const char* name, cudaStream_t s) : stream(s) {
-    if (!g_trace_on.load(std::memory_order_relaxed)) return;
+    if (!g_trace_on.load(std::memory_order_relaxed) || capturing(s)) return;
     TraceRec r{name, nullptr, nullptr};
     if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) {
         cudaGetLastError();
@@ -129,6 +142,7 @@ struct mc_db {
     uint64_t hbm_budget = 0;
     // taxonomy
     uint32_t n_taxa = 0;
+    std::vector<uint32_t> parent;  // host copy, for mc_db_save
     DevBuf depth, lineage;
     uint32_t lin_stride = 0, max_depth = 0;
     // targets
@@ -144,8 +158,19 @@ struct mc_db {
     uint64_t n_kept = 0, n_keys = 0, table_len = 0, overflow_keys = 0, n_pairs = 0;
     uint32_t log_t = 1, max_probe = 0;
     bool dirty = false, has_table = false;
+    uint64_t epoch = 0;  // finalizes so far (plans re-capture when it changes)
     cudaEvent_t ready = nullptr;
     DevBuf status;  // u32 device status word
+    mc::Tuning tuning = mc::DEFAULT_TUNING;
+    // streams that classified against this database, each with an event
+    // recorded after its last classify launches: buffers those launches may
+    // read are freed only after the database stream has waited on them
+    struct StreamUse {
+        cudaStream_t s;
+        cudaEvent_t ev;
+    };
+    mutable std::mutex use_mu;
+    mutable std::vector<StreamUse> uses;
 };
 
 namespace {
@@ -159,6 +184,31 @@ bool grab(mc_db* db, DevBuf& b, size_t bytes) {
     b.p = bytes ? db->mem.alloc(bytes, db->stream) : nullptr;
     b.bytes = bytes;
     return bytes == 0 || b.p != nullptr;
+}
+
+// Records that classify work was enqueued on `s`.
+cudaError_t note_use(const mc_db* db, cudaStream_t s) {
+    std::lock_guard<std::mutex> lock(db->use_mu);
+    for (auto& u : db->uses)
+        if (u.s == s) return cudaEventRecord(u.ev, s);
+    mc_db::StreamUse u{s, nullptr};
+    cudaError_t e = cudaEventCreateWithFlags(&u.ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return e;
+    db->uses.push_back(u);
+    return cudaEventRecord(u.ev, s);
+}
+
+// Makes the database stream wait for every classify enqueued so far.
+void wait_uses(mc_db* db) {
+    std::lock_guard<std::mutex> lock(db->use_mu);
+    for (auto& u : db->uses) cudaStreamWaitEvent(db->stream, u.ev, 0);
+}
+
+// Releases a buffer that classify launches may still read.
+void retire(mc_db* db, DevBuf& b) {
+    if (!b.p) return;
+    wait_uses(db);
+    release(db, b);
 }
 
 uint64_t held_bytes(const mc_db* db) {
@@ -178,7 +228,7 @@ int grow(mc_db* db, DevBuf& b, size_t need, size_t keep, const char* what) {
     DevBuf n;
     if (!grab(db, n, nb)) return fail(MC_ERR_OOM, "%s: cannot allocate %zu bytes", what, nb);
     if (keep) MC_CU(cudaMemcpyAsync(n.p, b.p, keep, cudaMemcpyDeviceToDevice, db->stream));
-    release(db, b);
+    retire(db, b);
     b = n;
     return MC_OK;
 }
@@ -301,6 +351,7 @@ int mc_db_create(const mc_db_params* params, uint32_t n_taxa, const uint32_t* pa
     db->cap = params->bucket_cap;
     db->hbm_budget = params->hbm_budget;
     db->n_taxa = n_taxa;
+    db->parent.assign(parent, parent + n_taxa);
     auto bail = [&](int code) {
         mc_db_free(db);
         return code;
@@ -445,8 +496,8 @@ int mc_db_finalize(mc_db* db) {
                            db->n_targets, &fo, s);
     cleanup();
     if (e != cudaSuccess) return cuda_fail(e, "finalize: layout");
-    release(db, db->locs);
-    release(db, db->table);
+    retire(db, db->locs);
+    retire(db, db->table);
     db->locs = DevBuf{fo.locs, fo.n_kept * 8};
     db->table = DevBuf{fo.table, fo.table_bytes};
     db->n_pairs += db->pending_real;
@@ -459,6 +510,7 @@ int mc_db_finalize(mc_db* db) {
     db->overflow_keys = fo.overflow_keys;
     db->dirty = false;
     db->has_table = true;
+    ++db->epoch;
     MC_CU(cudaEventRecord(db->ready, s));
     MC_CU(cudaStreamSynchronize(s));
     return MC_OK;
@@ -504,7 +556,10 @@ static int classify_impl(const mc_db* db, const mc_classify_params* params, uint
     q.cands = cands;
     q.counters = (unsigned long long*)counters;
     q.status = (uint32_t*)db->status.p;
-    MC_CU(mc::classify_launch(db->mem, cdb, q, s));
+    q.batches = nullptr;
+    q.bhdr = nullptr;
+    MC_CU(mc::classify_launch(db->mem, cdb, q, db->tuning, s));
+    MC_CU(note_use(db, s));
     return MC_OK;
 }
 
@@ -555,6 +610,17 @@ int classify_prepare(const mc_db* db, const mc_classify_params* params, const ch
     q->cands = nullptr;
     q->counters = nullptr;
     q->status = (uint32_t*)db->status.p;
+    q->batches = nullptr;
+    q->bhdr = nullptr;
+    return MC_OK;
+}
+
+int classify_done(const mc_db* db, cudaStream_t stream) {
+    cudaError_t e = note_use(db, stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return report_error(MC_ERR_CUDA, "classify: %s", cudaGetErrorString(e));
+    }
     return MC_OK;
 }
 }  // namespace mc
@@ -603,6 +669,153 @@ void mc_db_free(mc_db* db) {
     if (db->ready) cudaEventDestroy(db->ready);
     cudaGetLastError();
     delete db;
+}
+
+namespace {
+const char MAGIC[8] = {'M', 'C', 'G', 'B', '3', 'D', 'B', '1'};
+const uint32_t FILE_VERSION = 1;
+
+struct FileHeader {
+    char magic[8];
+    uint32_t version, k, s, w, stride, cap, n_taxa, n_targets, log_t, max_probe;
+    uint64_t n_windows, n_pairs, n_keys, n_kept, table_len, overflow_keys;
+};
+
+// Device <-> file through a host staging buffer.
+int write_device(FILE* f, const void* dev, size_t bytes, cudaStream_t s, std::vector<char>& stage) {
+    const size_t chunk = stage.size();
+    for (size_t off = 0; off < bytes; off += chunk) {
+        const size_t n = std::min(chunk, bytes - off);
+        MC_CU(cudaMemcpyAsync(stage.data(), (const char*)dev + off, n, cudaMemcpyDeviceToHost, s));
+        MC_CU(cudaStreamSynchronize(s));
+        if (fwrite(stage.data(), 1, n, f) != n) return fail(MC_ERR_ARG, "mc_db_save: write failed");
+    }
+    return MC_OK;
+}
+
+int read_device(FILE* f, void* dev, size_t bytes, cudaStream_t s, std::vector<char>& stage) {
+    const size_t chunk = stage.size();
+    for (size_t off = 0; off < bytes; off += chunk) {
+        const size_t n = std::min(chunk, bytes - off);
+        if (fread(stage.data(), 1, n, f) != n) return fail(MC_ERR_ARG, "mc_db_load: file is truncated");
+        MC_CU(cudaMemcpyAsync((char*)dev + off, stage.data(), n, cudaMemcpyHostToDevice, s));
+        MC_CU(cudaStreamSynchronize(s));
+    }
+    return MC_OK;
+}
+}  // namespace
+
+int mc_db_save(const mc_db* db, const char* path) {
+    g_err[0] = 0;
+    if (!db || !path) return fail(MC_ERR_ARG, "NULL argument");
+    if (!db->has_table || db->dirty) return fail(MC_ERR_STATE, "mc_db_save: finalize the database first");
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(MC_ERR_ARG, "mc_db_save: cannot open %s", path);
+    FileHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, MAGIC, 8);
+    h.version = FILE_VERSION;
+    h.k = db->sp.k;
+    h.s = db->sp.s;
+    h.w = db->sp.w;
+    h.stride = db->sp.stride;
+    h.cap = db->cap;
+    h.n_taxa = db->n_taxa;
+    h.n_targets = db->n_targets;
+    h.log_t = db->log_t;
+    h.max_probe = db->max_probe;
+    h.n_windows = db->n_windows;
+    h.n_pairs = db->n_pairs;
+    h.n_keys = db->n_keys;
+    h.n_kept = db->n_kept;
+    h.table_len = db->table_len;
+    h.overflow_keys = db->overflow_keys;
+    std::vector<char> stage(64u << 20);
+    int rc = MC_OK;
+    if (fwrite(&h, sizeof h, 1, f) != 1 || fwrite(db->parent.data(), 4, db->n_taxa, f) != db->n_taxa)
+        rc = fail(MC_ERR_ARG, "mc_db_save: write failed");
+    if (!rc) rc = write_device(f, db->taxon.p, (size_t)db->n_targets * 4, db->stream, stage);
+    if (!rc) rc = write_device(f, db->wbase.p, ((size_t)db->n_targets + 1) * 4, db->stream, stage);
+    if (!rc) rc = write_device(f, db->locs.p, db->n_kept * 8, db->stream, stage);
+    if (!rc) rc = write_device(f, db->table.p, db->table_len * sizeof(uint4), db->stream, stage);
+    if (fclose(f) != 0 && !rc) rc = fail(MC_ERR_ARG, "mc_db_save: close failed");
+    return rc;
+}
+
+int mc_db_load(const char* path, void* stream, mc_db** out) {
+    g_err[0] = 0;
+    if (!path || !out) return fail(MC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(MC_ERR_ARG, "mc_db_load: cannot open %s", path);
+    FileHeader h;
+    if (fread(&h, sizeof h, 1, f) != 1 || std::memcmp(h.magic, MAGIC, 8) != 0) {
+        fclose(f);
+        return fail(MC_ERR_ARG, "mc_db_load: %s is not a database file", path);
+    }
+    if (h.version != FILE_VERSION) {
+        fclose(f);
+        return fail(MC_ERR_ARG, "mc_db_load: format version %u, expected %u", h.version, FILE_VERSION);
+    }
+    std::vector<uint32_t> parent(h.n_taxa);
+    if (h.n_taxa == 0 || fread(parent.data(), 4, h.n_taxa, f) != h.n_taxa) {
+        fclose(f);
+        return fail(MC_ERR_ARG, "mc_db_load: file is truncated");
+    }
+    mc_db_params p;
+    std::memset(&p, 0, sizeof p);
+    p.k = h.k;
+    p.sketch_size = h.s;
+    p.window_len = h.w;
+    p.window_stride = h.stride;
+    p.bucket_cap = h.cap;
+    mc_db* db = nullptr;
+    int rc = mc_db_create(&p, h.n_taxa, parent.data(), stream, &db);
+    if (rc) {
+        fclose(f);
+        return rc;
+    }
+    std::vector<char> stage(64u << 20);
+    if (!grab(db, db->taxon, std::max<size_t>((size_t)h.n_targets * 4, 4)) ||
+        !grab(db, db->locs, h.n_kept * 8) || !grab(db, db->table, h.table_len * sizeof(uint4))) {
+        fclose(f);
+        mc_db_free(db);
+        return fail(MC_ERR_OOM, "mc_db_load: allocation failed");
+    }
+    release(db, db->wbase);
+    if (!grab(db, db->wbase, ((size_t)h.n_targets + 1) * 4)) {
+        fclose(f);
+        mc_db_free(db);
+        return fail(MC_ERR_OOM, "mc_db_load: allocation failed");
+    }
+    rc = read_device(f, db->taxon.p, (size_t)h.n_targets * 4, db->stream, stage);
+    if (!rc) rc = read_device(f, db->wbase.p, ((size_t)h.n_targets + 1) * 4, db->stream, stage);
+    if (!rc) rc = read_device(f, db->locs.p, h.n_kept * 8, db->stream, stage);
+    if (!rc) rc = read_device(f, db->table.p, h.table_len * sizeof(uint4), db->stream, stage);
+    fclose(f);
+    if (rc) {
+        mc_db_free(db);
+        return rc;
+    }
+    db->n_targets = h.n_targets;
+    db->n_windows = h.n_windows;
+    db->n_pairs = h.n_pairs;
+    db->n_keys = h.n_keys;
+    db->n_kept = h.n_kept;
+    db->table_len = h.table_len;
+    db->log_t = h.log_t;
+    db->max_probe = h.max_probe;
+    db->overflow_keys = h.overflow_keys;
+    db->has_table = true;
+    db->dirty = false;
+    ++db->epoch;
+    cudaError_t e = cudaEventRecord(db->ready, db->stream);
+    if (e != cudaSuccess) {
+        mc_db_free(db);
+        return cuda_fail(e, "mc_db_load");
+    }
+    *out = db;
+    return MC_OK;
 }
 
 int mc_db_stats(const mc_db* db, mc_db_stats_t* out) {
@@ -713,6 +926,326 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
     if (!seq || !offs || !win_offs || !sketch || !counts) return fail(MC_ERR_ARG, "NULL argument");
     MC_CU(mc::sketch_windows(sketch_params(params), n_seq, (const uint8_t*)seq, offs, win_offs, n_windows, sketch,
                              counts, (cudaStream_t)stream));
+    return MC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------
+// Batched classification, plans and the autotuner.
+
+namespace {
+
+mc::ClassifyDb db_view(const mc_db* db) {
+    mc::ClassifyDb cdb;
+    cdb.table = (const uint4*)db->table.p;
+    cdb.log_t = db->log_t;
+    cdb.max_probe = db->max_probe;
+    cdb.locs = (const uint64_t*)db->locs.p;
+    cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
+    cdb.n_targets = db->n_targets;
+    cdb.lineage = (const uint32_t*)db->lineage.p;
+    cdb.depth = (const uint32_t*)db->depth.p;
+    cdb.lin_stride = db->lin_stride;
+    cdb.n_taxa = db->n_taxa;
+    cdb.sp = db->sp;
+    return cdb;
+}
+
+mc::ClassifyQuery batch_query(const mc_db* db, const mc_classify_params* p, uint32_t n_q_cap,
+                              const mc::BatchDesc* desc, const uint32_t* bhdr) {
+    mc::ClassifyQuery q;
+    std::memset(&q, 0, sizeof q);
+    q.n_q = n_q_cap;
+    q.m = p->max_candidates;
+    q.hits_min = p->hits_min;
+    q.band = p->lca_band_pct;
+    q.max_insert = p->max_insert;
+    q.status = (uint32_t*)db->status.p;
+    q.batches = desc;
+    q.bhdr = bhdr;
+    return q;
+}
+
+int tuning_from(const mc_tuning* t, const mc::Tuning& dflt, mc::Tuning* out) {
+    if (!t) {
+        *out = dflt;
+        return MC_OK;
+    }
+    mc::Tuning x = mc::DEFAULT_TUNING;
+    if (t->hist_slots) x.hist_slots = t->hist_slots;
+    if (t->probe_batch) x.probe_batch = t->probe_batch;
+    if (t->gather_batch) x.gather_batch = t->gather_batch;
+    if (t->lookup_warps) x.lookup_warps = t->lookup_warps;
+    if (t->score_warps) x.score_warps = t->score_warps;
+    if (!mc::tuning_valid(x)) return fail(MC_ERR_ARG, "tuning: a value is outside its allowed set");
+    *out = x;
+    return MC_OK;
+}
+
+mc_tuning to_public(const mc::Tuning& t) {
+    return mc_tuning{t.hist_slots, t.probe_batch, t.gather_batch, t.lookup_warps, t.score_warps};
+}
+
+// Host image of the batch header + descriptors (layout of ClassifyQuery's
+// multi-batch form): bhdr words, then the descriptors at a 16-byte boundary.
+size_t desc_offset(uint32_t n_batches) { return ((size_t)(n_batches + 3) * 4 + 15) & ~(size_t)15; }
+size_t desc_bytes(uint32_t n_batches) { return desc_offset(n_batches) + (size_t)n_batches * sizeof(mc::BatchDesc); }
+
+int fill_batches(uint32_t n_batches, const mc_batch* batches, unsigned char* img, uint64_t* total_out) {
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(img);
+    mc::BatchDesc* d = reinterpret_cast<mc::BatchDesc*>(img + desc_offset(n_batches));
+    uint64_t total = 0;
+    hdr[0] = n_batches;
+    for (uint32_t b = 0; b < n_batches; ++b) {
+        const mc_batch& x = batches[b];
+        if (x.n_queries && (!x.seq || !x.offs || !x.qoffs || !x.label || !x.hits))
+            return fail(MC_ERR_ARG, "batch %u: NULL input or output pointer", b);
+        hdr[2 + b] = (uint32_t)total;
+        total += x.n_queries;
+        if (total >= 0xFFFFFFFFull) return fail(MC_ERR_ARG, "batches: more than 2^32-2 queries in total");
+        d[b] = mc::BatchDesc{(const uint8_t*)x.seq, x.offs, x.qoffs, x.label, x.hits, x.top_target};
+    }
+    hdr[1] = (uint32_t)total;
+    hdr[2 + n_batches] = (uint32_t)total;
+    *total_out = total;
+    return MC_OK;
+}
+
+}  // namespace
+
+struct mc_plan {
+    const mc_db* db = nullptr;
+    mc_classify_params params{};
+    mc::Tuning tuning{};
+    uint32_t max_batches = 0, max_queries = 0;
+    DevBuf scratch, desc;
+    mc::ClassifyScratch sc{};
+    unsigned char* host = nullptr;  // pinned image of the descriptors
+    cudaStream_t cap = nullptr;     // capture stream
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t copied = nullptr;   // the descriptor copy of the last run is done
+    cudaEvent_t done = nullptr;     // the last run is done
+    uint64_t epoch = ~0ull;
+    int n_kernels = 0;
+};
+
+namespace {
+
+void plan_drop_graph(mc_plan* p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
+int plan_capture(mc_plan* p) {
+    plan_drop_graph(p);
+    const mc_db* db = p->db;
+    const mc::ClassifyDb cdb = db_view(db);
+    const uint32_t* bhdr = (const uint32_t*)p->desc.p;
+    const mc::BatchDesc* d = (const mc::BatchDesc*)((unsigned char*)p->desc.p + desc_offset(p->max_batches));
+    const mc::ClassifyQuery q = batch_query(db, &p->params, p->max_queries, d, bhdr);
+    MC_CU(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    int nk = 0;
+    cudaError_t e = mc::classify_enqueue(cdb, q, p->tuning, p->sc, p->cap, &nk);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(p->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return cuda_fail(e != cudaSuccess ? e : e2, "mc_plan: capture");
+    }
+    p->graph = g;
+    e = cudaGraphInstantiate(&p->exec, g, 0);
+    if (e != cudaSuccess) {
+        plan_drop_graph(p);
+        return cuda_fail(e, "mc_plan: instantiate");
+    }
+    p->n_kernels = nk;
+    p->epoch = db->epoch;
+    return MC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mc_db_set_tuning(mc_db* db, const mc_tuning* tuning) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    mc::Tuning t;
+    int rc = tuning_from(tuning, mc::DEFAULT_TUNING, &t);
+    if (rc) return rc;
+    db->tuning = t;
+    return MC_OK;
+}
+
+int mc_classify_batches(const mc_db* db, const mc_classify_params* params, const mc_tuning* tuning,
+                        uint32_t n_batches, const mc_batch* batches, void* stream) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (!db->has_table) return fail(MC_ERR_STATE, "mc_classify_batches before mc_db_finalize");
+    if (n_batches == 0) return MC_OK;
+    if (!batches) return fail(MC_ERR_ARG, "batches is NULL");
+    mc::Tuning t;
+    if ((rc = tuning_from(tuning, db->tuning, &t))) return rc;
+    std::vector<unsigned char> img(desc_bytes(n_batches));
+    uint64_t total = 0;
+    if ((rc = fill_batches(n_batches, batches, img.data(), &total))) return rc;
+    if (total == 0) return MC_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    MC_CU(cudaStreamWaitEvent(s, db->ready, 0));
+    const uint32_t lw = mc::classify_default_large_warps();
+    const size_t sbytes = mc::classify_scratch_bytes((uint32_t)total, db->sp.s, lw);
+    mc::Tmp<unsigned char> dev(db->mem, img.size(), s);
+    mc::Tmp<unsigned char> scratch(db->mem, sbytes, s);
+    if (!dev.ok() || !scratch.ok()) return fail(MC_ERR_OOM, "mc_classify_batches: allocation failed");
+    // pageable source: the copy is staged before the call returns
+    MC_CU(cudaMemcpyAsync(dev.ptr, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+    const mc::ClassifyScratch sc = mc::classify_scratch_carve(scratch.ptr, (uint32_t)total, db->sp.s, lw);
+    const mc::ClassifyQuery q = batch_query(db, params, (uint32_t)total,
+                                            (const mc::BatchDesc*)(dev.ptr + desc_offset(n_batches)),
+                                            (const uint32_t*)dev.ptr);
+    MC_CU(mc::classify_enqueue(db_view(db), q, t, sc, s, nullptr));
+    MC_CU(note_use(db, s));
+    return MC_OK;
+}
+
+int mc_plan_create(const mc_db* db, const mc_classify_params* params, const mc_tuning* tuning,
+                   uint32_t max_batches, uint32_t max_queries, mc_plan** out) {
+    g_err[0] = 0;
+    if (!db || !out) return fail(MC_ERR_ARG, "NULL argument");
+    *out = nullptr;
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (!db->has_table) return fail(MC_ERR_STATE, "mc_plan_create before mc_db_finalize");
+    if (max_batches == 0 || max_queries == 0 || max_queries >= 0xFFFFFFFFu)
+        return fail(MC_ERR_ARG, "mc_plan_create: max_batches and max_queries must be positive");
+    mc_plan* p = new mc_plan();
+    p->db = db;
+    p->params = *params;
+    p->max_batches = max_batches;
+    p->max_queries = max_queries;
+    if ((rc = tuning_from(tuning, db->tuning, &p->tuning))) {
+        delete p;
+        return rc;
+    }
+    auto bail = [&](int code) {
+        mc_plan_free(p);
+        return code;
+    };
+    mc_db* mdb = const_cast<mc_db*>(db);
+    const uint32_t lw = mc::classify_default_large_warps();
+    if (!grab(mdb, p->scratch, mc::classify_scratch_bytes(max_queries, db->sp.s, lw)) ||
+        !grab(mdb, p->desc, desc_bytes(max_batches)))
+        return bail(fail(MC_ERR_OOM, "mc_plan_create: allocation failed"));
+    p->sc = mc::classify_scratch_carve((unsigned char*)p->scratch.p, max_queries, db->sp.s, lw);
+    cudaError_t e;
+    if ((e = cudaMallocHost(&p->host, desc_bytes(max_batches))) != cudaSuccess) {
+        p->host = nullptr;
+        return bail(cuda_fail(e, "mc_plan_create: pinned buffer"));
+    }
+    if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(cuda_fail(e, "mc_plan_create: stream"));
+    if ((e = cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+        return bail(cuda_fail(e, "mc_plan_create: event"));
+    // the allocations above are stream-ordered on the database stream
+    if ((e = cudaStreamSynchronize(db->stream)) != cudaSuccess) return bail(cuda_fail(e, "mc_plan_create"));
+    if ((rc = plan_capture(p))) return bail(rc);
+    *out = p;
+    return MC_OK;
+}
+
+int mc_plan_run(mc_plan* p, uint32_t n_batches, const mc_batch* batches, void* stream) {
+    g_err[0] = 0;
+    if (!p) return fail(MC_ERR_ARG, "plan is NULL");
+    if (n_batches && !batches) return fail(MC_ERR_ARG, "batches is NULL");
+    if (n_batches > p->max_batches)
+        return fail(MC_ERR_CAPACITY, "mc_plan_run: %u batches, plan holds %u", n_batches, p->max_batches);
+    const mc_db* db = p->db;
+    if (!db->has_table || db->dirty) return fail(MC_ERR_STATE, "mc_plan_run: database has pending additions");
+    int rc;
+    if (db->epoch != p->epoch && (rc = plan_capture(p))) return rc;
+    // the previous run's descriptor copy must be done before the image is rewritten
+    MC_CU(cudaEventSynchronize(p->copied));
+    std::vector<unsigned char> img(desc_bytes(n_batches));
+    uint64_t total = 0;
+    if ((rc = fill_batches(n_batches, batches, img.data(), &total))) return rc;
+    if (total > p->max_queries)
+        return fail(MC_ERR_CAPACITY, "mc_plan_run: %llu queries, plan holds %u", (unsigned long long)total,
+                    p->max_queries);
+    // the plan's image layout has its descriptors after max_batches header words
+    uint32_t* hdr = reinterpret_cast<uint32_t*>(p->host);
+    std::memcpy(hdr, img.data(), (size_t)(n_batches + 3) * 4);
+    std::memcpy(p->host + desc_offset(p->max_batches), img.data() + desc_offset(n_batches),
+                (size_t)n_batches * sizeof(mc::BatchDesc));
+    cudaStream_t s = (cudaStream_t)stream;
+    MC_CU(cudaStreamWaitEvent(s, db->ready, 0));
+    MC_CU(cudaMemcpyAsync(p->desc.p, p->host, desc_bytes(p->max_batches), cudaMemcpyHostToDevice, s));
+    MC_CU(cudaEventRecord(p->copied, s));
+    MC_CU(cudaGraphLaunch(p->exec, s));
+    MC_CU(cudaEventRecord(p->done, s));
+    mc::note_launches((uint64_t)p->n_kernels);
+    MC_CU(note_use(db, s));
+    return MC_OK;
+}
+
+int mc_plan_kernels(const mc_plan* p) { return p ? p->n_kernels : 0; }
+
+void mc_plan_free(mc_plan* p) {
+    if (!p) return;
+    if (p->done) cudaEventSynchronize(p->done);
+    plan_drop_graph(p);
+    mc_db* mdb = const_cast<mc_db*>(p->db);
+    release(mdb, p->scratch);
+    release(mdb, p->desc);
+    cudaStreamSynchronize(mdb->stream);
+    if (p->host) cudaFreeHost(p->host);
+    if (p->copied) cudaEventDestroy(p->copied);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    cudaGetLastError();
+    delete p;
+}
+
+int mc_autotune(const mc_db* db, const mc_classify_params* params, uint32_t n_batches, const mc_batch* batches,
+                uint32_t reps, mc_tuning* best, mc_tuning_time* times, uint32_t max_times, uint32_t* n_times) {
+    g_err[0] = 0;
+    if (!db || !best) return fail(MC_ERR_ARG, "NULL argument");
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (!db->has_table) return fail(MC_ERR_STATE, "mc_autotune before mc_db_finalize");
+    if (n_batches == 0 || !batches || reps == 0) return fail(MC_ERR_ARG, "mc_autotune: no sample");
+    std::vector<unsigned char> img(desc_bytes(n_batches));
+    uint64_t total = 0;
+    if ((rc = fill_batches(n_batches, batches, img.data(), &total))) return rc;
+    if (total == 0 || total > mc::CLASSIFY_CHUNK)
+        return fail(MC_ERR_ARG, "mc_autotune: sample must hold 1..%u queries", mc::CLASSIFY_CHUNK);
+    cudaStream_t s = db->stream;
+    MC_CU(cudaStreamWaitEvent(s, db->ready, 0));
+    const uint32_t lw = mc::classify_default_large_warps();
+    mc::Tmp<unsigned char> dev(db->mem, img.size(), s);
+    mc::Tmp<unsigned char> scratch(db->mem, mc::classify_scratch_bytes((uint32_t)total, db->sp.s, lw), s);
+    if (!dev.ok() || !scratch.ok()) return fail(MC_ERR_OOM, "mc_autotune: allocation failed");
+    MC_CU(cudaMemcpyAsync(dev.ptr, img.data(), img.size(), cudaMemcpyHostToDevice, s));
+    const mc::ClassifyScratch sc = mc::classify_scratch_carve(scratch.ptr, (uint32_t)total, db->sp.s, lw);
+    const mc::ClassifyQuery q = batch_query(db, params, (uint32_t)total,
+                                            (const mc::BatchDesc*)(dev.ptr + desc_offset(n_batches)),
+                                            (const uint32_t*)dev.ptr);
+    mc::Tuning t;
+    std::vector<mc::TuneRecord> rec;
+    MC_CU(mc::classify_autotune(db_view(db), q, sc, reps, s, &t, &rec));
+    *best = to_public(t);
+    if (times)
+        for (uint32_t i = 0; i < max_times && i < rec.size(); ++i)
+            times[i] = mc_tuning_time{to_public(rec[i].t), rec[i].stage, rec[i].ms};
+    if (n_times) *n_times = (uint32_t)rec.size();
+    MC_CU(cudaStreamSynchronize(s));
     return MC_OK;
 }
 

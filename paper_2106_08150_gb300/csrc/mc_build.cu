@@ -1,5 +1,5 @@
-// Database build kernels (Section 3.1 build phase, Section 4.1 GPU hash
-// tables, Section 4.2 build pipeline) for sm_103a.
+// Database build kernels (Section 4.1 build phase, Section 5.1 GPU hash
+// tables, Section 5.2 build pipeline) for sm_103a.
 //
 // GB300 design.  The paper inserts each (feature, location) pair into a
 // multi-bucket hash table with warp-aggregated atomics.  Here the build is
@@ -10,11 +10,11 @@
 //   2. a stable LSD radix sort (4 passes of 8 bits over the upper word)
 //      groups the pairs by feature while keeping them in window order,
 //      which is (target, window) order, so every bucket comes out sorted;
-//   3. finalize keeps the first `cap` pairs of each feature (Section 3.1:
+//   3. finalize keeps the first `cap` pairs of each feature (Section 4.1:
 //      at most 254 locations per feature; the smallest are kept, as in the
 //      CPU version that inserts in ascending order), converts global windows
 //      to (target, window) locations, and lays out the condensed layout of
-//      Section 4.1: one contiguous location array plus a feature table;
+//      Section 5.1: one contiguous location array plus a feature table;
 //   4. the feature table is an ordered linear-probing table built without
 //      atomics: features arrive sorted by h2, so slot(k) = max(home(k),
 //      slot(k-1)+1) = k + max_{k'<=k}(home(k') - k'), a max-scan.

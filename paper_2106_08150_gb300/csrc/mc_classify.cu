@@ -1,21 +1,21 @@
-// Read classification kernels (Section 3.2 query phase, Section 4.2 query
-// steps 1-8, Sections 4.3-4.6) for sm_103a.
+// Read classification kernels (Section 4.2 query phase, Section 5.2 query
+// steps 1-8, Sections 5.3-5.6) for sm_103a.
 //
 // GB300 design.  The paper runs the query as a pipeline of kernels with
 // global-memory hand-offs: sketch+lookup, compaction, a segmented sort
-// (about half of its query time, Section 5.4) and a top-candidate kernel.
+// (about half of its query time, Section 6.4) and a top-candidate kernel.
 // Here one warp carries a whole query (a read or a read pair) through all
 // steps without leaving the SM:
 //   1. sketch every window of every mate (mc_sketch.cuh) and look each
-//      feature up in the feature table (one 16-byte probe, Section 4.3);
+//      feature up in the feature table (one 16-byte probe, Section 5.3);
 //   2. gather the bucket locations into a per-warp hash histogram in shared
 //      memory, location -> hit count (the window count statistic of
-//      Section 3.2, replacing compaction + segmented sort + run-length
-//      accumulation of Sections 4.4-4.6: order does not matter for counts);
+//      Section 4.2, replacing compaction + segmented sort + run-length
+//      accumulation of Sections 5.4-5.6: order does not matter for counts);
 //   3. score every distinct location (t, j0) as the sum of counts of
-//      (t, j0 .. j0+sws-1) by histogram lookups (Section 4.6 sliding window);
+//      (t, j0 .. j0+sws-1) by histogram lookups (Section 5.6 sliding window);
 //   4. keep per-lane top-m lists with one candidate per target, merge them
-//      with warp shuffles (Section 4.6), and label the query by its top
+//      with warp shuffles (Section 5.6), and label the query by its top
 //      target or the LCA of the close candidates via the lineage table.
 // Queries whose histogram does not fit the shared-memory table (rare) are
 // queued and processed by a second kernel whose warps use a larger table in
@@ -43,7 +43,7 @@ struct Cand {
 };
 
 // Order of candidates: higher score first, then smaller target, then
-// smaller first window (Section 3.2 top hits; ties are our reading).
+// smaller first window (Section 4.2 top hits; ties are our reading).
 __device__ __forceinline__ bool better(const Cand& a, const Cand& b) {
     if (a.score != b.score) return a.score > b.score;
     if (a.t != b.t) return a.t < b.t;
@@ -114,8 +114,8 @@ __device__ __forceinline__ uint32_t lca2(const ClassifyDb& db, uint32_t a, uint3
 enum { Q_DONE = 0, Q_ESCALATE = 1, Q_TOO_LARGE = 2 };
 
 constexpr uint32_t MAX_MATES = MC_MAX_QUERY_MATES;  // mates per query (lane i holds mate i)
-constexpr int LB = 4;               // feature-table probes in flight per lane
-constexpr int GB = 8;               // bucket loads in flight per lane
+constexpr int LB_DEFAULT = 4;       // feature-table probes in flight per lane
+constexpr int GB_DEFAULT = 8;       // bucket loads in flight per lane
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -184,14 +184,59 @@ struct Counters {
     unsigned long long features = 0, locations = 0, distinct = 0, found = 0, sectors = 0;
 };
 
+// Batch holding query q of a multi-batch launch: the last batch whose
+// first query is <= q (empty batches share their first query number with
+// the next batch, so they are never chosen).
+__device__ __forceinline__ uint32_t find_batch(const ClassifyQuery& Q, uint32_t q) {
+    const uint32_t* pre = Q.bhdr + 2;
+    uint32_t lo = 0, hi = Q.bhdr[0];
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pre[mid] <= q) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// Number of queries of the launch (read on the device in the multi-batch
+// form, so that a captured launch serves any batch set within capacity).
+__device__ __forceinline__ uint32_t total_queries(const ClassifyQuery& Q) {
+    return Q.batches ? Q.bhdr[1] : Q.n_q;
+}
+
+// Input of query q: its sequences and its mates' range.
+struct QueryIn {
+    const uint8_t* seq;
+    const uint64_t* offs;
+    uint32_t m0, m1;
+};
+
+__device__ __forceinline__ QueryIn query_in(const ClassifyQuery& Q, uint32_t q) {
+    if (!Q.batches) return QueryIn{Q.seq, Q.offs, Q.qoffs[q], Q.qoffs[q + 1]};
+    const uint32_t b = find_batch(Q, q);
+    const BatchDesc& B = Q.batches[b];
+    const uint32_t lq = q - Q.bhdr[2 + b];
+    return QueryIn{B.seq, B.offs, B.qoffs[lq], B.qoffs[lq + 1]};
+}
+
 // Lane i (< m) writes candidate slot i; `mine` is the lane's candidate.
 __device__ __forceinline__ void write_result(const ClassifyQuery& Q, uint32_t q, uint32_t label, uint32_t hits,
                                              uint32_t top, const Cand& mine) {
     const uint32_t lane = lane_id();
     if (lane == 0) {
-        Q.label[q] = label;
-        Q.hits[q] = hits;
-        if (Q.top_target) Q.top_target[q] = top;
+        uint32_t* lab = Q.label;
+        uint32_t* hit = Q.hits;
+        uint32_t* tt = Q.top_target;
+        uint32_t lq = q;
+        if (Q.batches) {
+            const uint32_t b = find_batch(Q, q);
+            lab = Q.batches[b].label;
+            hit = Q.batches[b].hits;
+            tt = Q.batches[b].top_target;
+            lq = q - Q.bhdr[2 + b];
+        }
+        lab[lq] = label;
+        hit[lq] = hits;
+        if (tt) tt[lq] = top;
     }
     if (Q.cands && lane < Q.m) {
         uint32_t* o = Q.cands + ((uint64_t)q * Q.m + lane) * 4;
@@ -212,26 +257,27 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
-// Query steps 1-4 of Section 4.2 on one warp (sketch every window of every
+// Query steps 1-4 of Section 5.2 on one warp (sketch every window of every
 // mate, look every feature up): the found buckets are written to `list`
 // (working memory or global scratch), packed as offset << 16 | size.  Also
 // returns the sliding-window size.
 // Returns Q_DONE, Q_ESCALATE (needs the large path) or Q_TOO_LARGE.
 // Also returns the number of features and the 32-byte sectors of the found
 // buckets (warp totals) for the counters.
-template <int R, int KC, class CntT>
+template <int R, int KC, int LB, class CntT>
 __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
                                             const Scratch<CntT>& S, uint64_t* __restrict__ list, uint32_t& n_list_out, uint32_t& sws_out,
                                             uint32_t& n_feat_out, uint32_t& n_sect_out) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     const SketchParams& p = db.sp;
-    const uint32_t m0 = Q.qoffs[q], m1 = Q.qoffs[q + 1];
+    const QueryIn in = query_in(Q, q);
+    const uint32_t m0 = in.m0, m1 = in.m1;
     if (m1 < m0 || m1 - m0 > MAX_MATES) return Q_TOO_LARGE;
     const uint32_t nm = m1 - m0;
 
     // mates: lane i holds mate i's offset, length and window count
-    const uint64_t o = lane <= nm ? Q.offs[m0 + lane] : 0;
+    const uint64_t o = lane <= nm ? in.offs[m0 + lane] : 0;
     const uint64_t o_next = __shfl_down_sync(FULL_MASK, o, 1);
     const uint64_t L = (lane < nm && o_next > o) ? o_next - o : 0;
     const uint64_t nw = lane < nm ? num_windows(L, p.k, p.stride) : 0;
@@ -253,7 +299,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     // all in flight), placed at the same offset mod 16 in the buffer, with
     // the partial chunks at both ends copied byte by byte.
     const uint64_t start = __shfl_sync(FULL_MASK, o, 0);
-    const uintptr_t first = (uintptr_t)(Q.seq + start);
+    const uintptr_t first = (uintptr_t)(in.seq + start);
     const uint32_t shift = (uint32_t)(first & 15u);
     {
         const uintptr_t a0 = first - shift;
@@ -271,7 +317,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     }
     __syncwarp();
 
-    // 1b. sketch every window of every mate (Section 3.2: reads are windowed
+    // 1b. sketch every window of every mate (Section 4.2: reads are windowed
     // like the targets), SK_NW windows at a time; feat[] gets the features
     // in window order
     uint32_t F = 0;
@@ -355,11 +401,11 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     return Q_DONE;
 }
 
-// Query steps 5-8 of Section 4.2 on one warp, from the bucket list in
+// Query steps 5-8 of Section 5.2 on one warp, from the bucket list in
 // working memory: gather, window count statistic, sliding-window scores,
 // top m, label.  Writes the outputs and returns Q_DONE, or Q_ESCALATE if the
 // histogram does not fit the working memory.
-template <class CntT>
+template <int GB, class CntT>
 __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
                                            const Scratch<CntT>& S, uint32_t n_list, uint32_t sws, Counters& ctr) {
     const uint32_t lane = lane_id();
@@ -391,7 +437,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     __syncwarp();
 
     // 3. gather the buckets into the hit histogram (window count statistic,
-    // Section 3.2): each lane loads GB consecutive locations of the flat
+    // Section 4.2): each lane loads GB consecutive locations of the flat
     // list (all in flight), then inserts them; the slots of new locations
     // are appended to a dense list
     const uint32_t limit = kq - kq / 8;
@@ -430,7 +476,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     ctr.locations += H;
     ctr.distinct += D;
 
-    // 4. sliding-window scores (Section 4.6): score(t, j0) = sum of the
+    // 4. sliding-window scores (Section 5.6): score(t, j0) = sum of the
     // counts of (t, j0 .. j0+sws-1), for the distinct locations
     for (uint32_t i = lane; i < D; i += 32) {
         const uint32_t slot = S.dense[i];
@@ -442,11 +488,11 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     }
     __syncwarp();
 
-    // 5. top m with one candidate per target (Section 3.2 / 4.6): rounds of
+    // 5. top m with one candidate per target (Section 4.2 / 5.6): rounds of
     // warp arg-max; the winner's target is excluded from later rounds by
     // zeroing the scores of its entries.  The label is folded as the
-    // candidates come (hit threshold of Section 5.5, LCA of the close
-    // candidates of Section 3.2).  Later rounds only give lower scores, so
+    // candidates come (hit threshold of Section 6.5, LCA of the close
+    // candidates of Section 4.2).  Later rounds only give lower scores, so
     // unless the full top-m list is requested the rounds stop once the
     // query is unclassified or the best remaining score is not close.
     const int m = (int)Q.m;
@@ -513,9 +559,9 @@ template <int R, int KC, class CntT>
 __device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
                                              const Scratch<CntT>& S, Counters& ctr) {
     uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
-    int r = query_lookup<R, KC>(db, Q, q, S, S.list, n_list, sws, n_feat, n_sect);
+    int r = query_lookup<R, KC, LB_DEFAULT>(db, Q, q, S, S.list, n_list, sws, n_feat, n_sect);
     if (r != Q_DONE) return r;
-    r = query_score(db, Q, q, S, n_list, sws, ctr);
+    r = query_score<GB_DEFAULT>(db, Q, q, S, n_list, sws, ctr);
     if (r == Q_DONE) {
         ctr.features += n_feat;
         ctr.found += n_list;
@@ -548,9 +594,9 @@ constexpr uint32_t ESCALATED = 0xFFFFFFFFu;
 // many warps fit on an SM.  Writes each query's bucket list to
 // glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
 // meta; queries that need the large path are queued.
-template <int R, int KC>
+template <int R, int KC, int LB>
 __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
-                                                                  uint32_t nq, uint32_t list_cap,
+                                                                  uint32_t chunk, uint32_t list_cap,
                                                                   uint64_t* __restrict__ glist,
                                                                   uint4* __restrict__ meta,
                                                                   uint32_t* __restrict__ ovf_list,
@@ -559,12 +605,15 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
     const uint32_t w = threadIdx.x >> 5;
     const size_t per_warp = scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
     const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, 0, 0, list_cap, BUF_A, WIN_A);
+    const uint32_t total = total_queries(Q);
+    if (q0 >= total) return;
+    const uint32_t nq = min(chunk, total - q0);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = gw; i < nq; i += nwarp) {
         const uint32_t q = q0 + i;
         uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
-        int r = query_lookup<R, KC>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
+        int r = query_lookup<R, KC, LB>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
         if (r == Q_ESCALATE) {
             if (lane_id() == 0) {
                 ovf_list[atomicAdd(ovf_n, 1u)] = q;
@@ -585,9 +634,9 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
 
 // Main path, part 2 (gather + score + label): one warp per query of the
 // chunk, KA histogram slots per warp in shared memory.
-template <int KA>
+template <int KA, int GB>
 __global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
-                                                                     uint32_t nq, uint32_t list_cap,
+                                                                     uint32_t chunk, uint32_t list_cap,
                                                                      const uint64_t* __restrict__ glist,
                                                                      const uint4* __restrict__ meta,
                                                                      uint32_t* __restrict__ ovf_list,
@@ -598,6 +647,9 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb
     const size_t per_warp = scratch_bytes<uint16_t>(KA, list_cap, 0, 0);
     const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, KA, list_cap, 0, 0, WIN_A);
     Counters ctr;
+    const uint32_t total = total_queries(Q);
+    if (q0 >= total) return;
+    const uint32_t nq = min(chunk, total - q0);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
     for (uint32_t i = gw; i < nq; i += nwarp) {
@@ -607,7 +659,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb
         for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
         __syncwarp();
         const uint32_t q = q0 + i;
-        if (query_score(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
+        if (query_score<GB>(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
             if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
         } else {
             ctr.features += mt.z;
@@ -652,152 +704,338 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
     if (Q.counters && lane_id() == 0 && n_large) atomicAdd(Q.counters + 3, n_large);
 }
 
-constexpr int KA_DEFAULT = 512;
-constexpr uint32_t CHUNK = 1u << 20;  // queries per lookup/score round
+
+constexpr uint32_t CHUNK = CLASSIFY_CHUNK;
+
+using LookupKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint32_t, uint64_t*, uint4*, uint32_t*,
+                              uint32_t*);
+using ScoreKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint32_t, const uint64_t*, const uint4*,
+                             uint32_t*, uint32_t*);
+using LargeKernel = void (*)(ClassifyDb, ClassifyQuery, const uint32_t*, const uint32_t*, uint32_t*, unsigned char*,
+                             size_t);
 
 template <int R, int KC>
-cudaError_t launch_all(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
-    cudaError_t e;
-    const uint32_t list_cap = WIN_A * db.sp.s;
-    int dev = 0, sms = NUM_SMS_HINT;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-
-    const size_t smem_l = LK_WARPS * scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
-    const size_t smem_s = CLS_WARPS * scratch_bytes<uint16_t>(KA_DEFAULT, list_cap, 0, 0);
-    auto kl = k_classify_lookup<R, KC>;
-    auto ks = k_classify_score<KA_DEFAULT>;
-    if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s)) != cudaSuccess)
-        return e;
-    int occ_l = 1, occ_s = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, kl, LK_WARPS * 32, smem_l)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, CLS_WARPS * 32, smem_s)) != cudaSuccess) return e;
-    occ_l = std::max(occ_l, 1);
-    occ_s = std::max(occ_s, 1);
-
-    // scratch: overflow queue + counters, bucket lists and metadata of a chunk
-    const uint32_t chunk = std::min<uint32_t>(Q.n_q, CHUNK);
-    Tmp<uint32_t> ovf(mem, (size_t)Q.n_q + 4, s);
-    Tmp<uint64_t> glist(mem, (size_t)chunk * list_cap, s);
-    Tmp<uint4> meta(mem, chunk, s);
-    if (!ovf.ok() || !glist.ok() || !meta.ok()) return cudaErrorMemoryAllocation;
-    uint32_t* ovf_n = ovf.ptr + Q.n_q;
-    uint32_t* work = ovf_n + 1;
-    if ((e = cudaMemsetAsync(ovf_n, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-
-    for (uint32_t q0 = 0; q0 < Q.n_q; q0 += chunk) {
-        const uint32_t nq = std::min(chunk, Q.n_q - q0);
-        const uint32_t gl = (uint32_t)std::min<uint64_t>(((uint64_t)nq + LK_WARPS - 1) / LK_WARPS, (uint64_t)sms * occ_l);
-        const uint32_t gs = (uint32_t)std::min<uint64_t>(((uint64_t)nq + CLS_WARPS - 1) / CLS_WARPS, (uint64_t)sms * occ_s);
-        MC_LAUNCH("classify_lookup", s,
-                  kl<<<gl, LK_WARPS * 32, smem_l, s>>>(db, Q, q0, nq, list_cap, glist.ptr, meta.ptr, ovf.ptr, ovf_n));
-        MC_LAUNCH("classify_score", s,
-                  ks<<<gs, CLS_WARPS * 32, smem_s, s>>>(db, Q, q0, nq, list_cap, glist.ptr, meta.ptr, ovf.ptr, ovf_n));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-
-    // large path (persistent warps; exits at once if nothing was queued)
-    const uint32_t b_blocks = std::max(1u, (uint32_t)(sms * B_WARPS_PER_SM / CLS_WARPS));
-    const uint64_t b_warps = (uint64_t)b_blocks * CLS_WARPS;
-    const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
-    Tmp<unsigned char> scratch(mem, b_warps * per_warp_b, s);
-    if (!scratch.ok()) return cudaErrorMemoryAllocation;
-    MC_LAUNCH("classify_large", s,
-              k_classify_large<R, KC><<<b_blocks, CLS_WARPS * 32, 0, s>>>(db, Q, ovf.ptr, ovf_n, work, scratch.ptr,
-                                                                     per_warp_b));
-    return cudaGetLastError();
+LookupKernel lookup_for_lb(uint32_t lb) {
+    if (lb == 2) return k_classify_lookup<R, KC, 2>;
+    if (lb == 8) return k_classify_lookup<R, KC, 8>;
+    return k_classify_lookup<R, KC, 4>;
 }
 
-// Number of large-path warps of the allocation-free launch.
-constexpr uint32_t NOALLOC_B_WARPS = 8;
+LookupKernel pick_lookup(const SketchParams& sp, uint32_t lb) {
+    const int r = sketch_r_for(sp.w);
+    const bool k16 = sp.k == 16;
+    if (r == 4) return k16 ? lookup_for_lb<4, 16>(lb) : lookup_for_lb<4, 0>(lb);
+    if (r == 8) return k16 ? lookup_for_lb<8, 16>(lb) : lookup_for_lb<8, 0>(lb);
+    return k16 ? lookup_for_lb<16, 16>(lb) : lookup_for_lb<16, 0>(lb);
+}
+
+template <int KA>
+ScoreKernel score_for_gb(uint32_t gb) {
+    if (gb == 4) return k_classify_score<KA, 4>;
+    if (gb == 16) return k_classify_score<KA, 16>;
+    return k_classify_score<KA, 8>;
+}
+
+ScoreKernel pick_score(uint32_t ka, uint32_t gb) {
+    if (ka == 256) return score_for_gb<256>(gb);
+    if (ka == 1024) return score_for_gb<1024>(gb);
+    return score_for_gb<512>(gb);
+}
+
+LargeKernel pick_large(const SketchParams& sp) {
+    const int r = sketch_r_for(sp.w);
+    const bool k16 = sp.k == 16;
+    if (r == 4) return k16 ? k_classify_large<4, 16> : k_classify_large<4, 0>;
+    if (r == 8) return k16 ? k_classify_large<8, 16> : k_classify_large<8, 0>;
+    return k16 ? k_classify_large<16, 16> : k_classify_large<16, 0>;
+}
+
+// Kernels and launch shapes of one launch set.
+struct Geometry {
+    LookupKernel kl;
+    ScoreKernel ks;
+    LargeKernel kb;
+    uint32_t list_cap;
+    size_t smem_l, smem_s, per_warp_b;
+    uint32_t threads_l, threads_s, grid_l, grid_s, blocks_b;
+};
+
+cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratch& sc, Geometry* g) {
+    cudaError_t e;
+    int dev = 0, sms = NUM_SMS_HINT;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    g->list_cap = WIN_A * db.sp.s;
+    g->kl = pick_lookup(db.sp, t.probe_batch);
+    g->ks = pick_score(t.hist_slots, t.gather_batch);
+    g->kb = pick_large(db.sp);
+    g->threads_l = t.lookup_warps * 32;
+    g->threads_s = t.score_warps * 32;
+    g->smem_l = t.lookup_warps * scratch_bytes<uint16_t>(0, 0, g->list_cap, BUF_A);
+    g->smem_s = t.score_warps * scratch_bytes<uint16_t>(t.hist_slots, g->list_cap, 0, 0);
+    if ((e = cudaFuncSetAttribute(g->kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_l)) != cudaSuccess)
+        return e;
+    if ((e = cudaFuncSetAttribute(g->ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_s)) != cudaSuccess)
+        return e;
+    int occ_l = 1, occ_s = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, g->kl, g->threads_l, g->smem_l)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, g->ks, g->threads_s, g->smem_s)) != cudaSuccess)
+        return e;
+    occ_l = std::max(occ_l, 1);
+    occ_s = std::max(occ_s, 1);
+    const uint64_t c = std::max<uint32_t>(sc.chunk, 1);
+    g->grid_l = (uint32_t)std::min<uint64_t>((c + t.lookup_warps - 1) / t.lookup_warps, (uint64_t)sms * occ_l);
+    g->grid_s = (uint32_t)std::min<uint64_t>((c + t.score_warps - 1) / t.score_warps, (uint64_t)sms * occ_s);
+    g->per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
+    g->blocks_b = std::max<uint32_t>(1, sc.large_warps / CLS_WARPS);
+    return cudaSuccess;
+}
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Scratch layout of the allocation-free launch: overflow queue + counters,
-// query metadata, bucket lists, large-path working memory.
-struct NoAllocLayout {
+// Scratch layout: escalation queue + counters, chunk metadata, chunk bucket
+// lists, large-path working memory.
+struct ScratchLayout {
     size_t ovf, meta, glist, large, total;
+    uint32_t chunk;
 };
 
-NoAllocLayout noalloc_layout(uint32_t n_q, uint32_t sketch_size) {
-    NoAllocLayout L;
+ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, uint32_t large_warps) {
+    ScratchLayout L;
     const size_t list_cap = (size_t)WIN_A * sketch_size;
     const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
+    L.chunk = std::min(n_q_cap, CHUNK);
     L.ovf = 0;
-    L.meta = align256(L.ovf + ((size_t)n_q + 4) * 4);
-    L.glist = align256(L.meta + (size_t)n_q * sizeof(uint4));
-    L.large = align256(L.glist + (size_t)n_q * list_cap * 8);
-    L.total = align256(L.large + NOALLOC_B_WARPS * per_warp_b);
+    L.meta = align256(L.ovf + ((size_t)n_q_cap + 4) * 4);
+    L.glist = align256(L.meta + (size_t)L.chunk * sizeof(uint4));
+    L.large = align256(L.glist + (size_t)L.chunk * list_cap * 8);
+    L.total = align256(L.large + (size_t)large_warps * per_warp_b);
     return L;
 }
 
-template <int R, int KC>
-cudaError_t launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch, size_t scratch_len,
-                           cudaStream_t s) {
-    cudaError_t e;
-    const NoAllocLayout Lay = noalloc_layout(Q.n_q, db.sp.s);
-    if (Lay.total > scratch_len) return cudaErrorInvalidValue;
-    const uint32_t list_cap = WIN_A * db.sp.s;
-    int dev = 0, sms = NUM_SMS_HINT;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem_l = LK_WARPS * scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
-    const size_t smem_s = CLS_WARPS * scratch_bytes<uint16_t>(KA_DEFAULT, list_cap, 0, 0);
-    auto kl = k_classify_lookup<R, KC>;
-    auto ks = k_classify_score<KA_DEFAULT>;
-    if ((e = cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l)) != cudaSuccess)
-        return e;
-    if ((e = cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_s)) != cudaSuccess)
-        return e;
-    int occ_l = 1, occ_s = 1;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_l, kl, LK_WARPS * 32, smem_l)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_s, ks, CLS_WARPS * 32, smem_s)) != cudaSuccess) return e;
-    occ_l = std::max(occ_l, 1);
-    occ_s = std::max(occ_s, 1);
-    uint32_t* ovf = reinterpret_cast<uint32_t*>(scratch + Lay.ovf);
-    uint32_t* ovf_n = ovf + Q.n_q;
-    uint32_t* work = ovf_n + 1;
-    uint4* meta = reinterpret_cast<uint4*>(scratch + Lay.meta);
-    uint64_t* glist = reinterpret_cast<uint64_t*>(scratch + Lay.glist);
-    unsigned char* large = scratch + Lay.large;
-    // the queue counters are the only scratch that must start at zero
-    if ((e = cudaMemsetAsync(ovf_n, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
-    const uint32_t nq = Q.n_q;
-    const uint32_t gl = (uint32_t)std::min<uint64_t>(((uint64_t)nq + LK_WARPS - 1) / LK_WARPS, (uint64_t)sms * occ_l);
-    const uint32_t gs = (uint32_t)std::min<uint64_t>(((uint64_t)nq + CLS_WARPS - 1) / CLS_WARPS, (uint64_t)sms * occ_s);
-    MC_LAUNCH("classify_lookup", s, kl<<<gl, LK_WARPS * 32, smem_l, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
-    MC_LAUNCH("classify_score", s, ks<<<gs, CLS_WARPS * 32, smem_s, s>>>(db, Q, 0, nq, list_cap, glist, meta, ovf, ovf_n));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
+// Escalation queue counters: [0] queue length, [1] large-path work
+// counter, [2] saved queue length (autotuner).
+uint32_t* queue_counters(const ClassifyScratch& sc) { return sc.ovf + sc.n_q_cap; }
+
+cudaError_t launch_lookup(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
+                          uint32_t q0, cudaStream_t s) {
+    MC_LAUNCH("classify_lookup", s,
+              g.kl<<<g.grid_l, g.threads_l, g.smem_l, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, sc.ovf,
+                                                          queue_counters(sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
+                         uint32_t q0, cudaStream_t s) {
+    MC_LAUNCH("classify_score", s,
+              g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, sc.ovf,
+                                                          queue_counters(sc)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_large(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
+                         cudaStream_t s) {
+    uint32_t* qc = queue_counters(sc);
     MC_LAUNCH("classify_large", s,
-              k_classify_large<R, KC><<<NOALLOC_B_WARPS / CLS_WARPS, CLS_WARPS * 32, 0, s>>>(db, Q, ovf, ovf_n, work, large,
-                                                                                       per_warp_b));
+              g.kb<<<g.blocks_b, CLS_WARPS * 32, 0, s>>>(db, Q, sc.ovf, qc, qc + 1, sc.large, g.per_warp_b));
     return cudaGetLastError();
 }
 
 }  // namespace
 
-size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size) { return noalloc_layout(n_q, sketch_size).total; }
+bool tuning_valid(const Tuning& t) {
+    auto in = [](uint32_t v, std::initializer_list<uint32_t> set) {
+        for (uint32_t x : set)
+            if (v == x) return true;
+        return false;
+    };
+    return in(t.hist_slots, {256, 512, 1024}) && in(t.probe_batch, {2, 4, 8}) && in(t.gather_batch, {4, 8, 16}) &&
+           in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4});
+}
+
+uint32_t classify_default_large_warps() {
+    int dev = 0, sms = NUM_SMS_HINT;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        sms = NUM_SMS_HINT;
+    }
+    return (uint32_t)std::max(CLS_WARPS, (sms * B_WARPS_PER_SM / CLS_WARPS) * CLS_WARPS);
+}
+
+size_t classify_scratch_bytes(uint32_t n_q_cap, uint32_t sketch_size, uint32_t large_warps) {
+    return scratch_layout(n_q_cap, sketch_size, large_warps).total;
+}
+
+ClassifyScratch classify_scratch_carve(unsigned char* base, uint32_t n_q_cap, uint32_t sketch_size,
+                                       uint32_t large_warps) {
+    const ScratchLayout L = scratch_layout(n_q_cap, sketch_size, large_warps);
+    ClassifyScratch sc;
+    sc.ovf = reinterpret_cast<uint32_t*>(base + L.ovf);
+    sc.meta = reinterpret_cast<uint4*>(base + L.meta);
+    sc.glist = reinterpret_cast<uint64_t*>(base + L.glist);
+    sc.large = base + L.large;
+    sc.n_q_cap = n_q_cap;
+    sc.chunk = L.chunk;
+    sc.large_warps = large_warps;
+    return sc;
+}
+
+cudaError_t classify_enqueue(const ClassifyDb& db, const ClassifyQuery& Q, const Tuning& t, const ClassifyScratch& sc,
+                             cudaStream_t s, int* n_kernels) {
+    cudaError_t e;
+    int n = 0;
+    if (n_kernels) *n_kernels = 0;
+    if (Q.n_q == 0) return cudaSuccess;
+    if (Q.n_q > sc.n_q_cap) return cudaErrorInvalidValue;
+    Geometry g;
+    if ((e = geometry(db, t, sc, &g)) != cudaSuccess) return e;
+    // only the queue counters must start at zero
+    if ((e = cudaMemsetAsync(queue_counters(sc), 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    for (uint32_t q0 = 0; q0 < Q.n_q; q0 += sc.chunk) {
+        if ((e = launch_lookup(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
+        if ((e = launch_score(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
+        n += 2;
+        if (sc.chunk == 0) break;
+    }
+    if ((e = launch_large(g, db, Q, sc, s)) != cudaSuccess) return e;
+    if (n_kernels) *n_kernels = n + 1;
+    return cudaSuccess;
+}
+
+cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, const Tuning& t,
+                            cudaStream_t s) {
+    if (Q.n_q == 0) return cudaSuccess;
+    const uint32_t lw = classify_default_large_warps();
+    Tmp<unsigned char> buf(mem, classify_scratch_bytes(Q.n_q, db.sp.s, lw), s);
+    if (!buf.ok()) return cudaErrorMemoryAllocation;
+    const ClassifyScratch sc = classify_scratch_carve(buf.ptr, Q.n_q, db.sp.s, lw);
+    return classify_enqueue(db, Q, t, sc, s, nullptr);
+}
+
+// Number of large-path warps of the allocation-free launch.
+constexpr uint32_t NOALLOC_LARGE_WARPS = 8;
+
+size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size) {
+    return classify_scratch_bytes(n_q, sketch_size, NOALLOC_LARGE_WARPS);
+}
 
 cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch,
                                    size_t scratch_len, cudaStream_t s) {
     if (Q.n_q == 0) return cudaSuccess;
-    const int r = sketch_r_for(db.sp.w);
-    const bool k16 = db.sp.k == 16;
-    if (r == 4) return k16 ? launch_noalloc<4, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<4, 0>(db, Q, scratch, scratch_len, s);
-    if (r == 8) return k16 ? launch_noalloc<8, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<8, 0>(db, Q, scratch, scratch_len, s);
-    return k16 ? launch_noalloc<16, 16>(db, Q, scratch, scratch_len, s) : launch_noalloc<16, 0>(db, Q, scratch, scratch_len, s);
+    if (classify_noalloc_bytes(Q.n_q, db.sp.s) > scratch_len) return cudaErrorInvalidValue;
+    const ClassifyScratch sc = classify_scratch_carve(scratch, Q.n_q, db.sp.s, NOALLOC_LARGE_WARPS);
+    return classify_enqueue(db, Q, DEFAULT_TUNING, sc, s, nullptr);
 }
 
-cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& Q, cudaStream_t s) {
-    if (Q.n_q == 0) return cudaSuccess;
-    const int r = sketch_r_for(db.sp.w);
-    const bool k16 = db.sp.k == 16;
-    if (r == 4) return k16 ? launch_all<4, 16>(mem, db, Q, s) : launch_all<4, 0>(mem, db, Q, s);
-    if (r == 8) return k16 ? launch_all<8, 16>(mem, db, Q, s) : launch_all<8, 0>(mem, db, Q, s);
-    return k16 ? launch_all<16, 16>(mem, db, Q, s) : launch_all<16, 0>(mem, db, Q, s);
+cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc, uint32_t reps,
+                              cudaStream_t s, Tuning* best, std::vector<TuneRecord>* records) {
+    cudaError_t e = cudaSuccess;
+    if (Q.n_q == 0 || Q.n_q > sc.chunk || reps == 0) return cudaErrorInvalidValue;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if ((e = cudaEventCreate(&a)) != cudaSuccess) return e;
+    if ((e = cudaEventCreate(&b)) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return e;
+    }
+    uint32_t* qc = queue_counters(sc);
+    Tuning cur = DEFAULT_TUNING;
+    float best_ms = 0;
+    auto timed = [&](auto&& body, float* ms) -> cudaError_t {
+        cudaError_t err;
+        float total = 0;
+        for (uint32_t r = 0; r <= reps; ++r) {  // run 0 warms up
+            if ((err = cudaEventRecord(a, s)) != cudaSuccess) return err;
+            if ((err = body()) != cudaSuccess) return err;
+            if ((err = cudaEventRecord(b, s)) != cudaSuccess) return err;
+            if ((err = cudaEventSynchronize(b)) != cudaSuccess) return err;
+            float x = 0;
+            if ((err = cudaEventElapsedTime(&x, a, b)) != cudaSuccess) return err;
+            if (r) total += x;
+        }
+        *ms = total / reps;
+        return cudaSuccess;
+    };
+    // stage 0: lookup settings
+    {
+        bool first = true;
+        Tuning bl = cur;
+        for (uint32_t lb : {2u, 4u, 8u}) {
+            for (uint32_t lw : {4u, 8u}) {
+                Tuning t = cur;
+                t.probe_batch = lb;
+                t.lookup_warps = lw;
+                Geometry g;
+                if ((e = geometry(db, t, sc, &g)) != cudaSuccess) goto done;
+                float ms = 0;
+                e = timed(
+                    [&]() -> cudaError_t {
+                        cudaError_t err = cudaMemsetAsync(qc, 0, 2 * sizeof(uint32_t), s);
+                        return err != cudaSuccess ? err : launch_lookup(g, db, Q, sc, 0, s);
+                    },
+                    &ms);
+                if (e != cudaSuccess) goto done;
+                if (records) records->push_back(TuneRecord{t, 0, ms});
+                if (first || ms < best_ms) {
+                    best_ms = ms;
+                    bl = t;
+                    first = false;
+                }
+            }
+        }
+        cur = bl;
+    }
+    // lookup output of the chosen setting, and its queue length, for stage 1
+    {
+        Geometry g;
+        if ((e = geometry(db, cur, sc, &g)) != cudaSuccess) goto done;
+        if ((e = cudaMemsetAsync(qc, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) goto done;
+        if ((e = launch_lookup(g, db, Q, sc, 0, s)) != cudaSuccess) goto done;
+        if ((e = cudaMemcpyAsync(qc + 2, qc, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) goto done;
+    }
+    // stage 1: score settings (with the large path they leave)
+    {
+        bool first = true;
+        Tuning bs = cur;
+        for (uint32_t ka : {256u, 512u, 1024u}) {
+            for (uint32_t gb : {4u, 8u, 16u}) {
+                for (uint32_t sw : {2u, 4u}) {
+                    Tuning t = cur;
+                    t.hist_slots = ka;
+                    t.gather_batch = gb;
+                    t.score_warps = sw;
+                    Geometry g;
+                    if ((e = geometry(db, t, sc, &g)) != cudaSuccess) goto done;
+                    float ms = 0;
+                    e = timed(
+                        [&]() -> cudaError_t {
+                            cudaError_t err;
+                            if ((err = cudaMemcpyAsync(qc, qc + 2, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
+                                cudaSuccess)
+                                return err;
+                            if ((err = cudaMemsetAsync(qc + 1, 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
+                            if ((err = launch_score(g, db, Q, sc, 0, s)) != cudaSuccess) return err;
+                            return launch_large(g, db, Q, sc, s);
+                        },
+                        &ms);
+                    if (e != cudaSuccess) goto done;
+                    if (records) records->push_back(TuneRecord{t, 1, ms});
+                    if (first || ms < best_ms) {
+                        best_ms = ms;
+                        bs = t;
+                        first = false;
+                    }
+                }
+            }
+        }
+        cur = bs;
+    }
+    *best = cur;
+done:
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return e;
 }
 
 }  // namespace mc

@@ -30,7 +30,7 @@ struct SketchParams {
 
 // ---------------------------------------------------------------- hashing
 // h1: the lowbias32 mixer (C. Wellons, hash-prospector), a bijection on
-// 32-bit words, applied to the canonical k-mer code (Section 3.1).
+// 32-bit words, applied to the canonical k-mer code (Section 4.1).
 __host__ __device__ __forceinline__ uint32_t hash_h1(uint32_t x) {
     x ^= x >> 16;
     x *= 0x7feb352dU;
@@ -41,7 +41,7 @@ __host__ __device__ __forceinline__ uint32_t hash_h1(uint32_t x) {
 }
 
 // h2: MurmurHash3's 32-bit finalizer, a second bijection used only to place
-// features in the table (Section 3.1: "to counteract the biased distribution
+// features in the table (Section 4.1: "to counteract the biased distribution
 // of sketch values a second hash function h2 is applied").  Layout only: it
 // does not change any result.
 __host__ __device__ __forceinline__ uint32_t hash_h2(uint32_t x) {

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 #include "../../include/mc.h"
@@ -10,7 +11,8 @@
 namespace mc {
 
 // Launch accounting and optional per-kernel event tracing (mc_api.cu).
-void note_launch();
+void note_launch(cudaStream_t s);  // not counted while `s` is being captured
+void note_launches(uint64_t n);     // kernels of a graph replay
 struct TraceScope {
     int slot = -1;
     cudaStream_t stream = nullptr;
@@ -21,7 +23,7 @@ struct TraceScope {
     do {                                            \
         ::mc::TraceScope trace_scope_((name), (stream)); \
         __VA_ARGS__;                                \
-        ::mc::note_launch();                        \
+        ::mc::note_launch(stream);                  \
     } while (0)
 
 // Device memory through the database's allocator (stream-ordered).
@@ -133,21 +135,77 @@ struct ClassifyDb {
     SketchParams sp;
 };
 
-struct ClassifyQuery {
+// One batch of a multi-batch launch: the device pointers of an mc_batch.
+struct BatchDesc {
     const uint8_t* seq;
     const uint64_t* offs;
     const uint32_t* qoffs;
-    uint32_t n_q;
+    uint32_t* label;
+    uint32_t* hits;
+    uint32_t* top_target;
+};
+
+struct ClassifyQuery {
+    // single batch (batches == nullptr)
+    const uint8_t* seq;
+    const uint64_t* offs;
+    const uint32_t* qoffs;
+    uint32_t n_q;  // queries; in the multi-batch form the capacity the scratch was sized for
     uint32_t m, hits_min, band, max_insert;
     uint32_t* label;
     uint32_t* hits;
     uint32_t* top_target;
-    uint32_t* cands;
+    uint32_t* cands;  // indexed by query number (over all batches)
     unsigned long long* counters;
     uint32_t* status;
+    // multi-batch form: bhdr (device) = {number of batches B, total queries,
+    // then the B + 1 entry exclusive prefix of the batches' query counts};
+    // query q of the launch is query q - prefix[b] of the batch b holding it
+    const BatchDesc* batches = nullptr;
+    const uint32_t* bhdr = nullptr;
 };
 
-cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& q, cudaStream_t s);
+// Launch shape of the classification kernels (mc_tuning).
+struct Tuning {
+    uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps;
+};
+constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4};
+bool tuning_valid(const Tuning& t);
+
+// Device scratch of one classify launch set for up to n_q_cap queries.
+struct ClassifyScratch {
+    uint32_t* ovf;         // escalation queue (n_q_cap) + queue length + work counter
+    uint4* meta;           // per query of a chunk
+    uint64_t* glist;       // bucket lists of a chunk
+    unsigned char* large;  // large-path working memory
+    uint32_t n_q_cap, chunk, large_warps;
+};
+uint32_t classify_default_large_warps();
+size_t classify_scratch_bytes(uint32_t n_q_cap, uint32_t sketch_size, uint32_t large_warps);
+ClassifyScratch classify_scratch_carve(unsigned char* base, uint32_t n_q_cap, uint32_t sketch_size,
+                                       uint32_t large_warps);
+
+// Enqueues one launch set (queue reset, lookup + score per chunk, large
+// path) on `s`; no allocation, no synchronisation, so it can be captured
+// in a CUDA graph.  *n_kernels (nullable) receives the kernel launches.
+cudaError_t classify_enqueue(const ClassifyDb& db, const ClassifyQuery& q, const Tuning& t,
+                             const ClassifyScratch& sc, cudaStream_t s, int* n_kernels);
+
+// Allocates the scratch for q.n_q queries from `mem` and enqueues.
+cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const ClassifyQuery& q, const Tuning& t,
+                            cudaStream_t s);
+
+// Timing of one launch-shape candidate (autotuner).
+struct TuneRecord {
+    Tuning t;
+    uint32_t stage;  // 0 lookup, 1 score + large path
+    float ms;
+};
+// Times every lookup and score setting on the queries of q (at most one
+// chunk), reps runs each; returns the fastest setting.  Synchronises `s`.
+cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& q, const ClassifyScratch& sc,
+                              uint32_t reps, cudaStream_t s, Tuning* best, std::vector<TuneRecord>* records);
+constexpr uint32_t CLASSIFY_CHUNK = 1u << 20;  // queries per lookup/score round
 
 // Classification that allocates nothing: every scratch buffer is carved out
 // of `scratch` (scratch_len bytes, 256-byte aligned).  classify_noalloc_bytes
@@ -164,5 +222,8 @@ int report_error(int code, const char* fmt, ...);
 int classify_prepare(const mc_db* db, const mc_classify_params* params, const char* seq, const uint64_t* offs,
                      uint32_t n_queries, const uint32_t* qoffs, uint32_t* label, uint32_t* hits,
                      uint32_t* top_target, cudaStream_t stream, ClassifyDb* cdb, ClassifyQuery* q);
+// Records that classify work on `stream` reads the database's current
+// layout (a later finalize frees that layout only after this work).
+int classify_done(const mc_db* db, cudaStream_t stream);
 
 }  // namespace mc

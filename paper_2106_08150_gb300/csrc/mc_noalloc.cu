@@ -75,5 +75,5 @@ extern "C" int mc_classify_noalloc(const mc_db* db, const mc_classify_params* pa
         cudaGetLastError();
         return mc::report_error(MC_ERR_CUDA, "mc_classify_noalloc launch: %s", cudaGetErrorString(e));
     }
-    return MC_OK;
+    return mc::classify_done(db, s);
 }

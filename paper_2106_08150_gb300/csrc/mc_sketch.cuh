@@ -1,13 +1,13 @@
-// Warp-cooperative minhash sketch of one window (Section 2, Section 4.2
-// steps 1-3, Section 4.3).
+// Warp-cooperative minhash sketch of one window (Section 2, Section 5.2
+// steps 1-3, Section 5.3).
 //
 // One warp computes the sketch of one window of up to 32*R bases:
 //  1. lane l loads the R bases at window offsets R*l .. R*l+R-1 and encodes
-//     them into 2-bit codes plus an invalid-base mask (Section 4.3: "3-bit"
+//     them into 2-bit codes plus an invalid-base mask (Section 5.3: "3-bit"
 //     A,C,G,T,N representation);
 //  2. the codes of the next E = ceil((k-1)/R) lanes arrive by warp
 //     shuffles, so lane l holds the R + E*R bases its k-mers need and forms
-//     the k-mers starting at R*l .. R*l+R-1 (Section 4.3 does the same with
+//     the k-mers starting at R*l .. R*l+R-1 (Section 5.3 does the same with
 //     4-base loads and sub-warp shuffles; here the window start is any base,
 //     the stride need not be a multiple of 4);
 //  3. canonical code = min(forward, reverse complement), hashed by h1;

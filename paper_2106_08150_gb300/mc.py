@@ -53,6 +53,24 @@ class mc_db_stats_t(ctypes.Structure):
                [("load_factor", ctypes.c_double), ("finalized", ctypes.c_uint32), ("max_depth", ctypes.c_uint32)]
 
 
+class mc_batch(ctypes.Structure):
+    _fields_ = [("n_seq", ctypes.c_uint32), ("n_queries", ctypes.c_uint32), ("seq", ctypes.c_void_p),
+                ("offs", ctypes.c_void_p), ("qoffs", ctypes.c_void_p), ("label", ctypes.c_void_p),
+                ("hits", ctypes.c_void_p), ("top_target", ctypes.c_void_p)]
+
+
+class mc_tuning(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in
+                ["hist_slots", "probe_batch", "gather_batch", "lookup_warps", "score_warps"]]
+
+    def as_dict(self) -> dict:
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class mc_tuning_time(ctypes.Structure):
+    _fields_ = [("tuning", mc_tuning), ("stage", ctypes.c_uint32), ("ms", ctypes.c_float)]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -81,6 +99,18 @@ _SIGS = {
     "mc_db_dump": ([_vp, _u64, _u64, _u64, _u64, _vp, _vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64)], _i),
     "mc_window_offsets": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp], _i),
     "mc_sketch": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, _vp, _u64, _vp, _vp, _vp], _i),
+    "mc_db_save": ([_vp, ctypes.c_char_p], _i),
+    "mc_db_load": ([ctypes.c_char_p, _vp, ctypes.POINTER(_vp)], _i),
+    "mc_db_set_tuning": ([_vp, ctypes.POINTER(mc_tuning)], _i),
+    "mc_classify_batches": ([_vp, ctypes.POINTER(mc_classify_params), ctypes.POINTER(mc_tuning), _u32,
+                             ctypes.POINTER(mc_batch), _vp], _i),
+    "mc_plan_create": ([_vp, ctypes.POINTER(mc_classify_params), ctypes.POINTER(mc_tuning), _u32, _u32,
+                        ctypes.POINTER(_vp)], _i),
+    "mc_plan_run": ([_vp, _u32, ctypes.POINTER(mc_batch), _vp], _i),
+    "mc_plan_kernels": ([_vp], _i),
+    "mc_plan_free": ([_vp], None),
+    "mc_autotune": ([_vp, ctypes.POINTER(mc_classify_params), _u32, ctypes.POINTER(mc_batch), _u32,
+                     ctypes.POINTER(mc_tuning), ctypes.POINTER(mc_tuning_time), _u32, ctypes.POINTER(_u32)], _i),
     "mc_trace_enable": ([_i], _i),
     "mc_trace_report": ([ctypes.c_char_p, ctypes.c_size_t, _i], _i),
     "mc_kernel_launches": ([], _u64),
@@ -240,6 +270,16 @@ def mc_db_dump(db: int, key_lo: int = 0, key_hi: int = 1 << 32):
     return keys[:nk.value], counts[:nk.value], locs[:nl.value]
 
 
+def mc_db_save(db: int, path: str):
+    _check(_lib.mc_db_save(db, os.fsencode(path)))
+
+
+def mc_db_load(path: str, stream=None) -> int:
+    h = _vp()
+    _check(_lib.mc_db_load(os.fsencode(path), _stream(stream), ctypes.byref(h)))
+    return h.value
+
+
 def mc_window_offsets(params: mc_db_params, n_seq: int, offs, win_offs, stream=None):
     _check(_lib.mc_window_offsets(ctypes.byref(params), n_seq, _ptr(offs), _ptr(win_offs), _stream(stream)))
 
@@ -247,6 +287,70 @@ def mc_window_offsets(params: mc_db_params, n_seq: int, offs, win_offs, stream=N
 def mc_sketch(params: mc_db_params, n_seq: int, seq, offs, win_offs, n_windows: int, sketch, counts, stream=None):
     _check(_lib.mc_sketch(ctypes.byref(params), n_seq, _ptr(seq), _ptr(offs), _ptr(win_offs), n_windows,
                           _ptr(sketch), _ptr(counts), _stream(stream)))
+
+
+def tuning(**kw) -> mc_tuning:
+    """mc_tuning from keyword arguments (missing fields = 0 = default)."""
+    t = mc_tuning()
+    for k, v in kw.items():
+        setattr(t, k, int(v))
+    return t
+
+
+def batch(n_seq: int, seq, offs, qoffs, label, hits, top_target=None) -> mc_batch:
+    """mc_batch descriptor of device tensors (n_queries = len(qoffs) - 1)."""
+    n_q = (qoffs.numel() if hasattr(qoffs, "numel") else len(qoffs)) - 1
+    return mc_batch(n_seq, n_q, _ptr(seq), _ptr(offs), _ptr(qoffs), _ptr(label), _ptr(hits), _ptr(top_target))
+
+
+def _batch_array(batches):
+    arr = (mc_batch * max(1, len(batches)))(*batches)
+    return arr, len(batches)
+
+
+def mc_db_set_tuning(db: int, t: mc_tuning | None):
+    _check(_lib.mc_db_set_tuning(db, ctypes.byref(t) if t is not None else None))
+
+
+def mc_classify_batches(db: int, params: mc_classify_params, batches, t: mc_tuning | None = None, stream=None):
+    arr, n = _batch_array(batches)
+    _check(_lib.mc_classify_batches(db, ctypes.byref(params), ctypes.byref(t) if t is not None else None, n, arr,
+                                    _stream(stream)))
+
+
+class Plan:
+    """mc_plan: scratch + CUDA graph of one classify launch set, replayed by run()."""
+
+    def __init__(self, db: int, params: mc_classify_params, max_batches: int, max_queries: int,
+                 t: mc_tuning | None = None):
+        h = _vp()
+        _check(_lib.mc_plan_create(db, ctypes.byref(params), ctypes.byref(t) if t is not None else None,
+                                   max_batches, max_queries, ctypes.byref(h)))
+        self.handle = h.value
+
+    def run(self, batches, stream=None):
+        arr, n = _batch_array(batches)
+        _check(_lib.mc_plan_run(self.handle, n, arr, _stream(stream)))
+
+    @property
+    def kernels(self) -> int:
+        return _lib.mc_plan_kernels(self.handle)
+
+    def free(self):
+        if self.handle:
+            _lib.mc_plan_free(self.handle)
+            self.handle = 0
+
+
+def mc_autotune(db: int, params: mc_classify_params, batches, reps: int = 3):
+    """(best mc_tuning, [(stage, tuning dict, ms), ...]) on sample batches."""
+    arr, n = _batch_array(batches)
+    best = mc_tuning()
+    times = (mc_tuning_time * 64)()
+    nt = _u32()
+    _check(_lib.mc_autotune(db, ctypes.byref(params), n, arr, reps, ctypes.byref(best), times, 64, ctypes.byref(nt)))
+    rec = [(times[i].stage, times[i].tuning.as_dict(), float(times[i].ms)) for i in range(min(nt.value, 64))]
+    return best, rec
 
 
 def mc_trace_enable(on: bool = True):
@@ -289,6 +393,13 @@ class Database:
 
     def stats(self) -> dict:
         return mc_db_stats(self.handle)
+
+    def save(self, path: str):
+        mc_db_save(self.handle, path)
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Database":
+        return cls(mc_db_load(path, stream), None)
 
     def dump(self, lo=0, hi=1 << 32):
         return mc_db_dump(self.handle, lo, hi)

@@ -155,7 +155,7 @@ def _concat_reads(parts):
             np.append(np.concatenate(qoffs_l), np.uint32(base_s)).astype(np.uint32), np.concatenate(truth_l))
 
 
-def config0(seed: int = 1000, n_reads: int = 10_000, n_decoys: int = 1_000) -> Workload:
+def tiny_workload(seed: int = 1000, n_reads: int = 10_000, n_decoys: int = 1_000) -> Workload:
     """Tiny build+classify: 8 i.i.d. genomes of 200 kbp, taxonomy root -> 2
     genera -> 2 species each -> 2 strains each (targets are strains), 10k
     single-end 100 bp reads with 1% substitutions plus 1k i.i.d. decoys."""
@@ -167,7 +167,7 @@ def config0(seed: int = 1000, n_reads: int = 10_000, n_decoys: int = 1_000) -> W
     dblob, doffs = iid_genomes(seed + 7, [100] * n_decoys, stream_base=0xA000000000)
     d = (dblob, doffs, np.arange(n_decoys + 1, dtype=np.uint32), np.full(n_decoys, NO_GENOME, np.uint32))
     reads, roffs, qoffs, truth = _concat_reads([r, d])
-    return Workload("cfg0-tiny-8x200kbp-11kSE100", genomes, goffs, parent, taxon, reads, roffs, qoffs, truth,
+    return Workload("tiny-8x200kbp-11kSE100", genomes, goffs, parent, taxon, reads, roffs, qoffs, truth,
                     dict(DB_PARAMS), dict(CLS_PARAMS, max_insert=0),
                     recipe="8 iid uniform-ACGT genomes x 200 kbp; 3-level taxonomy; 10k SE 100 bp reads, "
                            "uniform start, random strand, 1% substitutions; 1k iid 100 bp decoys")
@@ -226,7 +226,7 @@ def genera_workload(seed: int, *, n_families: int, genera_per_family: int, speci
     return blob, goffs, parent, taxon, held
 
 
-def config1(seed: int = 1001, *, n_pairs: int = 10_000_000, n_families: int = 10, genera_per_family: int = 10,
+def mid_workload(seed: int = 1001, *, n_pairs: int = 10_000_000, n_families: int = 10, genera_per_family: int = 10,
             len_scale: float = 1.0, held_genera: int = 5, held_per_genus: int = 10) -> Workload:
     """Mid-size build+classify: 1,000 genomes (100 genera x 5 species x 2
     strains), genus length lognormal (median 3 Mbp, sigma 0.5), GC U(0.3,0.7),
@@ -242,10 +242,48 @@ def config1(seed: int = 1001, *, n_pairs: int = 10_000_000, n_families: int = 10
     reads, roffs, qoffs, truth = simulate_reads(
         seed, n_pairs, blob, goffs, paired=True, len_lo=150, len_hi=150, sub=0.005, indel=0.0005,
         frag_b=300.0, frag_sd_abs=30.0, held=held, held_frac=0.05 if held is not None else 0.0)
-    name = "cfg1-mid-1000genomes-10Mpairs" if (len_scale == 1.0 and n_families == 10 and n_pairs == 10_000_000) \
-        else f"cfg1-scaled-{n_families * genera_per_family * 10}genomes-x{len_scale:g}-{n_pairs}pairs"
+    name = "mid-1000genomes-10Mpairs" if (len_scale == 1.0 and n_families == 10 and n_pairs == 10_000_000) \
+        else f"scaled-{n_families * genera_per_family * 10}genomes-x{len_scale:g}-{n_pairs}pairs"
     return Workload(name, blob, goffs, parent, taxon, reads, roffs, qoffs, truth,
                     dict(DB_PARAMS), dict(CLS_PARAMS, max_insert=390),
                     recipe="genera of related genomes (lognormal length, GC U(0.3,0.7), species 1-5% "
                            "divergent, strains +0.1%); 2x150 bp pairs, fragment N(300,30), 0.5% sub, "
                            "0.05% indel, 5% from held-out species")
+
+
+def mixed_batches(seed: int, genomes: np.ndarray, goffs: np.ndarray, *, n_batches: int = 256,
+                  median: float = 5e4, sigma: float = 1.0, lo: int = 1000, hi: int = 2_000_000,
+                  len_lo: int = 50, len_hi: int = 300, sub: float = 0.005, indel: float = 0.0005,
+                  sizes=None):
+    """Query batches of uneven size and read length: batch sizes lognormal
+    (median, sigma) clamped to [lo, hi] (or the given `sizes`); in each batch
+    half the queries are single-end reads and half are pairs, read length
+    uniform in [len_lo, len_hi] (both mates of a pair alike), fragment
+    N(1.5 * len + 50, 0.1 * mean).  Returns a list of (reads, roffs, qoffs,
+    truth) per batch, each with its own offsets."""
+    rng = np.random.default_rng(seed)
+    if sizes is None:
+        sizes = np.clip(np.round(np.exp(rng.normal(math.log(median), sigma, n_batches))), lo, hi).astype(np.int64)
+    out = []
+    for b, n in enumerate(sizes):
+        n = int(n)
+        n_se = n // 2
+        parts = []
+        if n_se:
+            parts.append(simulate_reads(seed * 7919 + 2 * b, n_se, genomes, goffs, paired=False, len_lo=len_lo,
+                                        len_hi=len_hi, sub=sub, indel=indel, stream_base=0xA000000000))
+        if n - n_se:
+            parts.append(simulate_reads(seed * 7919 + 2 * b + 1, n - n_se, genomes, goffs, paired=True,
+                                        len_lo=len_lo, len_hi=len_hi, sub=sub, indel=indel, frag_a=1.5,
+                                        frag_b=50.0, frag_sd_rel=0.1, stream_base=0xB000000000))
+        if not parts:
+            out.append((np.zeros(0, np.uint8), np.zeros(1, np.uint64), np.zeros(1, np.uint32),
+                        np.zeros(0, np.uint32)))
+        else:
+            out.append(_concat_reads(parts))
+    return out
+
+
+def concat_batches(batches):
+    """One (reads, roffs, qoffs, truth) holding all batches in order."""
+    return _concat_reads(batches)

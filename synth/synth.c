@@ -1,6 +1,6 @@
 /*
  * Seeded synthetic inputs: genomes, taxonomies and reads shaped like the
- * workloads of the MetaCache-GPU evaluation (Section 5, Tables 1 and 2).
+ * workloads of the MetaCache-GPU evaluation (Section 6, Tables 1 and 2).
  *
  * This module holds none of the classification method's arithmetic: it only
  * draws random bases, substitutions, indels and read placements.  It is

@@ -55,3 +55,14 @@ def test_invalid_taxonomy_is_rejected(mc):
     with pytest.raises(mc.McError) as e:
         mc.mc_db_create(mc.db_params(), 3, np.array([0, 5, 1], np.uint32), stream=0)
     assert e.value.code == mc.MC_ERR_ARG
+
+
+def test_load_rejects_missing_and_foreign_files(mc, tmp_path):
+    with pytest.raises(mc.McError) as e:
+        mc.mc_db_load(str(tmp_path / "nope.mcdb"), stream=0)
+    assert e.value.code == mc.MC_ERR_ARG
+    junk = tmp_path / "junk.mcdb"
+    junk.write_bytes(b"not a database" * 10)
+    with pytest.raises(mc.McError) as e:
+        mc.mc_db_load(str(junk), stream=0)
+    assert e.value.code == mc.MC_ERR_ARG

@@ -22,7 +22,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.fixture(scope="module")
 def mid():
-    return synth.config1(seed=1001)
+    return synth.mid_workload(seed=1001)
 
 
 def test_fullsize_sampled_parity(mid):

@@ -166,13 +166,13 @@ def test_h1_avalanche():
 
 # -------------------------------------------------------------- windows
 def test_window_count_closed_form_and_paper_arithmetic():
-    # Section 4.2 defaults: w=127, k=16, overlap k-1 -> stride 112
+    # Section 5.2 defaults: w=127, k=16, overlap k-1 -> stride 112
     assert 127 - 16 + 1 == 112
     for L in list(range(0, 600)) + [10 ** 6 + 7]:
         for k, stride in [(16, 112), (16, 113), (4, 5), (1, 1)]:
             brute = sum(1 for j in range(L + 1) if j * stride <= L - k) if L >= k else 0
             assert oracle.num_windows(L, k, stride) == brute
-    # Section 5.2: reads up to the window size give one window, longer reads two
+    # Section 6.2: reads up to the window size give one window, longer reads two
     assert oracle.num_windows(100, 16, 113) == 1
     assert oracle.num_windows(128, 16, 113) == 1
     assert oracle.num_windows(150, 16, 113) == 2
@@ -230,7 +230,7 @@ def test_sketch_handles_repeats_and_small_windows():
 
 
 def test_sketch_reverse_complement_invariance():
-    """Section 3.1: canonical k-mers make a window and its reverse complement
+    """Section 4.1: canonical k-mers make a window and its reverse complement
     produce the same sketch."""
     rng = random.Random(11)
     for _ in range(60):
@@ -275,7 +275,7 @@ def test_exhaustive_lookup_on_tiny_tables():
     for key, v in expect.items():
         got = list(db.lookup(key))
         assert got == v
-        assert all(a < b for a, b in zip(got, got[1:]))  # strictly ascending (Section 3.1)
+        assert all(a < b for a, b in zip(got, got[1:]))  # strictly ascending (Section 4.1)
     absent = set(rng.getrandbits(32) for _ in range(20000)) - set(expect)
     absent |= {k + 1 for k in expect if k + 1 not in expect and k + 1 < 1 << 32}
     for key in list(absent)[:5000]:
@@ -287,7 +287,7 @@ def test_exhaustive_lookup_on_tiny_tables():
 
 
 def test_bucket_cap_keeps_the_smallest_locations():
-    """Section 3.1 cap (254 by default): a window repeated 300 times on the
+    """Section 4.1 cap (254 by default): a window repeated 300 times on the
     window grid gives each of its features 300 locations; the 254 smallest
     (target, window) pairs are kept."""
     rng = random.Random(9)
@@ -333,7 +333,7 @@ def test_lca_hand_worked_cases():
 # -------------------------------------------------------------- classify
 @pytest.fixture(scope="module")
 def tiny():
-    w = synth.config0(n_reads=1500, n_decoys=200)
+    w = synth.tiny_workload(n_reads=1500, n_decoys=200)
     db = oracle.DB(w.genomes, w.goffs, **w.db_params)
     return w, db
 
@@ -404,7 +404,7 @@ def test_lca_band_boundary():
     """Two strains of one species share most of their sequence; a read from
     one of them has two close candidates.  Just inside the band the label is
     the LCA (the species), just outside it is the top target's strain."""
-    w = synth.config1(seed=77, n_pairs=400, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=0)
+    w = synth.mid_workload(seed=77, n_pairs=400, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=0)
     db = oracle.DB(w.genomes, w.goffs, **w.db_params)
     p = dict(w.cls_params, hits_min=1)
     label, hits, top, cands = db.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, with_cands=True,
@@ -436,7 +436,7 @@ def test_lca_band_boundary():
 def test_classify_brute_force_tiny():
     """Window count statistic and sliding-window candidates recomputed from
     the raw bucket lists with Python counters, every window offset tried."""
-    w = synth.config1(seed=5, n_pairs=300, n_families=1, genera_per_family=1, len_scale=0.01, held_genera=0)
+    w = synth.mid_workload(seed=5, n_pairs=300, n_families=1, genera_per_family=1, len_scale=0.01, held_genera=0)
     p = w.db_params
     db = oracle.DB(w.genomes, w.goffs, **p)
     cp = dict(w.cls_params, max_candidates=4)

@@ -90,7 +90,7 @@ def test_sketch_matches_oracle(mc, p):
 
 
 def test_sketch_full_tiny_genomes(mc):
-    w = synth.config0(n_reads=10, n_decoys=1)
+    w = synth.tiny_workload(n_reads=10, n_decoys=1)
     win, sk, cnt = gpu_sketch(mc, w.genomes, w.goffs, **{k: w.db_params[k] for k in
                                                         ["k", "sketch_size", "window_len", "window_stride"]})
     owin, osk, ocnt = oracle.sketch(w.genomes, w.goffs, **w.db_params)
@@ -101,7 +101,7 @@ def test_sketch_full_tiny_genomes(mc):
 # ------------------------------------------------------------------- build
 @pytest.fixture(scope="module")
 def tiny():
-    return synth.config0()
+    return synth.tiny_workload()
 
 
 def test_build_dump_and_stats_tiny(mc, tiny):
@@ -136,7 +136,7 @@ def test_build_in_several_calls_and_with_empty_targets(mc):
 def test_live_extension_equals_build_from_scratch(mc):
     """Targets added after a finalize get larger ids; with keep-smallest the
     extended database equals a from-scratch build over all targets."""
-    w = synth.config1(seed=11, n_pairs=10, n_families=1, genera_per_family=2, len_scale=0.01, held_genera=0)
+    w = synth.mid_workload(seed=11, n_pairs=10, n_families=1, genera_per_family=2, len_scale=0.01, held_genera=0)
     p = dict(w.db_params, bucket_cap=4)
     odb = _oracle_db(w.genomes, w.goffs, p)
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, splits=[3, 9, 15], finalize_each=True, **p)
@@ -221,7 +221,7 @@ def test_classify_tiny_matches_oracle(mc, tiny):
 @pytest.mark.parametrize("m,hits_min,band,max_insert", [(1, 0, 0, 0), (2, 1, 50, 0), (8, 10, 100, 1000),
                                                         (3, 4, 10, 390), (4, 2, 1, 0)])
 def test_classify_parameters_match_oracle(mc, m, hits_min, band, max_insert):
-    w = synth.config1(seed=21, n_pairs=3000, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=1,
+    w = synth.mid_workload(seed=21, n_pairs=3000, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=1,
                       held_per_genus=2)
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **w.db_params)
     odb = _oracle_db(w.genomes, w.goffs, w.db_params)
@@ -231,7 +231,7 @@ def test_classify_parameters_match_oracle(mc, m, hits_min, band, max_insert):
 
 
 def test_classify_paired_genera_matches_oracle(mc):
-    w = synth.config1(seed=1001, n_pairs=20000, n_families=1, genera_per_family=3, len_scale=0.05, held_genera=1,
+    w = synth.mid_workload(seed=1001, n_pairs=20000, n_families=1, genera_per_family=3, len_scale=0.05, held_genera=1,
                       held_per_genus=3)
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **w.db_params)
     odb = _oracle_db(w.genomes, w.goffs, w.db_params)
@@ -242,7 +242,7 @@ def test_classify_paired_genera_matches_oracle(mc):
 
 
 def test_classify_other_database_parameters(mc):
-    w = synth.config1(seed=3, n_pairs=2000, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=0)
+    w = synth.mid_workload(seed=3, n_pairs=2000, n_families=1, genera_per_family=2, len_scale=0.02, held_genera=0)
     p = dict(k=12, sketch_size=8, window_len=64, window_stride=40, bucket_cap=20)
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **p)
     odb = _oracle_db(w.genomes, w.goffs, p)

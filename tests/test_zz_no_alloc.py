@@ -18,7 +18,7 @@ def test_noalloc_matches_classify_on_two_calls_in_a_row():
     import torch
     from paper_2106_08150_gb300 import mc
 
-    w = synth.config0(n_reads=4000, n_decoys=400)
+    w = synth.tiny_workload(n_reads=4000, n_decoys=400)
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **w.db_params)
     try:
         # the tiny read set plus long single-end reads whose 14 windows take
