@@ -18,6 +18,7 @@ collective), so N ranks run independent replicas (weak scaling).
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -51,6 +52,9 @@ def parse_args():
     ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
     ap.add_argument("--batches", type=int, default=256,
                     help="mixed-length query batches of the batched-classification section (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the served-loop section (0 = skip)")
+    ap.add_argument("--serve-pool", type=int, default=32, help="distinct jobs the served section cycles through")
     return ap.parse_args()
 
 
@@ -251,8 +255,12 @@ def run_gpu(args, rank, world, local_rank):
     cp = mc.classify_params(**w.cls_params)
     torch.cuda.synchronize()
 
+    tuned = None
+
     def step(seq_g, off_g, seq_r, off_r, off_q, evs=None):
         db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+        if tuned is not None:
+            mc.mc_db_set_tuning(db.handle, tuned)
         db.add_targets(seq_g, off_g, w.taxon_of_target)
         db.finalize()
         if evs is not None:
@@ -271,6 +279,11 @@ def run_gpu(args, rank, world, local_rank):
     mc.mc_classify_debug(db.handle, cp, w.n_seq, r, ro, nq, qo, label, hits, top, None, ctr, stream=stream)
     mc.mc_classify_status(db.handle, stream)
     ctr = ctr.cpu().numpy()
+    # launch shape of the classify kernels: the autotuner on the first 2^20
+    # pairs (any shape gives the same labels)
+    n_s = min(nq, 1 << 20)
+    sample = [mc.batch(int(w.qoffs[n_s]), r, ro, qo[: n_s + 1], label, hits, top)]
+    tuned, tune_rec = mc.mc_autotune(db.handle, cp, sample, reps=2)
     db.free()
     torch.cuda.synchronize()
 
@@ -423,9 +436,13 @@ def run_gpu(args, rank, world, local_rank):
         "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4)} for k, v in kernels.items()},
         "clocks": clk,
         "generation_s": round(t_gen, 1),
+        "classify_tuning": tuned.as_dict(),
     }
     if args.batches and world == 1:
         out["batched"] = run_batched(args, w, dev, stream)
+    if args.serve_seconds > 0 and world == 1 and w.held is not None:
+        rate = out.get("batched", {}).get("graph_tuned", {}).get("mreads_s")
+        out["served"] = run_served(args, w, dev, stream, rate)
     return out, w
 
 
@@ -524,6 +541,133 @@ def run_batched(args, w, dev, stream):
         "autotune_s": round(tune_s, 2), "autotune_sample_queries": n,
         "autotune_times_ms": [[r[0], r[1], round(r[2], 4)] for r in rec],
         "generation_s": round(gen_s, 1),
+    }
+
+
+# ------------------------------------------------------------ served loop
+def run_served(args, w, dev, stream, batched_rate_mreads_s: float | None):
+    """Request loop over the resident database (mc_server): Poisson job
+    arrivals at 70% of the batched throughput, job sizes lognormal (median
+    1e5, sigma 1.5) in [1e3, 5e6], read lengths U(75, 250), half single-end
+    half pairs, 5% of reads from not-yet-inserted species; the held-out
+    species are inserted live in two extensions during the run.  The same
+    arrival sequence is then replayed through the plain path (one
+    mc_classify call per job, copies in and out, one job at a time)."""
+    import torch
+    import synth
+    from paper_2106_08150_gb300 import mc
+
+    rng = np.random.default_rng(1004)
+    t0 = time.time()
+    sizes = np.clip(np.round(np.exp(rng.normal(math.log(1e5), 1.5, args.serve_pool))), 1e3, 5e6).astype(np.int64)
+    pool = synth.mixed_batches(1004, w.genomes, w.goffs, sizes=sizes, len_lo=75, len_hi=250, held=w.held,
+                               held_frac=0.05)
+    gen_s = time.time() - t0
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    jobs = [(len(r[1]) - 1, len(r[2]) - 1, pin(r[0]), pin(r[1].view(np.int64)), pin(r[2].view(np.int32)))
+            for r in pool]
+    max_q = max(j[1] for j in jobs)
+    mean_q = float(np.mean(sizes))
+    ring = 64
+    outs = [[torch.empty(max_q, dtype=torch.int32).pin_memory() for _ in range(3)] for _ in range(ring)]
+    rate_q = 0.7 * (batched_rate_mreads_s or 50.0) * 1e6
+    rate_jobs = rate_q / mean_q
+    dur = args.serve_seconds
+    n_arr = int(rng.poisson(rate_jobs * dur))
+    arrivals = np.sort(rng.uniform(0, dur, n_arr))
+    which = rng.integers(0, len(jobs), n_arr)
+    hblob, hoffs, htaxon = w.held
+    n_held = len(htaxon)
+    ext_cut = [0, n_held // 2, n_held]
+    ext_at = [dur / 3, 2 * dur / 3]
+
+    db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+    db.add_targets(torch.from_numpy(w.genomes).to(dev), torch.from_numpy(w.goffs.view(np.int64)).to(dev),
+                   w.taxon_of_target)
+    db.finalize()
+    cp = mc.classify_params(**dict(w.cls_params, max_insert=0))
+    srv = mc.Server(db.handle, cp, n_streams=3)
+    n0 = mc.mc_kernel_launches()
+    ids, epochs, next_ext = [], [], 0
+    t_start = time.perf_counter()
+    for k, (ta, jb) in enumerate(zip(arrivals, which)):
+        while next_ext < 2 and time.perf_counter() - t_start >= ext_at[next_ext]:
+            a, b = ext_cut[next_ext], ext_cut[next_ext + 1]
+            lo, hi = int(hoffs[a]), int(hoffs[b])
+            srv.extend(hblob[lo:hi], hoffs[a:b + 1] - np.uint64(lo), htaxon[a:b])
+            next_ext += 1
+        delay = ta - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        if k >= ring:
+            srv.wait(ids[k - ring])  # the output slot is free again
+        n_seq, nq, seq, offs, qo = jobs[jb]
+        o = outs[k % ring]
+        ids.append(srv.submit(n_seq, seq, offs, qo, o[0], o[1], o[2]))
+    while next_ext < 2:
+        a, b = ext_cut[next_ext], ext_cut[next_ext + 1]
+        lo, hi = int(hoffs[a]), int(hoffs[b])
+        srv.extend(hblob[lo:hi], hoffs[a:b + 1] - np.uint64(lo), htaxon[a:b])
+        next_ext += 1
+    srv.drain()
+    wall = time.perf_counter() - t_start
+    st = srv.stats()
+    launches = mc.mc_kernel_launches() - n0
+    # the last jobs ran on the final database: replay them alone and compare
+    last = [(k, ids[k]) for k in range(max(0, len(ids) - 3), len(ids))]
+    infos = {k: srv.wait(i) for k, i in last}
+    srv.free()
+    same = True
+    for k, info in infos.items():
+        if info["epoch"] != 2:
+            continue
+        n_seq, nq, seq, offs, qo = jobs[which[k]]
+        out = [torch.empty(nq, dtype=torch.int32, device=dev) for _ in range(3)]
+        mc.mc_classify(db.handle, cp, n_seq, seq.to(dev), offs.to(dev), nq, qo.to(dev), *out, stream=stream)
+        stream.synchronize()
+        same = same and all(bool(torch.equal(x.cpu(), y[:nq])) for x, y in zip(out, outs[k % ring]))
+
+    # plain path over the same arrivals on the final database, one job at a time
+    plain_dur = min(dur, 20.0)
+    lat, q_done = [], 0
+    t_start = time.perf_counter()
+    d_out = [torch.empty(max_q, dtype=torch.int32, device=dev) for _ in range(3)]
+    for ta, jb in zip(arrivals, which):
+        if ta > plain_dur:
+            break
+        delay = ta - (time.perf_counter() - t_start)
+        if delay > 0:
+            time.sleep(delay)
+        n_seq, nq, seq, offs, qo = jobs[jb]
+        with torch.cuda.stream(stream):
+            ds, do, dq = seq.to(dev, non_blocking=True), offs.to(dev, non_blocking=True), qo.to(dev, non_blocking=True)
+            mc.mc_classify(db.handle, cp, n_seq, ds, do, nq, dq, *d_out, stream=stream)
+            for x, y in zip(outs[0], d_out):
+                x[:nq].copy_(y[:nq], non_blocking=True)
+        stream.synchronize()
+        lat.append(time.perf_counter() - t_start - ta)
+        q_done += nq
+    plain_wall = time.perf_counter() - t_start
+    db.free()
+    lat = np.sort(np.array(lat)) if lat else np.zeros(1)
+    return {
+        "workload": f"Poisson job arrivals, job size lognormal(median 1e5, sigma 1.5) in [1e3, 5e6], read length "
+                    f"U(75,250), half single-end half pairs, 5% from held-out species; {n_held} held-out species "
+                    f"genomes inserted live in 2 extensions; database {w.name}",
+        "seconds": dur, "offered_jobs_s": round(rate_jobs, 2), "offered_mreads_s": round(rate_q / 1e6, 3),
+        "jobs": int(st["jobs_done"]), "queries": int(st["queries_done"]),
+        "throughput_mreads_s": round(st["queries_done"] / max(st["busy_s"], 1e-9) / 1e6, 3),
+        "wall_s": round(wall, 2), "p50_latency_s": round(st["p50_latency_s"], 4),
+        "p99_latency_s": round(st["p99_latency_s"], 4), "max_latency_s": round(st["max_latency_s"], 4),
+        "launch_sets": int(st["launch_sets"]), "gpu_launches": int(launches), "extensions": int(st["extensions"]),
+        "hbm_peak_bytes": int(st["hbm_peak"]), "hbm_limit_bytes": int(st["hbm_limit"]),
+        "final_epoch_jobs_identical_alone": bool(same), "pool_jobs": len(jobs), "generation_s": round(gen_s, 1),
+        "plain_one_job_per_launch": {
+            "seconds_of_arrivals": plain_dur, "jobs": len(lat), "queries": int(q_done),
+            "throughput_mreads_s": round(q_done / plain_wall / 1e6, 3),
+            "p50_latency_s": round(float(lat[len(lat) // 2]), 4),
+            "p99_latency_s": round(float(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))]), 4),
+        },
     }
 
 

@@ -282,6 +282,99 @@ typedef struct mc_tuning_time {
 int mc_autotune(const mc_db* db, const mc_classify_params* params, uint32_t n_batches, const mc_batch* batches,
                 uint32_t reps, mc_tuning* best, mc_tuning_time* times, uint32_t max_times, uint32_t* n_times);
 
+/* ---------------------------------------------------------------------
+ * Served classification: a resident database and a request loop.
+ *
+ * The paper holds a database in memory for an interactive session of
+ * successive queries (Section 4) and queries a database straight after its
+ * build (on-the-fly mode, Section 6.3).  mc_server runs that as a service
+ * whose database also grows while it serves: jobs (host buffers) arrive at any time from any thread; a
+ * scheduler thread inside the library admits them while their device
+ * memory fits the server's HBM limit, and packs the admitted jobs into
+ * launch sets (continuous batching: jobs that arrive while earlier sets
+ * are on the GPU go into the next set, on the next of n_streams streams,
+ * so copies and kernels of consecutive sets overlap).  Each launch set is
+ * one replay of a classification plan (mc_plan).  Extensions (new
+ * genomes) are applied between launch sets.  Every job is classified
+ * against one database state (epoch): a job split over several launch
+ * sets delays a pending extension until its last piece is enqueued, a job
+ * submitted after an extension request runs after that extension, and
+ * launch sets in flight keep reading the state they were enqueued
+ * against while an extension replaces it. */
+
+typedef struct mc_server mc_server;
+
+typedef struct mc_server_config {
+    uint32_t n_streams;          /* launch sets in flight at once (0 = 2) */
+    uint32_t max_set_queries;    /* queries per launch set (0 = 2^21); larger jobs are split */
+    uint32_t max_set_jobs;       /* job pieces per launch set (0 = 256) */
+    uint32_t reserved;
+    uint64_t hbm_limit;          /* device bytes the server may hold for job buffers
+                                    (0 = half of the free memory at creation) */
+} mc_server_config;
+
+/* A classification job.  All buffers are on the host and must stay valid
+ * (and the outputs unread) until mc_server_wait reports the job done.
+ * Page-locked host memory lets the copies run asynchronously; pageable
+ * memory is copied synchronously by the scheduler thread. */
+typedef struct mc_job {
+    uint32_t n_seq;          /* sequences (mates) */
+    uint32_t n_queries;      /* queries */
+    const char* seq;         /* host, ASCII bases */
+    const uint64_t* offs;    /* host, n_seq+1 */
+    const uint32_t* qoffs;   /* host, n_queries+1 (as in mc_classify) */
+    uint32_t* label;         /* host out, n_queries */
+    uint32_t* hits;          /* host out, n_queries */
+    uint32_t* top_target;    /* host out, n_queries (nullable) */
+} mc_job;
+
+/* Timing and state of a finished job (seconds since server creation). */
+typedef struct mc_job_info {
+    double t_submit, t_launch, t_done;
+    uint64_t epoch;          /* database epoch the job was classified against */
+    uint32_t pieces;         /* launch sets the job was split over */
+    int status;              /* MC_OK, or the error of the job */
+} mc_job_info;
+
+typedef struct mc_server_stats {
+    uint64_t jobs_submitted, jobs_done, queries_done, launch_sets, extensions;
+    uint64_t epoch;              /* database epoch now */
+    uint64_t hbm_in_use, hbm_limit, hbm_peak;
+    double p50_latency_s, p99_latency_s, max_latency_s;  /* over finished jobs */
+    double busy_s;               /* from the first submission to the last completion */
+} mc_server_stats;
+
+/* Creates a server over a finalized database.  The server owns the
+ * database's use from then on: the caller makes no other call on `db`
+ * until mc_server_free (which does not free the database). */
+int mc_server_create(mc_db* db, const mc_classify_params* params, const mc_server_config* config,
+                     mc_server** out);
+
+/* Queues a job (non-blocking) and returns its id.  MC_ERR_OOM if the job
+ * alone needs more device memory than the server's limit. */
+int mc_server_submit(mc_server* srv, const mc_job* job, uint64_t* job_id);
+
+/* Queues the insertion of new targets (host buffers, copied before the
+ * call returns; taxon ids as in mc_db_add_targets).  The scheduler adds
+ * and finalizes them between launch sets.  *first_target_id receives the
+ * id of the first new target. */
+int mc_server_extend(mc_server* srv, uint32_t n_targets, const char* seq, const uint64_t* offs,
+                     const uint32_t* taxon, uint32_t* first_target_id);
+
+/* Waits up to timeout_s seconds (< 0: forever) for a job.  MC_OK and
+ * *info (nullable) when it is done (the job's own error is info->status);
+ * MC_ERR_TIMEOUT if it is not done yet; MC_ERR_ARG for an unknown id.
+ * A job's record is dropped after the first successful wait. */
+int mc_server_wait(mc_server* srv, uint64_t job_id, double timeout_s, mc_job_info* info);
+
+/* Waits until every queued job and extension is done (timeout as above). */
+int mc_server_drain(mc_server* srv, double timeout_s);
+
+int mc_server_stats_get(mc_server* srv, mc_server_stats* out);
+
+/* Drains, stops the scheduler and releases the server's resources. */
+void mc_server_free(mc_server* srv);
+
 /* Synchronises `stream` and returns (and clears) the first device-detected
  * error of earlier mc_classify calls of this database (MC_ERR_CAPACITY for
  * a query with more distinct hit locations than the largest per-query

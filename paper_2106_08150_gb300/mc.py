@@ -71,6 +71,29 @@ class mc_tuning_time(ctypes.Structure):
     _fields_ = [("tuning", mc_tuning), ("stage", ctypes.c_uint32), ("ms", ctypes.c_float)]
 
 
+class mc_server_config(ctypes.Structure):
+    _fields_ = [("n_streams", ctypes.c_uint32), ("max_set_queries", ctypes.c_uint32),
+                ("max_set_jobs", ctypes.c_uint32), ("reserved", ctypes.c_uint32), ("hbm_limit", ctypes.c_uint64)]
+
+
+class mc_job(ctypes.Structure):
+    _fields_ = [("n_seq", ctypes.c_uint32), ("n_queries", ctypes.c_uint32), ("seq", ctypes.c_void_p),
+                ("offs", ctypes.c_void_p), ("qoffs", ctypes.c_void_p), ("label", ctypes.c_void_p),
+                ("hits", ctypes.c_void_p), ("top_target", ctypes.c_void_p)]
+
+
+class mc_job_info(ctypes.Structure):
+    _fields_ = [("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("epoch", ctypes.c_uint64), ("pieces", ctypes.c_uint32), ("status", ctypes.c_int)]
+
+
+class mc_server_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in
+                ["jobs_submitted", "jobs_done", "queries_done", "launch_sets", "extensions", "epoch", "hbm_in_use",
+                 "hbm_limit", "hbm_peak"]] + \
+               [(n, ctypes.c_double) for n in ["p50_latency_s", "p99_latency_s", "max_latency_s", "busy_s"]]
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 
@@ -111,6 +134,14 @@ _SIGS = {
     "mc_plan_free": ([_vp], None),
     "mc_autotune": ([_vp, ctypes.POINTER(mc_classify_params), _u32, ctypes.POINTER(mc_batch), _u32,
                      ctypes.POINTER(mc_tuning), ctypes.POINTER(mc_tuning_time), _u32, ctypes.POINTER(_u32)], _i),
+    "mc_server_create": ([_vp, ctypes.POINTER(mc_classify_params), ctypes.POINTER(mc_server_config),
+                          ctypes.POINTER(_vp)], _i),
+    "mc_server_submit": ([_vp, ctypes.POINTER(mc_job), ctypes.POINTER(_u64)], _i),
+    "mc_server_extend": ([_vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_u32)], _i),
+    "mc_server_wait": ([_vp, _u64, ctypes.c_double, ctypes.POINTER(mc_job_info)], _i),
+    "mc_server_drain": ([_vp, ctypes.c_double], _i),
+    "mc_server_stats_get": ([_vp, ctypes.POINTER(mc_server_stats)], _i),
+    "mc_server_free": ([_vp], None),
     "mc_trace_enable": ([_i], _i),
     "mc_trace_report": ([ctypes.c_char_p, ctypes.c_size_t, _i], _i),
     "mc_kernel_launches": ([], _u64),
@@ -351,6 +382,65 @@ def mc_autotune(db: int, params: mc_classify_params, batches, reps: int = 3):
     _check(_lib.mc_autotune(db, ctypes.byref(params), n, arr, reps, ctypes.byref(best), times, 64, ctypes.byref(nt)))
     rec = [(times[i].stage, times[i].tuning.as_dict(), float(times[i].ms)) for i in range(min(nt.value, 64))]
     return best, rec
+
+
+class Server:
+    """mc_server: a request loop over a resident database.  Jobs are host
+    arrays (numpy or pinned torch tensors); their outputs are host arrays
+    filled when wait() reports the job done."""
+
+    def __init__(self, db: int, params: mc_classify_params, n_streams: int = 2, max_set_queries: int = 0,
+                 max_set_jobs: int = 0, hbm_limit: int = 0):
+        cfg = mc_server_config(n_streams, max_set_queries, max_set_jobs, 0, hbm_limit)
+        h = _vp()
+        _check(_lib.mc_server_create(db, ctypes.byref(params), ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h.value
+        self._keep = {}
+
+    def submit(self, n_seq: int, seq, offs, qoffs, label, hits, top_target=None) -> int:
+        n_q = (qoffs.numel() if hasattr(qoffs, "numel") else len(qoffs)) - 1
+        j = mc_job(n_seq, n_q, _ptr(seq), _ptr(offs), _ptr(qoffs), _ptr(label), _ptr(hits), _ptr(top_target))
+        jid = _u64()
+        _check(_lib.mc_server_submit(self.handle, ctypes.byref(j), ctypes.byref(jid)))
+        self._keep[jid.value] = (seq, offs, qoffs, label, hits, top_target)
+        return jid.value
+
+    def extend(self, seq: np.ndarray, offs: np.ndarray, taxon: np.ndarray) -> int:
+        seq = np.ascontiguousarray(seq, dtype=np.uint8)
+        offs = np.ascontiguousarray(offs, dtype=np.uint64)
+        taxon = np.ascontiguousarray(taxon, dtype=np.uint32)
+        first = _u32()
+        _check(_lib.mc_server_extend(self.handle, len(taxon), seq.ctypes.data, offs.ctypes.data, taxon.ctypes.data,
+                                     ctypes.byref(first)))
+        return first.value
+
+    def wait(self, job_id: int, timeout: float = -1.0) -> dict | None:
+        """Job info once done; None on timeout."""
+        info = mc_job_info()
+        code = _lib.mc_server_wait(self.handle, job_id, timeout, ctypes.byref(info))
+        if code == MC_ERR_TIMEOUT:
+            return None
+        _check(code)
+        self._keep.pop(job_id, None)
+        return {n: getattr(info, n) for n, _ in mc_job_info._fields_}
+
+    def drain(self, timeout: float = -1.0) -> bool:
+        code = _lib.mc_server_drain(self.handle, timeout)
+        if code == MC_ERR_TIMEOUT:
+            return False
+        _check(code)
+        return True
+
+    def stats(self) -> dict:
+        st = mc_server_stats()
+        _check(_lib.mc_server_stats_get(self.handle, ctypes.byref(st)))
+        return {n: getattr(st, n) for n, _ in mc_server_stats._fields_}
+
+    def free(self):
+        if self.handle:
+            _lib.mc_server_free(self.handle)
+            self.handle = 0
+            self._keep.clear()
 
 
 def mc_trace_enable(on: bool = True):

@@ -51,6 +51,7 @@ def _load():
         lib.synth_fill_genera.argtypes = [u64, u64, vp, vp, u32, u32, dbl, dbl, dbl, vp, vp,
                                           u32, vp, vp, vp, i32]
         lib.synth_fill_iid_many.argtypes = [u64, u64, u64, vp, vp, vp, vp, i32]
+        lib.synth_fill_repeat_rich.argtypes = [u64, u64, u64, vp, vp, u64, dbl, dbl, vp, vp, i32]
         lib.synth_reads.argtypes = [u64, u64, u64, vp, vp, u32, vp, vp, u32, dbl, i32, u32, u32,
                                     dbl, dbl, dbl, dbl, dbl, dbl, vp, vp, vp, vp, i32]
         lib.synth_reads.restype = u64
@@ -81,6 +82,9 @@ class Workload:
     db_params: dict = field(default_factory=dict)
     cls_params: dict = field(default_factory=dict)
     recipe: str = ""
+    # genomes generated but not inserted (new species of existing genera):
+    # (ASCII blob, offsets, taxon of each); their species taxa are in parent
+    held: tuple | None = None
 
     @property
     def n_targets(self) -> int:
@@ -181,7 +185,9 @@ def genera_workload(seed: int, *, n_families: int, genera_per_family: int, speci
     GC; each species is a mutated copy of the root; each strain a further
     0.1%-mutated copy of its species.  Taxonomy root -> families -> genera ->
     species -> strains; targets are the strains.  Returns (genomes, goffs,
-    parent, taxon_of_target, held_blob, held_offs)."""
+    parent, taxon_of_target, held) with held = (blob, offs, taxon) of the
+    held-out species copies (each a species taxon of its genus that has no
+    inserted target), or None."""
     lib = _load()
     n_genera = n_families * genera_per_family
     lens = np.zeros(n_genera, dtype=np.uint64)
@@ -222,7 +228,11 @@ def genera_workload(seed: int, *, n_families: int, genera_per_family: int, speci
     t = np.arange(n_genera * species * strains)
     parent[st0 + t] = sp0 + t // strains
     taxon = (st0 + t).astype(np.uint32)
-    held = (hblob[:int(hoffs[-1])], hoffs) if len(held_genus) else None
+    held = None
+    if len(held_genus):
+        held_taxon = np.arange(n_taxa, n_taxa + len(held_genus), dtype=np.uint32)
+        parent = np.concatenate([parent, (gen0 + held_genus).astype(np.uint32)])
+        held = (hblob[:int(hoffs[-1])], hoffs, held_taxon)
     return blob, goffs, parent, taxon, held
 
 
@@ -241,20 +251,21 @@ def mid_workload(seed: int = 1001, *, n_pairs: int = 10_000_000, n_families: int
         max_len=int(60e6 * len_scale), held_genera=held_genera, held_per_genus=held_per_genus)
     reads, roffs, qoffs, truth = simulate_reads(
         seed, n_pairs, blob, goffs, paired=True, len_lo=150, len_hi=150, sub=0.005, indel=0.0005,
-        frag_b=300.0, frag_sd_abs=30.0, held=held, held_frac=0.05 if held is not None else 0.0)
+        frag_b=300.0, frag_sd_abs=30.0, held=None if held is None else held[:2],
+        held_frac=0.05 if held is not None else 0.0)
     name = "mid-1000genomes-10Mpairs" if (len_scale == 1.0 and n_families == 10 and n_pairs == 10_000_000) \
         else f"scaled-{n_families * genera_per_family * 10}genomes-x{len_scale:g}-{n_pairs}pairs"
     return Workload(name, blob, goffs, parent, taxon, reads, roffs, qoffs, truth,
                     dict(DB_PARAMS), dict(CLS_PARAMS, max_insert=390),
                     recipe="genera of related genomes (lognormal length, GC U(0.3,0.7), species 1-5% "
                            "divergent, strains +0.1%); 2x150 bp pairs, fragment N(300,30), 0.5% sub, "
-                           "0.05% indel, 5% from held-out species")
+                           "0.05% indel, 5% from held-out species", held=held)
 
 
 def mixed_batches(seed: int, genomes: np.ndarray, goffs: np.ndarray, *, n_batches: int = 256,
                   median: float = 5e4, sigma: float = 1.0, lo: int = 1000, hi: int = 2_000_000,
                   len_lo: int = 50, len_hi: int = 300, sub: float = 0.005, indel: float = 0.0005,
-                  sizes=None):
+                  sizes=None, held: tuple | None = None, held_frac: float = 0.0):
     """Query batches of uneven size and read length: batch sizes lognormal
     (median, sigma) clamped to [lo, hi] (or the given `sizes`); in each batch
     half the queries are single-end reads and half are pairs, read length
@@ -271,11 +282,13 @@ def mixed_batches(seed: int, genomes: np.ndarray, goffs: np.ndarray, *, n_batche
         parts = []
         if n_se:
             parts.append(simulate_reads(seed * 7919 + 2 * b, n_se, genomes, goffs, paired=False, len_lo=len_lo,
-                                        len_hi=len_hi, sub=sub, indel=indel, stream_base=0xA000000000))
+                                        len_hi=len_hi, sub=sub, indel=indel, stream_base=0xA000000000,
+                                        held=None if held is None else held[:2], held_frac=held_frac))
         if n - n_se:
             parts.append(simulate_reads(seed * 7919 + 2 * b + 1, n - n_se, genomes, goffs, paired=True,
                                         len_lo=len_lo, len_hi=len_hi, sub=sub, indel=indel, frag_a=1.5,
-                                        frag_b=50.0, frag_sd_rel=0.1, stream_base=0xB000000000))
+                                        frag_b=50.0, frag_sd_rel=0.1, stream_base=0xB000000000,
+                                        held=None if held is None else held[:2], held_frac=held_frac))
         if not parts:
             out.append((np.zeros(0, np.uint8), np.zeros(1, np.uint64), np.zeros(1, np.uint32),
                         np.zeros(0, np.uint32)))
@@ -287,3 +300,65 @@ def mixed_batches(seed: int, genomes: np.ndarray, goffs: np.ndarray, *, n_batche
 def concat_batches(batches):
     """One (reads, roffs, qoffs, truth) holding all batches in order."""
     return _concat_reads(batches)
+
+
+def repeat_rich_genomes(seed: int, lengths, gcs, seg: int = 5000, p_rep: float = 0.3, d_rep: float = 0.005,
+                        stream_base: int = 0xC000000000) -> tuple[np.ndarray, np.ndarray]:
+    """Eukaryote-like genomes of the given lengths: 5 kbp segments, each with
+    probability p_rep a copy (d_rep substitutions) of an earlier segment of
+    the same genome placed at its own offset, else i.i.d. with the genome's
+    GC.  Returns (blob, offsets)."""
+    lib = _load()
+    lens = np.ascontiguousarray(lengths, dtype=np.uint64)
+    gc = np.ascontiguousarray(gcs, dtype=np.float64)
+    offs = np.zeros(len(lens) + 1, dtype=np.uint64)
+    offs[1:] = np.cumsum(lens)
+    blob = np.empty(max(1, int(offs[-1])), dtype=np.uint8)
+    starts = np.ascontiguousarray(offs[:-1])
+    lib.synth_fill_repeat_rich(seed, stream_base, len(lens), _p(lens), _p(gc), seg, p_rep, d_rep, _p(blob),
+                               _p(starts), _threads())
+    return blob[:int(offs[-1])], offs
+
+
+def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_000_000, n_families: int = 98,
+                   genera_per_family: int = 10, n_euk: int = 200, len_scale: float = 1.0,
+                   euk_scale: float = 1.0) -> Workload:
+    """Large single-GPU database: genera of bacterial-like genomes as in the
+    mid workload (980 genera x 5 species x 2 strains = 9,800 genomes) plus
+    n_euk repeat-rich eukaryote-like genomes of U(50, 200) Mbp (30% of 5 kbp
+    segments repeated with 0.5% substitutions), which overfill buckets.
+    scaled=True shrinks the bacterial median to 1.1 Mbp and the eukaryote
+    lengths x0.1 (about 15 Gbp in all instead of about 58).  Taxonomy: the
+    mid-workload tree plus one family of eukaryote genera (10 species per
+    genus, one target per species).  Reads: pairs as in the mid workload."""
+    median = (1.1e6 if scaled else 3e6) * len_scale
+    blob, goffs, parent, taxon, _ = genera_workload(
+        seed, n_families=n_families, genera_per_family=genera_per_family, species=5, strains=2,
+        median_len=median, sigma=0.5, min_len=max(1000, int(20_000 * len_scale)), max_len=int(60e6 * len_scale))
+    rng = np.random.default_rng(seed)
+    f = (0.1 if scaled else 1.0) * euk_scale
+    elens = np.round(rng.uniform(50e6, 200e6, n_euk) * f).astype(np.uint64)
+    egc = rng.uniform(0.3, 0.7, n_euk)
+    eblob, eoffs = repeat_rich_genomes(seed, elens, egc)
+    genomes = np.concatenate([blob, eblob])
+    del blob
+    goffs = np.concatenate([goffs, eoffs[1:] + goffs[-1]]).astype(np.uint64)
+    # taxonomy: family -> n_euk / 10 genera -> species (= targets)
+    n_taxa = len(parent)
+    n_eg = max(1, (n_euk + 9) // 10)
+    fam = n_taxa
+    gen = np.arange(fam + 1, fam + 1 + n_eg, dtype=np.uint32)
+    sp = np.arange(fam + 1 + n_eg, fam + 1 + n_eg + n_euk, dtype=np.uint32)
+    parent = np.concatenate([parent, np.array([0], np.uint32), np.full(n_eg, fam, np.uint32),
+                             gen[np.arange(n_euk) // 10]]).astype(np.uint32)
+    taxon = np.concatenate([taxon, sp]).astype(np.uint32)
+    reads, roffs, qoffs, truth = simulate_reads(
+        seed, n_pairs, genomes, goffs, paired=True, len_lo=150, len_hi=150, sub=0.005, indel=0.0005,
+        frag_b=300.0, frag_sd_abs=30.0)
+    n_t = len(goffs) - 1
+    name = f"large-{n_t}genomes-{int(goffs[-1]) / 1e9:.1f}Gbp-{n_pairs}pairs" + ("-scaled" if scaled else "")
+    return Workload(name, genomes, goffs, parent, taxon, reads, roffs, qoffs, truth,
+                    dict(DB_PARAMS), dict(CLS_PARAMS, max_insert=390),
+                    recipe="mid-workload genera (980 genera x 10 genomes) + repeat-rich eukaryote-like genomes "
+                           "U(50,200) Mbp (30% of 5 kbp segments repeated, 0.5% sub)"
+                           + (", bacterial median 1.1 Mbp and eukaryotes x0.1" if scaled else ""))
