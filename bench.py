@@ -55,6 +55,7 @@ def parse_args():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="length of the served-loop section (0 = skip)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct jobs the served section cycles through")
+    ap.add_argument("--no-autotune", action="store_true", help="default launch shape for the classify kernels")
     return ap.parse_args()
 
 
@@ -174,10 +175,16 @@ def measured_peaks():
     return 6800.0, "fallback 6.8 TB/s"
 
 
-def kernel_source_hash() -> str:
+# sources that make up each kernel (a capture's traffic figure is valid
+# while these files are unchanged)
+_CLASSIFY_SRC = ["mc_classify.cu", "mc_sketch.cuh", "mc_common.cuh"]
+_BUILD_SRC = ["mc_build.cu", "mc_sketch.cuh", "mc_common.cuh"]
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_2106_08150_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in (_CLASSIFY_SRC if kernel.startswith("classify") else _BUILD_SRC):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -283,7 +290,8 @@ def run_gpu(args, rank, world, local_rank):
     # pairs (any shape gives the same labels)
     n_s = min(nq, 1 << 20)
     sample = [mc.batch(int(w.qoffs[n_s]), r, ro, qo[: n_s + 1], label, hits, top)]
-    tuned, tune_rec = mc.mc_autotune(db.handle, cp, sample, reps=2)
+    if not args.no_autotune:
+        tuned, tune_rec = mc.mc_autotune(db.handle, cp, sample, reps=2)
     db.free()
     torch.cuda.synchronize()
 
@@ -404,7 +412,7 @@ def run_gpu(args, rank, world, local_rank):
         tinfo = traffic_db.get(dom)
         if per_step_bytes is not None:
             per_launch_bytes = per_step_bytes / per_launch_count
-            if tinfo and tinfo.get("src_sha") == kernel_source_hash():
+            if tinfo and tinfo.get("src_sha") == kernel_source_hash(dom):
                 # DRAM bytes of one ncu capture (profiles/), scaled to this
                 # launch by the ratio of algorithmic bytes; null once the
                 # kernel sources changed after the capture
@@ -436,7 +444,7 @@ def run_gpu(args, rank, world, local_rank):
         "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4)} for k, v in kernels.items()},
         "clocks": clk,
         "generation_s": round(t_gen, 1),
-        "classify_tuning": tuned.as_dict(),
+        "classify_tuning": tuned.as_dict() if tuned is not None else "default",
     }
     if args.batches and world == 1:
         out["batched"] = run_batched(args, w, dev, stream)

@@ -51,7 +51,7 @@ def _load():
         lib.synth_fill_genera.argtypes = [u64, u64, vp, vp, u32, u32, dbl, dbl, dbl, vp, vp,
                                           u32, vp, vp, vp, i32]
         lib.synth_fill_iid_many.argtypes = [u64, u64, u64, vp, vp, vp, vp, i32]
-        lib.synth_fill_repeat_rich.argtypes = [u64, u64, u64, vp, vp, u64, dbl, dbl, vp, vp, i32]
+        lib.synth_fill_repeat_rich.argtypes = [u64, u64, u64, vp, vp, u64, dbl, dbl, dbl, u64, dbl, vp, vp, i32]
         lib.synth_reads.argtypes = [u64, u64, u64, vp, vp, u32, vp, vp, u32, dbl, i32, u32, u32,
                                     dbl, dbl, dbl, dbl, dbl, dbl, vp, vp, vp, vp, i32]
         lib.synth_reads.restype = u64
@@ -303,11 +303,14 @@ def concat_batches(batches):
 
 
 def repeat_rich_genomes(seed: int, lengths, gcs, seg: int = 5000, p_rep: float = 0.3, d_rep: float = 0.005,
+                        p_sat: float = 0.02, sat_period: int = 171, d_sat: float = 0.02,
                         stream_base: int = 0xC000000000) -> tuple[np.ndarray, np.ndarray]:
     """Eukaryote-like genomes of the given lengths: 5 kbp segments, each with
     probability p_rep a copy (d_rep substitutions) of an earlier segment of
-    the same genome placed at its own offset, else i.i.d. with the genome's
-    GC.  Returns (blob, offsets)."""
+    the same genome placed at its own offset, with probability p_sat a
+    satellite array (tandem copies of the genome's own sat_period-base unit,
+    d_sat substitutions per copy), else i.i.d. with the genome's GC.
+    Returns (blob, offsets)."""
     lib = _load()
     lens = np.ascontiguousarray(lengths, dtype=np.uint64)
     gc = np.ascontiguousarray(gcs, dtype=np.float64)
@@ -315,8 +318,8 @@ def repeat_rich_genomes(seed: int, lengths, gcs, seg: int = 5000, p_rep: float =
     offs[1:] = np.cumsum(lens)
     blob = np.empty(max(1, int(offs[-1])), dtype=np.uint8)
     starts = np.ascontiguousarray(offs[:-1])
-    lib.synth_fill_repeat_rich(seed, stream_base, len(lens), _p(lens), _p(gc), seg, p_rep, d_rep, _p(blob),
-                               _p(starts), _threads())
+    lib.synth_fill_repeat_rich(seed, stream_base, len(lens), _p(lens), _p(gc), seg, p_rep, d_rep, p_sat,
+                               sat_period, d_sat, _p(blob), _p(starts), _threads())
     return blob[:int(offs[-1])], offs
 
 
@@ -326,7 +329,8 @@ def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_0
     """Large single-GPU database: genera of bacterial-like genomes as in the
     mid workload (980 genera x 5 species x 2 strains = 9,800 genomes) plus
     n_euk repeat-rich eukaryote-like genomes of U(50, 200) Mbp (30% of 5 kbp
-    segments repeated with 0.5% substitutions), which overfill buckets.
+    segments repeated with 0.5% substitutions, 2% satellite arrays of a
+    171-base unit), which overfill buckets.
     scaled=True shrinks the bacterial median to 1.1 Mbp and the eukaryote
     lengths x0.1 (about 15 Gbp in all instead of about 58).  Taxonomy: the
     mid-workload tree plus one family of eukaryote genera (10 species per
@@ -360,5 +364,6 @@ def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_0
     return Workload(name, genomes, goffs, parent, taxon, reads, roffs, qoffs, truth,
                     dict(DB_PARAMS), dict(CLS_PARAMS, max_insert=390),
                     recipe="mid-workload genera (980 genera x 10 genomes) + repeat-rich eukaryote-like genomes "
-                           "U(50,200) Mbp (30% of 5 kbp segments repeated, 0.5% sub)"
+                           "U(50,200) Mbp (30% of 5 kbp segments repeated, 0.5% sub; 2% satellite arrays of a "
+                           "171-base unit, 2% sub)"
                            + (", bacterial median 1.1 Mbp and eukaryotes x0.1" if scaled else ""))

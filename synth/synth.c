@@ -254,13 +254,16 @@ void synth_fill_iid_many(uint64_t seed, uint64_t stream_base, uint64_t n, const 
 
 /* Repeat-rich (eukaryote-like) genomes: built from segments of `seg` bases;
  * segment k is, with probability p_rep, a copy of a uniformly chosen
- * earlier segment of the same genome with substitutions at rate d_rep,
- * else i.i.d. bases with the genome's GC.  Copies keep their own offset,
- * so a repeat starts at a different phase of the window grid whenever seg
- * is not a multiple of the window stride. */
+ * earlier segment of the same genome with substitutions at rate d_rep;
+ * else, with probability p_sat, a satellite array (tandem copies of the
+ * genome's own i.i.d. unit of sat_period bases, each copy with
+ * substitutions at rate d_sat); else i.i.d. bases with the genome's GC.
+ * Copies keep their own offset, so a repeat starts at a different phase of
+ * the window grid whenever seg is not a multiple of the window stride. */
 typedef struct {
     uint64_t seed; uint64_t stream_base; const uint64_t* len; const double* gc;
     uint64_t seg; double p_rep, d_rep;
+    double p_sat; uint64_t sat_period; double d_sat;
     char* blob; const uint64_t* off;
 } rep_ctx;
 
@@ -269,13 +272,22 @@ static void rep_item(void* vctx, uint64_t i) {
     rng_t r; rng_init(&r, c->seed, c->stream_base + i);
     char* g = c->blob + c->off[i];
     const uint64_t L = c->len[i];
+    char unit[1024];
+    const uint64_t per = c->sat_period < sizeof unit ? c->sat_period : sizeof unit;
+    for (uint64_t x = 0; x < per; ++x) unit[x] = draw_base(&r, c->gc[i]);
     for (uint64_t k = 0, pos = 0; pos < L; ++k, pos += c->seg) {
         const uint64_t n = (L - pos < c->seg) ? L - pos : c->seg;
-        if (k > 0 && rng_unif(&r) < c->p_rep) {
+        const double u = rng_unif(&r);
+        if (k > 0 && u < c->p_rep) {
             const uint64_t src = rng_below(&r, k) * c->seg;
             for (uint64_t x = 0; x < n; ++x) {
                 char b = g[src + x];
                 g[pos + x] = (rng_unif(&r) < c->d_rep) ? other_base(&r, b) : b;
+            }
+        } else if (per && u < c->p_rep + c->p_sat) {
+            for (uint64_t x = 0; x < n; ++x) {
+                char b = unit[x % per];
+                g[pos + x] = (rng_unif(&r) < c->d_sat) ? other_base(&r, b) : b;
             }
         } else {
             for (uint64_t x = 0; x < n; ++x) g[pos + x] = draw_base(&r, c->gc[i]);
@@ -284,10 +296,11 @@ static void rep_item(void* vctx, uint64_t i) {
 }
 
 void synth_fill_repeat_rich(uint64_t seed, uint64_t stream_base, uint64_t n, const uint64_t* len,
-                            const double* gc, uint64_t seg, double p_rep, double d_rep, char* blob,
-                            const uint64_t* off, int n_threads) {
+                            const double* gc, uint64_t seg, double p_rep, double d_rep, double p_sat,
+                            uint64_t sat_period, double d_sat, char* blob, const uint64_t* off, int n_threads) {
     rep_ctx c; c.seed = seed; c.stream_base = stream_base; c.len = len; c.gc = gc; c.seg = seg;
-    c.p_rep = p_rep; c.d_rep = d_rep; c.blob = blob; c.off = off;
+    c.p_rep = p_rep; c.d_rep = d_rep; c.p_sat = p_sat; c.sat_period = sat_period; c.d_sat = d_sat;
+    c.blob = blob; c.off = off;
     par_for(n, rep_item, &c, n_threads);
 }
 
