@@ -56,6 +56,9 @@ def parse_args():
                     help="length of the served-loop section (0 = skip)")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct jobs the served section cycles through")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape for the classify kernels")
+    ap.add_argument("--sections-db", choices=["main", "large"], default="main",
+                    help="database of the batched and served sections: the main workload's, or the large "
+                         "repeat-rich recipe (scaled, about 15 Gbp)")
     return ap.parse_args()
 
 
@@ -282,7 +285,7 @@ def run_gpu(args, rank, world, local_rank):
     db.add_targets(g, go, w.taxon_of_target)
     db.finalize()
     st = db.stats()
-    ctr = torch.zeros(6, dtype=torch.int64, device=dev)
+    ctr = torch.zeros(7, dtype=torch.int64, device=dev)
     mc.mc_classify_debug(db.handle, cp, w.n_seq, r, ro, nq, qo, label, hits, top, None, ctr, stream=stream)
     mc.mc_classify_status(db.handle, stream)
     ctr = ctr.cpu().numpy()
@@ -436,7 +439,8 @@ def run_gpu(args, rank, world, local_rank):
         "db": {k: st[k] for k in ["n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys", "table_slots",
                                   "max_probe", "load_factor"]},
         "classify_counters": {"features": int(ctr[0]), "locations": int(ctr[1]), "distinct_locations": int(ctr[2]),
-                              "large_path_queries": int(ctr[3]), "features_found": int(ctr[4]),
+                              "large_path_queries": int(ctr[3]), "medium_path_queries": int(ctr[6]),
+                              "features_found": int(ctr[4]),
                               "bucket_sectors": int(ctr[5])},
         "roofline": roof,
         "e2e": e2e,
@@ -446,11 +450,18 @@ def run_gpu(args, rank, world, local_rank):
         "generation_s": round(t_gen, 1),
         "classify_tuning": tuned.as_dict() if tuned is not None else "default",
     }
+    ws = w
+    if args.sections_db == "large" and world == 1 and (args.batches or args.serve_seconds > 0):
+        import synth
+        t0 = time.time()
+        ws = synth.large_workload(seed=1002, scaled=True, n_pairs=1000, held_genera=5, held_per_genus=10)
+        out["sections_db"] = {"workload": ws.name, "genomes": ws.n_targets, "genome_bp": ws.n_bp,
+                              "recipe": ws.recipe, "generation_s": round(time.time() - t0, 1)}
     if args.batches and world == 1:
-        out["batched"] = run_batched(args, w, dev, stream)
-    if args.serve_seconds > 0 and world == 1 and w.held is not None:
+        out["batched"] = run_batched(args, ws, dev, stream)
+    if args.serve_seconds > 0 and world == 1 and ws.held is not None:
         rate = out.get("batched", {}).get("graph_tuned", {}).get("mreads_s")
-        out["served"] = run_served(args, w, dev, stream, rate)
+        out["served"] = run_served(args, ws, dev, stream, rate)
     return out, w
 
 

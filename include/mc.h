@@ -453,10 +453,10 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
 /* mc_classify with test outputs.  cands (device out, nullable):
  * n_queries x max_candidates x {score, target, first window, last window}
  * of the top candidates (unused slots: score 0, target MC_NO_TARGET).
- * counters (device out, nullable, 6 x uint64, accumulated): features looked
+ * counters (device out, nullable, 7 x uint64, accumulated): features looked
  * up, locations gathered, distinct locations, queries sent to the
  * large-histogram path, features found, 32-byte sectors of the gathered
- * buckets. */
+ * buckets, queries finished on the medium-histogram path. */
 int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                       const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,

@@ -36,6 +36,8 @@ constexpr int WIN_A = 8;                     // windows per query on the shared-
 constexpr uint32_t KB_SLOTS = 1u << 16;      // large-path histogram slots per warp
 constexpr uint32_t LIST_B = MC_MAX_QUERY_WINDOWS * MAX_S;
 constexpr int B_WARPS_PER_SM = 2;
+constexpr uint32_t KM_SLOTS = 2048;          // medium-path histogram slots per warp
+constexpr int MED_WARPS = 2;                 // warps per CTA (medium path)
 constexpr int SK_NW = 2;  // windows sketched together
 
 struct Cand {
@@ -514,13 +516,14 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             const Cand c = Cand{sc, t, (uint32_t)key, 0};
             if (better(c, best)) best = c;
         }
-#pragma unroll
-        for (int o = 16; o >= 1; o >>= 1) {
-            Cand x;
-            x.score = __shfl_xor_sync(FULL_MASK, best.score, o);
-            x.t = __shfl_xor_sync(FULL_MASK, best.t, o);
-            x.j0 = __shfl_xor_sync(FULL_MASK, best.j0, o);
-            if (better(x, best)) best = x;
+        // warp arg-max in the candidate order: highest score, then smallest
+        // target, then smallest first window
+        {
+            const uint32_t ms = __reduce_max_sync(FULL_MASK, best.score);
+            const uint32_t mt = __reduce_min_sync(FULL_MASK, best.score == ms ? best.t : 0xFFFFFFFFu);
+            const uint32_t mj =
+                __reduce_min_sync(FULL_MASK, (best.score == ms && best.t == mt) ? best.j0 : 0xFFFFFFFFu);
+            best = Cand{ms, mt, mj, 0};
         }
         if (best.score == 0) break;
         prev_t = best.t;
@@ -572,7 +575,7 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
 
 // counters: [0] features looked up, [1] locations gathered, [2] distinct
 // locations, [3] queries on the large path, [4] features found, [5] 32-byte
-// sectors of the gathered buckets.
+// sectors of the gathered buckets, [6] queries finished on the medium path.
 __device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, const Counters& c) {
     const unsigned long long sect = c.sectors;
     if (Q.counters && lane_id() == 0) {
@@ -633,14 +636,15 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
 }
 
 // Main path, part 2 (gather + score + label): one warp per query of the
-// chunk, KA histogram slots per warp in shared memory.
+// chunk, KA histogram slots per warp in shared memory.  Queries whose
+// histogram does not fit are queued (chunk index) for the medium path.
 template <int KA, int GB>
-__global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+__global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                      uint32_t chunk, uint32_t list_cap,
                                                                      const uint64_t* __restrict__ glist,
                                                                      const uint4* __restrict__ meta,
-                                                                     uint32_t* __restrict__ ovf_list,
-                                                                     uint32_t* __restrict__ ovf_n) {
+                                                                     uint32_t* __restrict__ mid_list,
+                                                                     uint32_t* __restrict__ mid_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
@@ -660,7 +664,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb
         __syncwarp();
         const uint32_t q = q0 + i;
         if (query_score<GB>(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
-            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
+            if (lane == 0) mid_list[atomicAdd(mid_n, 1u)] = i;
         } else {
             ctr.features += mt.z;
             ctr.found += mt.x;
@@ -669,6 +673,53 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 6) k_classify_score(ClassifyDb
         __syncwarp();
     }
     flush_counters(Q, ctr);
+}
+
+// Medium path: the chunk's queries whose histogram did not fit the main
+// path, one warp each (work queue), KM_SLOTS histogram slots per warp in
+// shared memory, the bucket list taken over from the lookup.  Queries that
+// do not fit here either go to the large path.
+template <int GB>
+__global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+                                                                   uint32_t list_cap,
+                                                                   const uint64_t* __restrict__ glist,
+                                                                   const uint4* __restrict__ meta,
+                                                                   const uint32_t* __restrict__ mid_list,
+                                                                   const uint32_t* __restrict__ mid_n,
+                                                                   uint32_t* __restrict__ mid_work,
+                                                                   uint32_t* __restrict__ ovf_list,
+                                                                   uint32_t* __restrict__ ovf_n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const size_t per_warp = scratch_bytes<uint16_t>(KM_SLOTS, list_cap, 0, 0);
+    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, KM_SLOTS, list_cap, 0, 0, WIN_A);
+    Counters ctr;
+    const uint32_t n = *mid_n;
+    unsigned long long n_medium = 0;
+    for (;;) {
+        uint32_t k = 0;
+        if (lane == 0) k = atomicAdd(mid_work, 1u);
+        k = __shfl_sync(FULL_MASK, k, 0);
+        if (k >= n) break;
+        const uint32_t i = mid_list[k];
+        const uint4 mt = meta[i];
+        const uint64_t* src = glist + (uint64_t)i * list_cap;
+        for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
+        __syncwarp();
+        const uint32_t q = q0 + i;
+        if (query_score<GB>(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
+            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
+        } else {
+            ctr.features += mt.z;
+            ctr.found += mt.x;
+            ctr.sectors += mt.w;
+            ++n_medium;
+        }
+        __syncwarp();
+    }
+    flush_counters(Q, ctr);
+    if (Q.counters && lane == 0 && n_medium) atomicAdd(Q.counters + 6, n_medium);
 }
 
 // Large path: queries queued by the shared-memory path, one warp each, with
@@ -713,6 +764,8 @@ using ScoreKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint
                              uint32_t*, uint32_t*);
 using LargeKernel = void (*)(ClassifyDb, ClassifyQuery, const uint32_t*, const uint32_t*, uint32_t*, unsigned char*,
                              size_t);
+using MediumKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, const uint64_t*, const uint4*,
+                              const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*);
 
 template <int R, int KC>
 LookupKernel lookup_for_lb(uint32_t lb) {
@@ -754,10 +807,11 @@ LargeKernel pick_large(const SketchParams& sp) {
 struct Geometry {
     LookupKernel kl;
     ScoreKernel ks;
+    MediumKernel km;
     LargeKernel kb;
     uint32_t list_cap;
-    size_t smem_l, smem_s, per_warp_b;
-    uint32_t threads_l, threads_s, grid_l, grid_s, blocks_b;
+    size_t smem_l, smem_s, smem_m, per_warp_b;
+    uint32_t threads_l, threads_s, grid_l, grid_s, grid_m, blocks_b;
 };
 
 cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratch& sc, Geometry* g) {
@@ -769,6 +823,14 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     g->kl = pick_lookup(db.sp, t.probe_batch);
     g->ks = pick_score(t.hist_slots, t.gather_batch);
     g->kb = pick_large(db.sp);
+    g->km = k_classify_medium<GB_DEFAULT>;
+    g->smem_m = MED_WARPS * scratch_bytes<uint16_t>(KM_SLOTS, g->list_cap, 0, 0);
+    if ((e = cudaFuncSetAttribute(g->km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_m)) != cudaSuccess)
+        return e;
+    int occ_m = 1;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_m, g->km, MED_WARPS * 32, g->smem_m)) != cudaSuccess)
+        return e;
+    g->grid_m = (uint32_t)sms * (uint32_t)std::max(occ_m, 1);
     g->threads_l = t.lookup_warps * 32;
     g->threads_s = t.score_warps * 32;
     g->smem_l = t.lookup_warps * scratch_bytes<uint16_t>(0, 0, g->list_cap, BUF_A);
@@ -794,10 +856,10 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
 
 __host__ __device__ constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-// Scratch layout: escalation queue + counters, chunk metadata, chunk bucket
-// lists, large-path working memory.
+// Scratch layout: escalation queue + counters, chunk metadata, medium-path
+// queue, chunk bucket lists, large-path working memory.
 struct ScratchLayout {
-    size_t ovf, meta, glist, large, total;
+    size_t ovf, meta, mid, glist, large, total;
     uint32_t chunk;
 };
 
@@ -807,15 +869,17 @@ ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, uint32_t la
     const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     L.chunk = std::min(n_q_cap, CHUNK);
     L.ovf = 0;
-    L.meta = align256(L.ovf + ((size_t)n_q_cap + 4) * 4);
-    L.glist = align256(L.meta + (size_t)L.chunk * sizeof(uint4));
+    L.meta = align256(L.ovf + ((size_t)n_q_cap + 8) * 4);
+    L.mid = align256(L.meta + (size_t)L.chunk * sizeof(uint4));
+    L.glist = align256(L.mid + (size_t)L.chunk * 4);
     L.large = align256(L.glist + (size_t)L.chunk * list_cap * 8);
     L.total = align256(L.large + (size_t)large_warps * per_warp_b);
     return L;
 }
 
-// Escalation queue counters: [0] queue length, [1] large-path work
-// counter, [2] saved queue length (autotuner).
+// Queue counters: [0] large-path queue length, [1] large-path work counter,
+// [2] medium-path queue length, [3] medium-path work counter, [4] saved
+// large-path queue length (autotuner).
 uint32_t* queue_counters(const ClassifyScratch& sc) { return sc.ovf + sc.n_q_cap; }
 
 cudaError_t launch_lookup(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
@@ -826,11 +890,19 @@ cudaError_t launch_lookup(const Geometry& g, const ClassifyDb& db, const Classif
     return cudaGetLastError();
 }
 
+// Score (and the medium path for what it leaves) of the chunk at q0.
 cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
                          uint32_t q0, cudaStream_t s) {
+    uint32_t* qc = queue_counters(sc);
+    cudaError_t e = cudaMemsetAsync(qc + 2, 0, 2 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
     MC_LAUNCH("classify_score", s,
-              g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, sc.ovf,
-                                                          queue_counters(sc)));
+              g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, sc.mid,
+                                                          qc + 2));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    MC_LAUNCH("classify_medium", s,
+              g.km<<<g.grid_m, MED_WARPS * 32, g.smem_m, s>>>(db, Q, q0, g.list_cap, sc.glist, sc.meta, sc.mid, qc + 2,
+                                                             qc + 3, sc.ovf, qc));
     return cudaGetLastError();
 }
 
@@ -874,6 +946,7 @@ ClassifyScratch classify_scratch_carve(unsigned char* base, uint32_t n_q_cap, ui
     ClassifyScratch sc;
     sc.ovf = reinterpret_cast<uint32_t*>(base + L.ovf);
     sc.meta = reinterpret_cast<uint4*>(base + L.meta);
+    sc.mid = reinterpret_cast<uint32_t*>(base + L.mid);
     sc.glist = reinterpret_cast<uint64_t*>(base + L.glist);
     sc.large = base + L.large;
     sc.n_q_cap = n_q_cap;
@@ -896,7 +969,7 @@ cudaError_t classify_enqueue(const ClassifyDb& db, const ClassifyQuery& Q, const
     for (uint32_t q0 = 0; q0 < Q.n_q; q0 += sc.chunk) {
         if ((e = launch_lookup(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
         if ((e = launch_score(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
-        n += 2;
+        n += 3;
         if (sc.chunk == 0) break;
     }
     if ((e = launch_large(g, db, Q, sc, s)) != cudaSuccess) return e;
@@ -992,7 +1065,7 @@ cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, cons
         if ((e = geometry(db, cur, sc, &g)) != cudaSuccess) goto done;
         if ((e = cudaMemsetAsync(qc, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) goto done;
         if ((e = launch_lookup(g, db, Q, sc, 0, s)) != cudaSuccess) goto done;
-        if ((e = cudaMemcpyAsync(qc + 2, qc, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) goto done;
+        if ((e = cudaMemcpyAsync(qc + 4, qc, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) goto done;
     }
     // stage 1: score settings (with the large path they leave)
     {
@@ -1011,7 +1084,7 @@ cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, cons
                     e = timed(
                         [&]() -> cudaError_t {
                             cudaError_t err;
-                            if ((err = cudaMemcpyAsync(qc, qc + 2, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
+                            if ((err = cudaMemcpyAsync(qc, qc + 4, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
                                 cudaSuccess)
                                 return err;
                             if ((err = cudaMemsetAsync(qc + 1, 0, sizeof(uint32_t), s)) != cudaSuccess) return err;

@@ -174,8 +174,9 @@ bool tuning_valid(const Tuning& t);
 
 // Device scratch of one classify launch set for up to n_q_cap queries.
 struct ClassifyScratch {
-    uint32_t* ovf;         // escalation queue (n_q_cap) + queue length + work counter
+    uint32_t* ovf;         // large-path queue (n_q_cap) + queue counters
     uint4* meta;           // per query of a chunk
+    uint32_t* mid;         // medium-path queue of a chunk
     uint64_t* glist;       // bucket lists of a chunk
     unsigned char* large;  // large-path working memory
     uint32_t n_q_cap, chunk, large_warps;

@@ -325,7 +325,7 @@ def repeat_rich_genomes(seed: int, lengths, gcs, seg: int = 5000, p_rep: float =
 
 def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_000_000, n_families: int = 98,
                    genera_per_family: int = 10, n_euk: int = 200, len_scale: float = 1.0,
-                   euk_scale: float = 1.0) -> Workload:
+                   euk_scale: float = 1.0, held_genera: int = 0, held_per_genus: int = 10) -> Workload:
     """Large single-GPU database: genera of bacterial-like genomes as in the
     mid workload (980 genera x 5 species x 2 strains = 9,800 genomes) plus
     n_euk repeat-rich eukaryote-like genomes of U(50, 200) Mbp (30% of 5 kbp
@@ -334,11 +334,14 @@ def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_0
     scaled=True shrinks the bacterial median to 1.1 Mbp and the eukaryote
     lengths x0.1 (about 15 Gbp in all instead of about 58).  Taxonomy: the
     mid-workload tree plus one family of eukaryote genera (10 species per
-    genus, one target per species).  Reads: pairs as in the mid workload."""
+    genus, one target per species).  Reads: pairs as in the mid workload.
+    held_genera > 0 also generates held_per_genus not-inserted species
+    copies of that many genera (Workload.held), for live extension."""
     median = (1.1e6 if scaled else 3e6) * len_scale
-    blob, goffs, parent, taxon, _ = genera_workload(
+    blob, goffs, parent, taxon, held = genera_workload(
         seed, n_families=n_families, genera_per_family=genera_per_family, species=5, strains=2,
-        median_len=median, sigma=0.5, min_len=max(1000, int(20_000 * len_scale)), max_len=int(60e6 * len_scale))
+        median_len=median, sigma=0.5, min_len=max(1000, int(20_000 * len_scale)), max_len=int(60e6 * len_scale),
+        held_genera=held_genera, held_per_genus=held_per_genus)
     rng = np.random.default_rng(seed)
     f = (0.1 if scaled else 1.0) * euk_scale
     elens = np.round(rng.uniform(50e6, 200e6, n_euk) * f).astype(np.uint64)
@@ -366,4 +369,4 @@ def large_workload(seed: int = 1002, *, scaled: bool = True, n_pairs: int = 50_0
                     recipe="mid-workload genera (980 genera x 10 genomes) + repeat-rich eukaryote-like genomes "
                            "U(50,200) Mbp (30% of 5 kbp segments repeated, 0.5% sub; 2% satellite arrays of a "
                            "171-base unit, 2% sub)"
-                           + (", bacterial median 1.1 Mbp and eukaryotes x0.1" if scaled else ""))
+                           + (", bacterial median 1.1 Mbp and eukaryotes x0.1" if scaled else ""), held=held)

@@ -136,7 +136,7 @@ def test_plan_replays_new_batch_sets(mc, setup):
     total = sum(b.nq for b in dbs)
     plan = mc.Plan(db.handle, cp, max_batches=len(dbs), max_queries=total)
     try:
-        assert plan.kernels == 3
+        assert plan.kernels == 4  # lookup, score, medium path, large path
         for subset in [list(range(len(dbs))), [3, 0, 5], [7], list(range(len(dbs)))[::-1], []]:
             for b in dbs:
                 b.reset()

@@ -287,10 +287,12 @@ def test_classify_edge_queries(mc, tiny):
     db.free()
 
 
-def test_large_histogram_path(mc):
-    """300 identical targets: every feature keeps 254 locations, so a read
-    spanning three windows has about 760 distinct locations, beyond the
-    shared-memory histogram; the large path must give the same answers."""
+def test_medium_and_large_histogram_paths(mc):
+    """300 identical targets: every feature keeps 254 locations, so a 300 bp
+    read (three windows) has about 760 distinct locations, beyond the main
+    shared-memory histogram (medium path), and a 900 bp read (eight windows)
+    about 2,000, beyond the medium one (large path); both must give the
+    same answers."""
     rng = random.Random(12)
     base = _rand_seq(rng, 3000)
     n_t = 300
@@ -301,12 +303,12 @@ def test_large_histogram_path(mc):
     p = dict(k=16, sketch_size=16, window_len=128, window_stride=113, bucket_cap=254)
     db = gpu_build(mc, u8(genomes), goffs, parent, taxon, **p)
     odb = _oracle_db(genomes, goffs, p)
-    reads = [base[a:a + 300] for a in range(0, 2600, 37)]
+    reads = [base[a:a + 300] for a in range(0, 2600, 37)] + [base[a:a + 900] for a in range(0, 2000, 97)]
     roffs = offsets([len(r) for r in reads])
     qoffs = np.arange(len(reads) + 1, dtype=np.uint32)
     ctr = _check_classify(mc, db, odb, parent, taxon, "".join(reads), roffs, qoffs, m=8, hits_min=1,
                           lca_band_pct=10, max_insert=0)
-    assert ctr[3] > 0
+    assert ctr[3] > 0 and ctr[6] > 0
     db.free()
 
 
