@@ -527,6 +527,20 @@ def run_batched(args, w, dev, stream):
         return all(bool(torch.equal(x[:n], y[:n])) for (_, n, *_r), rx, ox in zip(ins, ref, out)
                    for x, y in zip(rx, ox))
 
+    # untimed: counters of all batches and a per-kernel trace of one launch set
+    ctr = torch.zeros(7, dtype=torch.int64, device=dev)
+    for (n_seq, nq, seq, offs, qo), o in zip(ins, out):
+        if nq:
+            mc.mc_classify_debug(db.handle, cp, n_seq, seq, offs, nq, qo, *o, None, ctr, stream=stream)
+    mc.mc_classify_status(db.handle, stream)
+    ctr = [int(x) for x in ctr.cpu()]
+    mc.mc_trace_report(reset=True)
+    mc.mc_trace_enable(True)
+    mc.mc_classify_batches(db.handle, cp, descs, stream=stream)
+    torch.cuda.synchronize()
+    mc.mc_trace_enable(False)
+    trace = {k: round(ms, 3) for k, (n, ms) in mc.mc_trace_report(reset=True).items()}
+
     res = {}
     res["per_batch"] = timed(lambda: per_batch(ref))
     res["one_launch_set"] = timed(lambda: mc.mc_classify_batches(db.handle, cp, descs, stream=stream))
@@ -557,6 +571,10 @@ def run_batched(args, w, dev, stream):
         "batches": len(batches), "queries": total_q, "mates": total_mates, "bases": total_bp,
         "batch_size_min": int(min(sizes)), "batch_size_max": int(max(sizes)),
         "unit": "Mreads/s", **res, "identical_results": bool(ok), "tuning": best.as_dict(),
+        "counters": {"features": ctr[0], "locations": ctr[1], "distinct_locations": ctr[2],
+                     "large_path_queries": ctr[3], "medium_path_queries": ctr[6], "features_found": ctr[4],
+                     "bucket_sectors": ctr[5]},
+        "kernel_ms_one_launch_set": trace,
         "autotune_s": round(tune_s, 2), "autotune_sample_queries": n,
         "autotune_times_ms": [[r[0], r[1], round(r[2], 4)] for r in rec],
         "generation_s": round(gen_s, 1),
