@@ -259,25 +259,44 @@ __device__ __forceinline__ uint64_t warp_sum_u64(uint64_t v) {
     return v;
 }
 
-// Query steps 1-4 of Section 5.2 on one warp (sketch every window of every
-// mate, look every feature up): the found buckets are written to `list`
-// (working memory or global scratch), packed as offset << 16 | size.  Also
-// returns the sliding-window size.
-// Returns Q_DONE, Q_ESCALATE (needs the large path) or Q_TOO_LARGE.
-// Also returns the number of features and the 32-byte sectors of the found
-// buckets (warp totals) for the counters.
-template <int R, int KC, int LB, class CntT>
-__device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
-                                            const Scratch<CntT>& S, uint64_t* __restrict__ list, uint32_t& n_list_out, uint32_t& sws_out,
-                                            uint32_t& n_feat_out, uint32_t& n_sect_out) {
+// 16-byte asynchronous copy global -> shared (completion: cp_async_wait_all).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// A query whose bases are (being) staged in working memory.  Per lane: the
+// length, window count and staging offset of mate `lane`; the rest is
+// warp-uniform.
+struct Staged {
+    int status;  // Q_DONE, Q_ESCALATE or Q_TOO_LARGE
+    uint32_t nm, shift, span, n_win;
+    uint32_t L, nw, boff;
+};
+
+// Query step 1a: reads the query's mates and stages its bases in buf (the
+// mates of a query are consecutive sequences, so this is one contiguous
+// range), placed at the same offset mod 16 as in memory.  ASYNC: every
+// 16-byte aligned chunk that holds a base of the query is copied with
+// cp.async (completion: cp_async_wait_all + __syncwarp; bytes of those
+// chunks outside the query are copied too and never read).  Otherwise the
+// aligned chunks inside the range are vector loads and the partial chunks
+// at both ends are copied byte by byte.
+template <bool ASYNC>
+__device__ __forceinline__ Staged stage_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, uint8_t* buf,
+                                              uint32_t buf_cap, uint32_t win_cap) {
     const uint32_t lane = lane_id();
-    const uint32_t lt = lanemask_lt();
     const SketchParams& p = db.sp;
+    Staged st{};
     const QueryIn in = query_in(Q, q);
     const uint32_t m0 = in.m0, m1 = in.m1;
-    if (m1 < m0 || m1 - m0 > MAX_MATES) return Q_TOO_LARGE;
+    if (m1 < m0 || m1 - m0 > MAX_MATES) {
+        st.status = Q_TOO_LARGE;
+        return st;
+    }
     const uint32_t nm = m1 - m0;
-
     // mates: lane i holds mate i's offset, length and window count
     const uint64_t o = lane <= nm ? in.offs[m0 + lane] : 0;
     const uint64_t o_next = __shfl_down_sync(FULL_MASK, o, 1);
@@ -285,8 +304,14 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     const uint64_t nw = lane < nm ? num_windows(L, p.k, p.stride) : 0;
     const uint64_t span_sum = warp_sum_u64(L);
     const uint64_t n_win = warp_sum_u64(nw);
-    if (n_win > MC_MAX_QUERY_WINDOWS) return Q_TOO_LARGE;
-    if (n_win > S.win_cap || span_sum > S.buf_cap) return Q_ESCALATE;
+    if (n_win > MC_MAX_QUERY_WINDOWS) {
+        st.status = Q_TOO_LARGE;
+        return st;
+    }
+    if (n_win > win_cap || span_sum > buf_cap) {
+        st.status = Q_ESCALATE;
+        return st;
+    }
     uint64_t boff = L;  // exclusive prefix of mate lengths
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -294,30 +319,54 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
         if ((int)lane >= d) boff += x;
     }
     boff -= L;
-
-    // 1a. stage the query's bases in working memory.  The mates of a query
-    // are consecutive sequences, so this is one contiguous range; it is
-    // copied in 16-byte chunks aligned in memory (one vector load per chunk,
-    // all in flight), placed at the same offset mod 16 in the buffer, with
-    // the partial chunks at both ends copied byte by byte.
     const uint64_t start = __shfl_sync(FULL_MASK, o, 0);
     const uintptr_t first = (uintptr_t)(in.seq + start);
     const uint32_t shift = (uint32_t)(first & 15u);
-    {
-        const uintptr_t a0 = first - shift;
-        const uint64_t n_chunks = (shift + span_sum + 15) / 16;
+    const uintptr_t a0 = first - shift;
+    const uint64_t n_chunks = (shift + span_sum + 15) / 16;
+    if (ASYNC) {
+        for (uint64_t c = lane; c < n_chunks; c += 32)
+            cp_async16(buf + 16 * c, reinterpret_cast<const void*>(a0 + 16 * c));
+        cp_async_commit();
+    } else {
         for (uint64_t c = lane; c < n_chunks; c += 32) {
             const uintptr_t cs = a0 + 16 * c;
             if (cs >= first && cs + 16 <= first + span_sum) {
-                *reinterpret_cast<uint4*>(S.buf + 16 * c) = __ldg(reinterpret_cast<const uint4*>(cs));
+                *reinterpret_cast<uint4*>(buf + 16 * c) = __ldg(reinterpret_cast<const uint4*>(cs));
             } else {
                 const uintptr_t lo = cs > first ? cs : first;
                 const uintptr_t hi = cs + 16 < first + span_sum ? cs + 16 : first + span_sum;
-                for (uintptr_t b = lo; b < hi; ++b) S.buf[b - a0] = __ldg(reinterpret_cast<const uint8_t*>(b));
+                for (uintptr_t b = lo; b < hi; ++b) buf[b - a0] = __ldg(reinterpret_cast<const uint8_t*>(b));
             }
         }
+        __syncwarp();
     }
-    __syncwarp();
+    st.status = Q_DONE;
+    st.nm = nm;
+    st.shift = shift;
+    st.span = (uint32_t)span_sum;
+    st.n_win = (uint32_t)n_win;
+    st.L = (uint32_t)L;
+    st.nw = (uint32_t)nw;
+    st.boff = (uint32_t)boff;
+    return st;
+}
+
+// Query steps 1b-4 of Section 5.2 on one warp, for a query staged in buf:
+// sketch every window of every mate, look every feature up; the found
+// buckets are written to `list` (working memory or global scratch), packed
+// as offset << 16 | size.  Also returns the sliding-window size, the number
+// of features and the 32-byte sectors of the found buckets (warp totals).
+template <int R, int KC, int LB, class CntT>
+__device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const ClassifyQuery& Q, const Scratch<CntT>& S,
+                                             const uint8_t* buf, const Staged& sq, uint64_t* __restrict__ list,
+                                             uint32_t& n_list_out, uint32_t& sws_out, uint32_t& n_feat_out,
+                                             uint32_t& n_sect_out) {
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    const SketchParams& p = db.sp;
+    const uint32_t nm = sq.nm, shift = sq.shift;
+    const uint64_t L = sq.L, nw = sq.nw, boff = sq.boff, n_win = sq.n_win, span_sum = sq.span;
 
     // 1b. sketch every window of every mate (Section 4.2: reads are windowed
     // like the targets), SK_NW windows at a time; feat[] gets the features
@@ -328,7 +377,7 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
         uint64_t jn = 0;          // its window index
         uint64_t nw_mi = __shfl_sync(FULL_MASK, nw, 0);
         for (uint64_t done = 0; done < n_win; done += SK_NW) {
-            const uint8_t* sq[SK_NW];
+            const uint8_t* sqp[SK_NW];
             uint64_t Ls[SK_NW], wss[SK_NW];
             bool act[SK_NW];
 #pragma unroll
@@ -339,13 +388,13 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
                     jn = 0;
                     nw_mi = __shfl_sync(FULL_MASK, nw, mi & 31);
                 }
-                sq[i] = S.buf + shift + __shfl_sync(FULL_MASK, boff, mi & 31);
+                sqp[i] = buf + shift + __shfl_sync(FULL_MASK, boff, mi & 31);
                 Ls[i] = act[i] ? __shfl_sync(FULL_MASK, L, mi & 31) : 0;
                 wss[i] = jn * p.stride;
                 if (act[i]) ++jn;
             }
             uint32_t f[SK_NW], cnt[SK_NW];
-            warp_sketch_multi<R, SK_NW, KC, false>(sq, Ls, wss, act, p, S.cand, f, cnt);
+            warp_sketch_multi<R, SK_NW, KC, false>(sqp, Ls, wss, act, p, S.cand, f, cnt);
 #pragma unroll
             for (int i = 0; i < SK_NW; ++i) {
                 if (lane < cnt[i]) S.feat[F + lane] = f[i];
@@ -400,6 +449,17 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
     const uint64_t span = (nm <= 1) ? span_sum : (span_sum > Q.max_insert ? span_sum : (uint64_t)Q.max_insert);
     sws_out = span >= p.k ? (uint32_t)((span - p.k + p.stride - 1) / p.stride + 1) : 0;
     n_list_out = n_list;
+}
+
+// Query steps 1-4 on one warp (staging, sketch, lookup), synchronously.
+// Returns Q_DONE, Q_ESCALATE (needs the large path) or Q_TOO_LARGE.
+template <int R, int KC, int LB, class CntT>
+__device__ __forceinline__ int query_lookup(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                            const Scratch<CntT>& S, uint64_t* __restrict__ list, uint32_t& n_list_out,
+                                            uint32_t& sws_out, uint32_t& n_feat_out, uint32_t& n_sect_out) {
+    const Staged st = stage_query<false>(db, Q, q, S.buf, S.buf_cap, S.win_cap);
+    if (st.status != Q_DONE) return st.status;
+    sketch_probe<R, KC, LB>(db, Q, S, S.buf, st, list, n_list_out, sws_out, n_feat_out, n_sect_out);
     return Q_DONE;
 }
 
@@ -594,10 +654,52 @@ constexpr uint32_t BUF_B = 16384;  // bases per query on the large path
 
 constexpr uint32_t ESCALATED = 0xFFFFFFFFu;
 
+// A Staged query kept in shared memory (per lane: L, nw, boff; then the
+// warp-uniform fields).
+constexpr size_t STAGED_BYTES = 3 * 32 * 4 + 8 * 4;
+
+__device__ __forceinline__ void save_staged(unsigned char* rec, const Staged& st) {
+    uint32_t* r = reinterpret_cast<uint32_t*>(rec);
+    const uint32_t lane = lane_id();
+    r[lane] = st.L;
+    r[32 + lane] = st.nw;
+    r[64 + lane] = st.boff;
+    if (lane == 0) {
+        r[96] = (uint32_t)st.status;
+        r[97] = st.nm;
+        r[98] = st.shift;
+        r[99] = st.span;
+        r[100] = st.n_win;
+    }
+}
+
+__device__ __forceinline__ Staged load_staged(const unsigned char* rec) {
+    const uint32_t* r = reinterpret_cast<const uint32_t*>(rec);
+    const uint32_t lane = lane_id();
+    Staged st;
+    st.L = r[lane];
+    st.nw = r[32 + lane];
+    st.boff = r[64 + lane];
+    st.status = (int)r[96];
+    st.nm = r[97];
+    st.shift = r[98];
+    st.span = r[99];
+    st.n_win = r[100];
+    return st;
+}
+
+// Shared memory of one lookup warp: working memory, a second staging buffer
+// and two staged-query records.
+__host__ __device__ constexpr size_t lookup_warp_bytes(uint32_t list_cap) {
+    return scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A) + align16(BUF_A + 16) + 2 * STAGED_BYTES;
+}
+
 // Main path, part 1 (sketch + lookup): one warp per query of the chunk
 // [q0, q0 + nq), shared memory for the query's bases and features only, so
-// many warps fit on an SM.  Writes each query's bucket list to
-// glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
+// many warps fit on an SM.  Software-pipelined: the bases of the warp's
+// next query are copied (cp.async) into the other staging buffer while the
+// current query is sketched and looked up.  Writes each query's bucket list
+// to glist[(q - q0) * list_cap ...] and {list size, sliding-window size} to
 // meta; queries that need the large path are queued.
 template <int R, int KC, int LB>
 __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
@@ -608,17 +710,33 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
                                                                   uint32_t* __restrict__ ovf_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
-    const size_t per_warp = scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
-    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, 0, 0, list_cap, BUF_A, WIN_A);
+    unsigned char* mine = smem + w * lookup_warp_bytes(list_cap);
+    const Scratch<uint16_t> S = carve<uint16_t>(mine, 0, 0, list_cap, BUF_A, WIN_A);
+    uint8_t* bufs[2];
+    bufs[0] = S.buf;
+    bufs[1] = mine + scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
+    unsigned char* recs = bufs[1] + align16(BUF_A + 16);
     const uint32_t total = total_queries(Q);
     if (q0 >= total) return;
     const uint32_t nq = min(chunk, total - q0);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
+    uint32_t cur = 0;
+    if (gw < nq) save_staged(recs, stage_query<true>(db, Q, q0 + gw, bufs[0], BUF_A, WIN_A));
     for (uint32_t i = gw; i < nq; i += nwarp) {
+        cp_async_wait_all();
+        __syncwarp();
+        const uint32_t nx = i + nwarp;
+        if (nx < nq)
+            save_staged(recs + (cur ^ 1) * STAGED_BYTES,
+                        stage_query<true>(db, Q, q0 + nx, bufs[cur ^ 1], BUF_A, WIN_A));
+        const Staged st = load_staged(recs + cur * STAGED_BYTES);
         const uint32_t q = q0 + i;
         uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
-        int r = query_lookup<R, KC, LB>(db, Q, q, S, glist + (uint64_t)i * list_cap, n_list, sws, n_feat, n_sect);
+        int r = st.status;
+        if (r == Q_DONE)
+            sketch_probe<R, KC, LB>(db, Q, S, bufs[cur], st, glist + (uint64_t)i * list_cap, n_list, sws, n_feat,
+                                    n_sect);
         if (r == Q_ESCALATE) {
             if (lane_id() == 0) {
                 ovf_list[atomicAdd(ovf_n, 1u)] = q;
@@ -634,7 +752,9 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
             meta[i] = make_uint4(n_list, sws, n_feat, n_sect);
         }
         __syncwarp();
+        cur ^= 1;
     }
+    cp_async_wait_all();
 }
 
 // Main path, part 2 (gather + score + label): one warp per query of the
@@ -835,7 +955,7 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     g->grid_m = (uint32_t)sms * (uint32_t)std::max(occ_m, 1);
     g->threads_l = t.lookup_warps * 32;
     g->threads_s = t.score_warps * 32;
-    g->smem_l = t.lookup_warps * scratch_bytes<uint16_t>(0, 0, g->list_cap, BUF_A);
+    g->smem_l = t.lookup_warps * lookup_warp_bytes(g->list_cap);
     g->smem_s = t.score_warps * scratch_bytes<uint16_t>(t.hist_slots, g->list_cap, 0, 0);
     if ((e = cudaFuncSetAttribute(g->kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_l)) != cudaSuccess)
         return e;
