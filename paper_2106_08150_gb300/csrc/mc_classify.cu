@@ -712,30 +712,29 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
     const uint32_t w = threadIdx.x >> 5;
     unsigned char* mine = smem + w * lookup_warp_bytes(list_cap);
     const Scratch<uint16_t> S = carve<uint16_t>(mine, 0, 0, list_cap, BUF_A, WIN_A);
-    uint8_t* bufs[2];
-    bufs[0] = S.buf;
-    bufs[1] = mine + scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
-    unsigned char* recs = bufs[1] + align16(BUF_A + 16);
+    uint8_t* const buf0 = S.buf;
+    uint8_t* const buf1 = mine + scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A);
+    unsigned char* recs = buf1 + align16(BUF_A + 16);
     const uint32_t total = total_queries(Q);
     if (q0 >= total) return;
     const uint32_t nq = min(chunk, total - q0);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
     uint32_t cur = 0;
-    if (gw < nq) save_staged(recs, stage_query<true>(db, Q, q0 + gw, bufs[0], BUF_A, WIN_A));
+    if (gw < nq) save_staged(recs, stage_query<true>(db, Q, q0 + gw, buf0, BUF_A, WIN_A));
     for (uint32_t i = gw; i < nq; i += nwarp) {
         cp_async_wait_all();
         __syncwarp();
         const uint32_t nx = i + nwarp;
         if (nx < nq)
             save_staged(recs + (cur ^ 1) * STAGED_BYTES,
-                        stage_query<true>(db, Q, q0 + nx, bufs[cur ^ 1], BUF_A, WIN_A));
+                        stage_query<true>(db, Q, q0 + nx, cur ? buf0 : buf1, BUF_A, WIN_A));
         const Staged st = load_staged(recs + cur * STAGED_BYTES);
         const uint32_t q = q0 + i;
         uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
         int r = st.status;
         if (r == Q_DONE)
-            sketch_probe<R, KC, LB>(db, Q, S, bufs[cur], st, glist + (uint64_t)i * list_cap, n_list, sws, n_feat,
+            sketch_probe<R, KC, LB>(db, Q, S, cur ? buf1 : buf0, st, glist + (uint64_t)i * list_cap, n_list, sws, n_feat,
                                     n_sect);
         if (r == Q_ESCALATE) {
             if (lane_id() == 0) {
