@@ -426,6 +426,21 @@ def run_gpu(args, rank, world, local_rank):
                     "frac": round(achieved / peak, 4), "traffic": traffic,
                     "algorithmic_bytes_per_launch": per_launch_bytes, "peak_source": peak_src + " (burst)"}
 
+    # random-access roofline: the feature-table probes and bucket gathers
+    # read 16-32 bytes at random positions, which HBM serves far below the
+    # copy bandwidth; measured here on this GPU (8 GiB buffer, 2^28 reads)
+    rand = {w_: round(mc.mc_measure_random_read(8 << 30, w_, 1 << 28, stream), 1) for w_ in (16, 32)}
+    rand_roof = {"read16_gbs": rand[16], "read32_gbs": rand[32], "unit": "GB/s",
+                 "note": "best of 6 shapes of random aligned reads of 16 / 32 bytes, 8 GiB buffer; the classify "
+                         "kernels' algorithmic bytes count 32-byte sectors, so they are compared with read32_gbs"}
+    for kname in ("classify_lookup", "classify_score"):
+        if kname in kernels:
+            b = algorithmic_bytes(kname, w, st, ctr)
+            per = kernels[kname]["launches"] / args.steps
+            if b is not None and per:
+                ach = b / per / (kernels[kname]["avg_ms"] * 1e-3) / 1e9
+                rand_roof[kname] = {"achieved_gbs": round(ach, 1), "frac_of_read32": round(ach / rand[32], 4)}
+
     value = whole_job_rate(nq, world, args.steps, total_ms)
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -443,6 +458,7 @@ def run_gpu(args, rank, world, local_rank):
                               "features_found": int(ctr[4]),
                               "bucket_sectors": int(ctr[5])},
         "roofline": roof,
+        "random_access_roofline": rand_roof,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4)} for k, v in kernels.items()},

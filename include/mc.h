@@ -462,6 +462,19 @@ int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,
                       void* stream);
 
+/* Random-access read bandwidth of the current device (the roofline of the
+ * feature-table probes and bucket gathers, which read 16-32 bytes at
+ * random positions): n_reads reads of `width` bytes (16 or 32, aligned) at
+ * uniformly random positions of a fresh device buffer of buf_bytes
+ * (>= 1 MiB; take it much larger than L2), 8 reads in flight per thread,
+ * at 16, 32 and 64 warps per SM and two index generators, each timed with
+ * CUDA events after a warm-up launch.  *gbs receives the best
+ * width x reads / time in GB/s (more requests in flight can lower random
+ * DRAM throughput, so the best shape is the roofline).  The buffer comes from
+ * cudaMallocAsync on `stream` and is freed before the call returns
+ * (synchronises `stream`).  Not part of the method: a measurement aid. */
+int mc_measure_random_read(uint64_t buf_bytes, uint32_t width, uint64_t n_reads, void* stream, double* gbs);
+
 /* ---------------------------------------------------------------------
  * Tracing and launch accounting (no counterpart in the paper beyond its
  * per-stage breakdown, Section 6.4).

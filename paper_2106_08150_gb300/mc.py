@@ -142,6 +142,7 @@ _SIGS = {
     "mc_server_drain": ([_vp, ctypes.c_double], _i),
     "mc_server_stats_get": ([_vp, ctypes.POINTER(mc_server_stats)], _i),
     "mc_server_free": ([_vp], None),
+    "mc_measure_random_read": ([_u64, _u32, _u64, _vp, ctypes.POINTER(ctypes.c_double)], _i),
     "mc_trace_enable": ([_i], _i),
     "mc_trace_report": ([ctypes.c_char_p, ctypes.c_size_t, _i], _i),
     "mc_kernel_launches": ([], _u64),
@@ -441,6 +442,13 @@ class Server:
             _lib.mc_server_free(self.handle)
             self.handle = 0
             self._keep.clear()
+
+
+def mc_measure_random_read(buf_bytes: int, width: int, n_reads: int, stream=None) -> float:
+    """GB/s of `width`-byte reads at random positions of a buf_bytes buffer."""
+    v = ctypes.c_double()
+    _check(_lib.mc_measure_random_read(buf_bytes, width, n_reads, _stream(stream), ctypes.byref(v)))
+    return v.value
 
 
 def mc_trace_enable(on: bool = True):

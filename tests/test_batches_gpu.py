@@ -245,3 +245,11 @@ def test_classify_in_flight_during_extension_sees_its_epoch(mc):
         _assert_same(b.result(), want)
     finally:
         db.free()
+
+
+def test_random_read_bandwidth_is_measured(mc):
+    g16 = mc.mc_measure_random_read(1 << 30, 16, 1 << 24)
+    g32 = mc.mc_measure_random_read(1 << 30, 32, 1 << 24)
+    assert 10.0 < g16 < 20000.0 and 10.0 < g32 < 20000.0
+    with pytest.raises(mc.McError):
+        mc.mc_measure_random_read(1 << 30, 24, 1 << 20)
