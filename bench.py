@@ -738,9 +738,9 @@ def oracle_sample(w, n_genera: int, n_pairs: int):
     return genomes, goffs, reads, roffs, qoffs, n_t
 
 
-def time_oracle(w, n_genera: int, n_pairs: int):
+def time_oracle(w, n_genera: int, n_pairs: int, threads: int = 0):
     import oracle
-    cores = os.cpu_count() or 1
+    cores = threads or os.cpu_count() or 1
     genomes, goffs, reads, roffs, qoffs, n_t = oracle_sample(w, n_genera, n_pairs)
     t0 = time.perf_counter()
     odb = oracle.DB(genomes, goffs, n_threads=cores, **w.db_params)
@@ -800,6 +800,8 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             cb, _ = time_oracle(w, args.cpu_sample_genera, args.cpu_sample_pairs)
+            one, _ = time_oracle(w, 1, 2000, threads=1)
+            cb["single_thread"] = {k: one[k] for k in ("value", "sample", "build_gbps", "classify_mreads_s")}
             out["cpu_baseline"] = cb
         else:
             out["cpu_baseline"] = None
