@@ -725,11 +725,12 @@ def run_served(args, w, dev, stream, batched_rate_mreads_s: float | None):
 
 
 # ------------------------------------------------------------ CPU arms
-def oracle_sample(w, n_genera: int, n_pairs: int):
-    """A bounded slice of the workload: the first n_genera genera (10 genomes
-    each) and read pairs drawn from them, generated like the full reads."""
+def oracle_sample(w, n_targets: int, n_pairs: int):
+    """A bounded slice of the workload: the first n_targets genomes (a genus
+    is 10 genomes) and read pairs drawn from them, generated like the full
+    reads."""
     import synth
-    n_t = min(w.n_targets, 10 * n_genera)
+    n_t = min(w.n_targets, n_targets)
     hi = int(w.goffs[n_t])
     genomes, goffs = w.genomes[:hi], w.goffs[:n_t + 1].copy()
     reads, roffs, qoffs, _ = synth.simulate_reads(
@@ -738,10 +739,10 @@ def oracle_sample(w, n_genera: int, n_pairs: int):
     return genomes, goffs, reads, roffs, qoffs, n_t
 
 
-def time_oracle(w, n_genera: int, n_pairs: int, threads: int = 0):
+def time_oracle(w, n_targets: int, n_pairs: int, threads: int = 0):
     import oracle
     cores = threads or os.cpu_count() or 1
-    genomes, goffs, reads, roffs, qoffs, n_t = oracle_sample(w, n_genera, n_pairs)
+    genomes, goffs, reads, roffs, qoffs, n_t = oracle_sample(w, n_targets, n_pairs)
     t0 = time.perf_counter()
     odb = oracle.DB(genomes, goffs, n_threads=cores, **w.db_params)
     tb = time.perf_counter() - t0
@@ -764,11 +765,11 @@ def run_reference(args, rank, world):
     w = make_workload(args.workload, 0)
     n_gen, n_pairs = max(1, args.cpu_sample_genera // 2), max(1000, args.cpu_sample_pairs // 4)
     for _ in range(args.warmup):
-        time_oracle(w, n_gen, n_pairs)
+        time_oracle(w, 10 * n_gen, n_pairs)
     vals, secs = [], 0.0
     last = None
     for _ in range(args.steps):
-        last, s = time_oracle(w, n_gen, n_pairs)
+        last, s = time_oracle(w, 10 * n_gen, n_pairs)
         vals.append(last["value"])
         secs += s
     value = statistics.median(vals)
@@ -799,8 +800,8 @@ def main():
     out, w = run_gpu(args, rank, world, local_rank)
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
-            cb, _ = time_oracle(w, args.cpu_sample_genera, args.cpu_sample_pairs)
-            one, _ = time_oracle(w, 1, 2000, threads=1)
+            cb, _ = time_oracle(w, 10 * args.cpu_sample_genera, args.cpu_sample_pairs)
+            one, _ = time_oracle(w, 2, 2000, threads=1)
             cb["single_thread"] = {k: one[k] for k in ("value", "sample", "build_gbps", "classify_mreads_s")}
             out["cpu_baseline"] = cb
         else:
