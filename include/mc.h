@@ -229,6 +229,10 @@ typedef struct mc_batch {
  *                or 16.
  *  lookup_warps: warps per CTA of the lookup kernel: 4 or 8 (default).
  *  score_warps : warps per CTA of the score kernel: 2 or 4 (default).
+ *  wide_keys   : 0 (default) = the shared-memory histograms key a location
+ *                by 32 bits (target << b | window) when every target and
+ *                window id of the database fits 32 bits, else by 64; 1 =
+ *                always 64-bit keys.
  * One warp carries one query in every kernel. */
 typedef struct mc_tuning {
     uint32_t hist_slots;
@@ -236,6 +240,7 @@ typedef struct mc_tuning {
     uint32_t gather_batch;
     uint32_t lookup_warps;
     uint32_t score_warps;
+    uint32_t wide_keys;
 } mc_tuning;
 
 /* Sets the launch shape used by later classify calls on this database that

@@ -150,6 +150,7 @@ struct mc_db {
     DevBuf taxon;  // u32 per target
     DevBuf wbase;  // u32 global window base per target, n_targets+1 entries
     uint64_t n_windows = 0;
+    uint64_t max_target_windows = 0;  // most windows of one target
     // additions not yet finalized
     DevBuf pending;  // u64 pairs
     uint64_t pending_n = 0, pending_real = 0;
@@ -440,6 +441,7 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
         MC_CU(cudaStreamSynchronize(s));
         std::vector<uint32_t> wb(n_targets + 1);
         for (uint32_t i = 0; i <= n_targets; ++i) wb[i] = (uint32_t)(db->n_windows + h[i]);
+        for (uint32_t i = 0; i < n_targets; ++i) db->max_target_windows = std::max(db->max_target_windows, h[i + 1] - h[i]);
         MC_CU(cudaMemcpyAsync((uint32_t*)db->wbase.p + t0, wb.data(), wb.size() * 4, cudaMemcpyHostToDevice, s));
         MC_CU(mc::emit_pairs(db->sp, n_targets, (const uint8_t*)seq, offs, win_offs.ptr, nw, (uint32_t)db->n_windows,
                              (uint64_t*)db->pending.p + db->pending_n, ctr.ptr + 1, s));
@@ -541,6 +543,7 @@ static int classify_impl(const mc_db* db, const mc_classify_params* params, uint
     cdb.lin_stride = db->lin_stride;
     cdb.n_taxa = db->n_taxa;
     cdb.sp = db->sp;
+    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
     mc::ClassifyQuery q;
     q.seq = (const uint8_t*)seq;
     q.offs = offs;
@@ -596,6 +599,7 @@ int classify_prepare(const mc_db* db, const mc_classify_params* params, const ch
     cdb->lin_stride = db->lin_stride;
     cdb->n_taxa = db->n_taxa;
     cdb->sp = db->sp;
+    cdb->jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
     q->seq = (const uint8_t*)seq;
     q->offs = offs;
     q->qoffs = qoffs;
@@ -806,6 +810,17 @@ int mc_db_load(const char* path, void* stream, mc_db** out) {
     db->log_t = h.log_t;
     db->max_probe = h.max_probe;
     db->overflow_keys = h.overflow_keys;
+    {
+        // most windows of one target, for the compact histogram keys
+        std::vector<uint32_t> wb((size_t)h.n_targets + 1);
+        if (cudaMemcpy(wb.data(), db->wbase.p, wb.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            mc_db_free(db);
+            return fail(MC_ERR_CUDA, "mc_db_load: window bases");
+        }
+        for (uint32_t i = 0; i < h.n_targets; ++i)
+            db->max_target_windows = std::max<uint64_t>(db->max_target_windows, wb[i + 1] - wb[i]);
+    }
     db->has_table = true;
     db->dirty = false;
     ++db->epoch;
@@ -949,6 +964,7 @@ mc::ClassifyDb db_view(const mc_db* db) {
     cdb.lin_stride = db->lin_stride;
     cdb.n_taxa = db->n_taxa;
     cdb.sp = db->sp;
+    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
     return cdb;
 }
 
@@ -978,13 +994,14 @@ int tuning_from(const mc_tuning* t, const mc::Tuning& dflt, mc::Tuning* out) {
     if (t->gather_batch) x.gather_batch = t->gather_batch;
     if (t->lookup_warps) x.lookup_warps = t->lookup_warps;
     if (t->score_warps) x.score_warps = t->score_warps;
+    if (t->wide_keys) x.wide_keys = t->wide_keys;
     if (!mc::tuning_valid(x)) return fail(MC_ERR_ARG, "tuning: a value is outside its allowed set");
     *out = x;
     return MC_OK;
 }
 
 mc_tuning to_public(const mc::Tuning& t) {
-    return mc_tuning{t.hist_slots, t.probe_batch, t.gather_batch, t.lookup_warps, t.score_warps};
+    return mc_tuning{t.hist_slots, t.probe_batch, t.gather_batch, t.lookup_warps, t.score_warps, t.wide_keys};
 }
 
 // Host image of the batch header + descriptors (layout of ClassifyQuery's

@@ -56,6 +56,39 @@ __device__ __forceinline__ uint32_t loc_slot(uint64_t loc, uint32_t mask) {
     uint64_t h = (loc ^ (loc >> 29)) * 0x9E3779B97F4A7C15ull;
     return (uint32_t)(h >> 32) & mask;
 }
+__device__ __forceinline__ uint32_t loc_slot(uint32_t key, uint32_t mask) {
+    uint32_t h = key * 0x9E3779B1u;
+    return (h ^ (h >> 15)) & mask;
+}
+
+// Histogram keys: the location (target << 32 | window) as is, or, when the
+// database's target and window ids fit 32 bits, packed into 32 bits as
+// target << jbits | window (halves the key memory of the shared-memory
+// histograms).
+template <class KeyT>
+struct KeyCodec {
+    uint32_t jbits;
+    __device__ __forceinline__ KeyT encode(uint64_t loc) const {
+        if (sizeof(KeyT) == 8) return (KeyT)loc;
+        return (KeyT)(((uint32_t)(loc >> 32) << jbits) | (uint32_t)loc);
+    }
+    __device__ __forceinline__ uint32_t target(KeyT k) const {
+        return sizeof(KeyT) == 8 ? (uint32_t)((uint64_t)k >> 32) : (uint32_t)k >> jbits;
+    }
+    __device__ __forceinline__ uint32_t window(KeyT k) const {
+        return sizeof(KeyT) == 8 ? (uint32_t)k : (uint32_t)k & ((1u << jbits) - 1u);
+    }
+    // windows after this key's window before the id field would overflow
+    __device__ __forceinline__ uint32_t room(KeyT k) const {
+        return sizeof(KeyT) == 8 ? 0xFFFFFFFFu - (uint32_t)k : ((1u << jbits) - 1u) - window(k);
+    }
+    static constexpr KeyT empty() { return (KeyT)~(KeyT)0; }
+};
+
+__device__ __forceinline__ uint64_t key_cas(uint64_t* p, uint64_t cmp, uint64_t val) {
+    return atomicCAS((unsigned long long*)p, (unsigned long long)cmp, (unsigned long long)val);
+}
+__device__ __forceinline__ uint32_t key_cas(uint32_t* p, uint32_t cmp, uint32_t val) { return atomicCAS(p, cmp, val); }
 
 // Histogram count increment: 32-bit counts use atomicAdd directly; 16-bit
 // counts add 1 << 16*(slot&1) to the aligned 32-bit word holding them (a
@@ -67,21 +100,21 @@ __device__ __forceinline__ void count_inc(uint16_t* cnts, uint32_t slot) {
 
 // Histogram insert (count + 1).  `fresh_slot` receives the slot if the
 // location was new, else stays -1.  Returns false if the table is full.
-template <class CntT>
-__device__ __forceinline__ bool hist_insert(uint64_t* keys, CntT* cnts, uint32_t mask, uint64_t loc, int& fresh_slot) {
-    uint32_t slot = loc_slot(loc, mask);
+template <class CntT, class KeyT>
+__device__ __forceinline__ bool hist_insert(KeyT* keys, CntT* cnts, uint32_t mask, KeyT key, int& fresh_slot) {
+    constexpr KeyT EMPTY = KeyCodec<KeyT>::empty();
+    uint32_t slot = loc_slot(key, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        uint64_t k = *(volatile uint64_t*)(keys + slot);
-        if (k == loc) {
+        KeyT k = *(volatile KeyT*)(keys + slot);
+        if (k == key) {
             count_inc(cnts, slot);
             return true;
         }
-        if (k == EMPTY_LOC) {
-            unsigned long long prev =
-                atomicCAS((unsigned long long*)(keys + slot), (unsigned long long)EMPTY_LOC, (unsigned long long)loc);
-            if (prev == EMPTY_LOC || prev == loc) {
+        if (k == EMPTY) {
+            const KeyT prev = key_cas(keys + slot, EMPTY, key);
+            if (prev == EMPTY || prev == key) {
                 count_inc(cnts, slot);
-                if (prev == EMPTY_LOC) fresh_slot = (int)slot;
+                if (prev == EMPTY) fresh_slot = (int)slot;
                 return true;
             }
         }
@@ -90,13 +123,14 @@ __device__ __forceinline__ bool hist_insert(uint64_t* keys, CntT* cnts, uint32_t
     return false;
 }
 
-template <class CntT>
-__device__ __forceinline__ uint32_t hist_count(const uint64_t* keys, const CntT* cnts, uint32_t mask, uint64_t loc) {
-    uint32_t slot = loc_slot(loc, mask);
+template <class CntT, class KeyT>
+__device__ __forceinline__ uint32_t hist_count(const KeyT* keys, const CntT* cnts, uint32_t mask, KeyT key) {
+    constexpr KeyT EMPTY = KeyCodec<KeyT>::empty();
+    uint32_t slot = loc_slot(key, mask);
     for (uint32_t probe = 0; probe <= mask; ++probe) {
-        uint64_t k = keys[slot];
-        if (k == loc) return cnts[slot];
-        if (k == EMPTY_LOC) return 0;
+        const KeyT k = keys[slot];
+        if (k == key) return cnts[slot];
+        if (k == EMPTY) return 0;
         slot = (slot + 1) & mask;
     }
     return 0;
@@ -125,9 +159,9 @@ __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(siz
 // on the large path).  CntT is the histogram count type: 16 bits on the
 // shared-memory path (whose queries gather at most 65,535 locations), 32
 // bits on the large path.  Unused regions have size 0.
-template <class CntT>
+template <class CntT, class KeyT = uint64_t>
 struct Scratch {
-    uint64_t* keys;    // histogram keys (location), kcap
+    KeyT* keys;        // histogram keys (location), kcap
     CntT* cnts;        // histogram counts, kcap
     CntT* score;       // sliding-window scores of the dense entries, kcap
     uint16_t* dense;   // slots of the distinct locations, kcap
@@ -143,22 +177,22 @@ struct Scratch {
     uint32_t max_locs; // locations per query
 };
 
-template <class CntT>
+template <class CntT, class KeyT = uint64_t>
 __host__ __device__ constexpr size_t scratch_bytes(uint32_t kcap, uint32_t list_cap, uint32_t feat_cap,
                                                    uint32_t buf_cap) {
-    return align16((size_t)kcap * 8) + 2 * align16((size_t)kcap * sizeof(CntT)) + align16((size_t)kcap * 2) +
+    return align16((size_t)kcap * sizeof(KeyT)) + 2 * align16((size_t)kcap * sizeof(CntT)) + align16((size_t)kcap * 2) +
            align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + align16((size_t)feat_cap * 4) +
            (feat_cap ? align16(4 * 32 * SK_NW) : 0) + (buf_cap ? align16(buf_cap + 16) : 0);
 }
 
 // Carves a Scratch out of `base` (16-byte aligned), in scratch_bytes order.
-template <class CntT>
-__device__ __forceinline__ Scratch<CntT> carve(unsigned char* base, uint32_t kcap, uint32_t list_cap,
-                                               uint32_t feat_cap, uint32_t buf_cap, uint32_t win_cap) {
-    Scratch<CntT> S;
+template <class CntT, class KeyT = uint64_t>
+__device__ __forceinline__ Scratch<CntT, KeyT> carve(unsigned char* base, uint32_t kcap, uint32_t list_cap,
+                                                     uint32_t feat_cap, uint32_t buf_cap, uint32_t win_cap) {
+    Scratch<CntT, KeyT> S;
     unsigned char* p = base;
-    S.keys = reinterpret_cast<uint64_t*>(p);
-    p += align16((size_t)kcap * 8);
+    S.keys = reinterpret_cast<KeyT*>(p);
+    p += align16((size_t)kcap * sizeof(KeyT));
     S.cnts = reinterpret_cast<CntT*>(p);
     p += align16((size_t)kcap * sizeof(CntT));
     S.score = reinterpret_cast<CntT*>(p);
@@ -467,11 +501,14 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
 // working memory: gather, window count statistic, sliding-window scores,
 // top m, label.  Writes the outputs and returns Q_DONE, or Q_ESCALATE if the
 // histogram does not fit the working memory.
-template <int GB, class CntT>
+template <int GB, class CntT, class KeyT>
 __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
-                                           const Scratch<CntT>& S, uint32_t n_list, uint32_t sws, Counters& ctr) {
+                                           const Scratch<CntT, KeyT>& S, uint32_t n_list, uint32_t sws,
+                                           Counters& ctr) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
+    const KeyCodec<KeyT> kc{db.jbits};
+    constexpr KeyT EMPTY = KeyCodec<KeyT>::empty();
 
     // 2. exclusive prefix of bucket sizes; H = locations to gather
     uint32_t H = 0;
@@ -493,7 +530,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     while (kq < 2 * H && kq < S.kcap) kq <<= 1;
     const uint32_t mask = kq - 1;
     for (uint32_t s = lane; s < kq; s += 32) {
-        S.keys[s] = EMPTY_LOC;
+        S.keys[s] = EMPTY;
         S.cnts[s] = 0;
     }
     __syncwarp();
@@ -529,7 +566,7 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             int slot = -1;
-            if (v[g] != EMPTY_LOC) ok &= hist_insert(S.keys, S.cnts, mask, v[g], slot);
+            if (v[g] != EMPTY_LOC) ok &= hist_insert(S.keys, S.cnts, mask, kc.encode(v[g]), slot);
             const uint32_t fresh = __ballot_sync(FULL_MASK, slot >= 0);
             if (slot >= 0) S.dense[D + __popc(fresh & lt)] = (uint16_t)slot;
             D += __popc(fresh);
@@ -544,10 +581,10 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
     // counts of (t, j0 .. j0+sws-1), for the distinct locations
     for (uint32_t i = lane; i < D; i += 32) {
         const uint32_t slot = S.dense[i];
-        const uint64_t key = S.keys[slot];
+        const KeyT key = S.keys[slot];
         uint32_t sc = S.cnts[slot];
-        const uint32_t room = 0xFFFFFFFFu - (uint32_t)key;  // windows left before the id wraps
-        for (uint32_t d = 1; d < sws && d <= room; ++d) sc += hist_count(S.keys, S.cnts, mask, key + d);
+        const uint32_t room = kc.room(key);  // windows left before the id wraps
+        for (uint32_t d = 1; d < sws && d <= room; ++d) sc += hist_count(S.keys, S.cnts, mask, (KeyT)(key + d));
         S.score[i] = (CntT)sc;
     }
     __syncwarp();
@@ -569,13 +606,13 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
         for (uint32_t i = lane; i < D; i += 32) {
             uint32_t sc = S.score[i];
             if (sc == 0) continue;
-            const uint64_t key = S.keys[S.dense[i]];
-            const uint32_t t = (uint32_t)(key >> 32);
+            const KeyT key = S.keys[S.dense[i]];
+            const uint32_t t = kc.target(key);
             if (t == prev_t) {
                 S.score[i] = 0;
                 continue;
             }
-            const Cand c = Cand{sc, t, (uint32_t)key, 0};
+            const Cand c = Cand{sc, t, kc.window(key), 0};
             if (better(c, best)) best = c;
         }
         // warp arg-max in the candidate order: highest score, then smallest
@@ -593,9 +630,9 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             // last window of the range present in the histogram
             uint32_t j1 = best.j0;
             for (uint32_t i = lane; i < D; i += 32) {
-                const uint64_t key = S.keys[S.dense[i]];
-                const uint32_t j = (uint32_t)key;
-                if ((uint32_t)(key >> 32) == best.t && j >= best.j0 && (uint64_t)j < (uint64_t)best.j0 + sws && j > j1)
+                const KeyT key = S.keys[S.dense[i]];
+                const uint32_t j = kc.window(key);
+                if (kc.target(key) == best.t && j >= best.j0 && (uint64_t)j < (uint64_t)best.j0 + sws && j > j1)
                     j1 = j;
             }
             best.j1 = __reduce_max_sync(FULL_MASK, j1);
@@ -759,7 +796,7 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
 // Main path, part 2 (gather + score + label): one warp per query of the
 // chunk, KA histogram slots per warp in shared memory.  Queries whose
 // histogram does not fit are queued (chunk index) for the medium path.
-template <int KA, int GB>
+template <int KA, int GB, class KeyT>
 __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                      uint32_t chunk, uint32_t list_cap,
                                                                      const uint64_t* __restrict__ glist,
@@ -769,8 +806,8 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    const size_t per_warp = scratch_bytes<uint16_t>(KA, list_cap, 0, 0);
-    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, KA, list_cap, 0, 0, WIN_A);
+    const size_t per_warp = scratch_bytes<uint16_t, KeyT>(KA, list_cap, 0, 0);
+    const Scratch<uint16_t, KeyT> S = carve<uint16_t, KeyT>(smem + w * per_warp, KA, list_cap, 0, 0, WIN_A);
     Counters ctr;
     const uint32_t total = total_queries(Q);
     if (q0 >= total) return;
@@ -800,7 +837,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
 // path, one warp each (work queue), KM_SLOTS histogram slots per warp in
 // shared memory, the bucket list taken over from the lookup.  Queries that
 // do not fit here either go to the large path.
-template <int GB>
+template <int GB, class KeyT>
 __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                    uint32_t list_cap,
                                                                    const uint64_t* __restrict__ glist,
@@ -813,8 +850,8 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    const size_t per_warp = scratch_bytes<uint16_t>(KM_SLOTS, list_cap, 0, 0);
-    const Scratch<uint16_t> S = carve<uint16_t>(smem + w * per_warp, KM_SLOTS, list_cap, 0, 0, WIN_A);
+    const size_t per_warp = scratch_bytes<uint16_t, KeyT>(KM_SLOTS, list_cap, 0, 0);
+    const Scratch<uint16_t, KeyT> S = carve<uint16_t, KeyT>(smem + w * per_warp, KM_SLOTS, list_cap, 0, 0, WIN_A);
     Counters ctr;
     const uint32_t n = *mid_n;
     unsigned long long n_medium = 0;
@@ -903,17 +940,22 @@ LookupKernel pick_lookup(const SketchParams& sp, uint32_t lb) {
     return k16 ? lookup_for_lb<16, 16>(lb) : lookup_for_lb<16, 0>(lb);
 }
 
-template <int KA>
+template <int KA, class KeyT>
 ScoreKernel score_for_gb(uint32_t gb) {
-    if (gb == 4) return k_classify_score<KA, 4>;
-    if (gb == 16) return k_classify_score<KA, 16>;
-    return k_classify_score<KA, 8>;
+    if (gb == 4) return k_classify_score<KA, 4, KeyT>;
+    if (gb == 16) return k_classify_score<KA, 16, KeyT>;
+    return k_classify_score<KA, 8, KeyT>;
 }
 
-ScoreKernel pick_score(uint32_t ka, uint32_t gb) {
-    if (ka == 256) return score_for_gb<256>(gb);
-    if (ka == 1024) return score_for_gb<1024>(gb);
-    return score_for_gb<512>(gb);
+template <class KeyT>
+ScoreKernel score_for_ka(uint32_t ka, uint32_t gb) {
+    if (ka == 256) return score_for_gb<256, KeyT>(gb);
+    if (ka == 1024) return score_for_gb<1024, KeyT>(gb);
+    return score_for_gb<512, KeyT>(gb);
+}
+
+ScoreKernel pick_score(uint32_t ka, uint32_t gb, bool compact) {
+    return compact ? score_for_ka<uint32_t>(ka, gb) : score_for_ka<uint64_t>(ka, gb);
 }
 
 LargeKernel pick_large(const SketchParams& sp) {
@@ -942,10 +984,12 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     g->list_cap = WIN_A * db.sp.s;
     g->kl = pick_lookup(db.sp, t.probe_batch);
-    g->ks = pick_score(t.hist_slots, t.gather_batch);
+    const bool compact = db.jbits != 0 && !t.wide_keys;
+    g->ks = pick_score(t.hist_slots, t.gather_batch, compact);
     g->kb = pick_large(db.sp);
-    g->km = k_classify_medium<GB_DEFAULT>;
-    g->smem_m = MED_WARPS * scratch_bytes<uint16_t>(KM_SLOTS, g->list_cap, 0, 0);
+    g->km = compact ? k_classify_medium<GB_DEFAULT, uint32_t> : k_classify_medium<GB_DEFAULT, uint64_t>;
+    g->smem_m = MED_WARPS * (compact ? scratch_bytes<uint16_t, uint32_t>(KM_SLOTS, g->list_cap, 0, 0)
+                                     : scratch_bytes<uint16_t, uint64_t>(KM_SLOTS, g->list_cap, 0, 0));
     if ((e = cudaFuncSetAttribute(g->km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_m)) != cudaSuccess)
         return e;
     int occ_m = 1;
@@ -955,7 +999,8 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     g->threads_l = t.lookup_warps * 32;
     g->threads_s = t.score_warps * 32;
     g->smem_l = t.lookup_warps * lookup_warp_bytes(g->list_cap);
-    g->smem_s = t.score_warps * scratch_bytes<uint16_t>(t.hist_slots, g->list_cap, 0, 0);
+    g->smem_s = t.score_warps * (compact ? scratch_bytes<uint16_t, uint32_t>(t.hist_slots, g->list_cap, 0, 0)
+                                         : scratch_bytes<uint16_t, uint64_t>(t.hist_slots, g->list_cap, 0, 0));
     if ((e = cudaFuncSetAttribute(g->kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_l)) != cudaSuccess)
         return e;
     if ((e = cudaFuncSetAttribute(g->ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_s)) != cudaSuccess)
@@ -1037,6 +1082,19 @@ cudaError_t launch_large(const Geometry& g, const ClassifyDb& db, const Classify
 
 }  // namespace
 
+uint32_t compact_key_bits(uint64_t n_targets, uint64_t max_windows) {
+    auto bits = [](uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; };
+    if (n_targets == 0 || max_windows == 0) return 0;
+    const uint32_t jb = std::max(1u, bits(max_windows - 1));
+    const uint32_t tb = bits(n_targets - 1);
+    if (jb + tb < 32) return jb;
+    // 32 bits: usable unless the all-ones key (the empty-slot marker) is a
+    // location; a sliding-window lookup of that key only ever meets empty
+    // slots and counts 0
+    if (jb + tb == 32 && !(n_targets == (1ull << tb) && max_windows == (1ull << jb))) return jb;
+    return 0;
+}
+
 bool tuning_valid(const Tuning& t) {
     auto in = [](uint32_t v, std::initializer_list<uint32_t> set) {
         for (uint32_t x : set)
@@ -1044,7 +1102,7 @@ bool tuning_valid(const Tuning& t) {
         return false;
     };
     return in(t.hist_slots, {256, 512, 1024}) && in(t.probe_batch, {2, 4, 8}) && in(t.gather_batch, {4, 8, 16}) &&
-           in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4});
+           in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4}) && t.wide_keys <= 1;
 }
 
 uint32_t classify_default_large_warps() {

@@ -133,7 +133,15 @@ struct ClassifyDb {
     uint32_t lin_stride;
     uint32_t n_taxa;
     SketchParams sp;
+    // > 0: every (target, window) of the database fits 32 bits as
+    // target << jbits | window without being all ones (compact histogram
+    // keys); 0: 64-bit keys
+    uint32_t jbits;
 };
+
+// jbits for a database of n_targets targets with at most max_windows
+// windows each (0 when target and window ids do not fit 32 bits together).
+uint32_t compact_key_bits(uint64_t n_targets, uint64_t max_windows);
 
 // One batch of a multi-batch launch: the device pointers of an mc_batch.
 struct BatchDesc {
@@ -167,9 +175,9 @@ struct ClassifyQuery {
 
 // Launch shape of the classification kernels (mc_tuning).
 struct Tuning {
-    uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps;
+    uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps, wide_keys;
 };
-constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4};
+constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4, 0};
 bool tuning_valid(const Tuning& t);
 
 // Device scratch of one classify launch set for up to n_q_cap queries.

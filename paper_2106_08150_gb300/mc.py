@@ -61,7 +61,7 @@ class mc_batch(ctypes.Structure):
 
 class mc_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ["hist_slots", "probe_batch", "gather_batch", "lookup_warps", "score_warps"]]
+                ["hist_slots", "probe_batch", "gather_batch", "lookup_warps", "score_warps", "wide_keys"]]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -95,6 +95,8 @@ TUNINGS = [
     dict(hist_slots=256, probe_batch=2, gather_batch=4, lookup_warps=4, score_warps=2),
     dict(hist_slots=1024, probe_batch=8, gather_batch=16, lookup_warps=8, score_warps=4),
     dict(hist_slots=256, gather_batch=16, score_warps=4),
+    dict(wide_keys=1),
+    dict(hist_slots=256, probe_batch=2, gather_batch=4, score_warps=2, wide_keys=1),
 ]
 
 
