@@ -375,6 +375,8 @@ def run_gpu(args, rank, world, local_rank):
                 ev_reads = torch.cuda.Event()
                 ev_reads.record(copy_stream)
             db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+            if tuned is not None:
+                mc.mc_db_set_tuning(db.handle, tuned)
             for (a, b), do, ev in zip(chunks, dgo, evs):
                 stream.wait_event(ev)
                 lo = int(w.goffs[a])
