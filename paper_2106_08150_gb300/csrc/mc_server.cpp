@@ -24,6 +24,11 @@
 
 #include "../../include/mc.h"
 
+namespace mc {
+// Records the message of mc_last_error_string and returns `code` (mc_api.cu).
+int report_error(int code, const char* fmt, ...);
+}
+
 namespace {
 
 using Clock = std::chrono::steady_clock;
@@ -399,19 +404,20 @@ void mc_server::run() {
 extern "C" {
 
 int mc_server_create(mc_db* db, const mc_classify_params* params, const mc_server_config* config, mc_server** out) {
-    if (!db || !params || !out) return MC_ERR_ARG;
+    if (!db || !params || !out) return mc::report_error(MC_ERR_ARG, "mc_server_create: NULL argument");
     *out = nullptr;
     mc_db_stats_t st;
     int rc = mc_db_stats(db, &st);
     if (rc) return rc;
-    if (!st.finalized) return MC_ERR_STATE;
+    if (!st.finalized) return mc::report_error(MC_ERR_STATE, "mc_server_create: finalize the database first");
     auto s = std::make_unique<mc_server>();
     s->db = db;
     s->params = *params;
     const uint32_t n_streams = config && config->n_streams ? config->n_streams : 2;
     s->max_set_queries = config && config->max_set_queries ? config->max_set_queries : (1u << 21);
     s->max_set_jobs = config && config->max_set_jobs ? config->max_set_jobs : 256;
-    if (n_streams > 16 || s->max_set_queries >= 0xFFFFFFF0u) return MC_ERR_ARG;
+    if (n_streams > 16 || s->max_set_queries >= 0xFFFFFFF0u)
+        return mc::report_error(MC_ERR_ARG, "mc_server_create: n_streams <= 16, max_set_queries < 2^32 - 16");
     cudaGetDevice(&s->device);
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -441,21 +447,26 @@ int mc_server_create(mc_db* db, const mc_classify_params* params, const mc_serve
 }
 
 int mc_server_submit(mc_server* s, const mc_job* job, uint64_t* job_id) {
-    if (!s || !job || !job_id) return MC_ERR_ARG;
-    if (job->n_queries && (!job->seq || !job->offs || !job->qoffs || !job->label || !job->hits)) return MC_ERR_ARG;
-    if (!job->offs) return MC_ERR_ARG;
+    if (!s || !job || !job_id) return mc::report_error(MC_ERR_ARG, "mc_server_submit: NULL argument");
+    if (!job->offs || (job->n_queries && (!job->seq || !job->qoffs || !job->label || !job->hits)))
+        return mc::report_error(MC_ERR_ARG, "mc_server_submit: NULL input or output pointer");
     // the kernels index offs with qoffs: check both on the host
     for (uint32_t i = 0; i < job->n_seq; ++i)
-        if (job->offs[i + 1] < job->offs[i]) return MC_ERR_ARG;
+        if (job->offs[i + 1] < job->offs[i])
+            return mc::report_error(MC_ERR_ARG, "mc_server_submit: offsets decrease at sequence %u", i);
     if (job->n_queries) {
         for (uint32_t q = 0; q < job->n_queries; ++q)
-            if (job->qoffs[q + 1] < job->qoffs[q]) return MC_ERR_ARG;
-        if (job->qoffs[job->n_queries] > job->n_seq) return MC_ERR_ARG;
+            if (job->qoffs[q + 1] < job->qoffs[q])
+                return mc::report_error(MC_ERR_ARG, "mc_server_submit: query offsets decrease at query %u", q);
+        if (job->qoffs[job->n_queries] > job->n_seq)
+            return mc::report_error(MC_ERR_ARG, "mc_server_submit: query offsets point past the last sequence");
     }
     auto j = std::make_unique<Job>();
     j->j = *job;
     j->bytes = job_bytes(*job, &j->o_offs, &j->o_qoffs, &j->o_label, &j->o_hits, &j->o_top);
-    if (j->bytes > s->hbm_limit) return MC_ERR_OOM;
+    if (j->bytes > s->hbm_limit)
+        return mc::report_error(MC_ERR_OOM, "mc_server_submit: the job needs %zu device bytes, the limit is %llu",
+                                j->bytes, (unsigned long long)s->hbm_limit);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) return MC_ERR_STATE;
@@ -483,10 +494,10 @@ int mc_server_submit(mc_server* s, const mc_job* job, uint64_t* job_id) {
 
 int mc_server_extend(mc_server* s, uint32_t n_targets, const char* seq, const uint64_t* offs, const uint32_t* taxon,
                      uint32_t* first_target_id) {
-    if (!s || !offs || (n_targets && !taxon)) return MC_ERR_ARG;
+    if (!s || !offs || (n_targets && !taxon)) return mc::report_error(MC_ERR_ARG, "mc_server_extend: NULL argument");
     Extension e;
     const uint64_t nb = offs[n_targets];
-    if (nb && !seq) return MC_ERR_ARG;
+    if (nb && !seq) return mc::report_error(MC_ERR_ARG, "mc_server_extend: NULL sequence");
     e.seq.assign(seq, seq + nb);
     e.offs.assign(offs, offs + n_targets + 1);
     e.taxon.assign(taxon, taxon + n_targets);
@@ -511,7 +522,7 @@ int mc_server_wait(mc_server* s, uint64_t job_id, double timeout_s, mc_job_info*
     if (!s) return MC_ERR_ARG;
     std::unique_lock<std::mutex> lk(s->mu);
     auto it = s->jobs.find(job_id);
-    if (it == s->jobs.end()) return MC_ERR_ARG;
+    if (it == s->jobs.end()) return mc::report_error(MC_ERR_ARG, "mc_server_wait: unknown job id");
     Job* j = it->second.get();
     auto ready = [&] { return j->done; };
     if (timeout_s < 0) {
