@@ -77,16 +77,6 @@ __host__ __device__ __forceinline__ uint32_t hash_h2_inverse(uint32_t y) {
 }
 
 // ------------------------------------------------------------- encoding
-// 2-bit code of an ASCII base: A/a -> 0, C/c -> 1, G/g -> 2, T/t -> 3 (bits
-// 1 and 2 of the ASCII code decide it).  Only meaningful when valid.
-__device__ __forceinline__ uint32_t base_code(uint32_t c) { return ((c >> 1) ^ (c >> 2)) & 3u; }
-
-// A, C, G, T in either case; every other byte is an invalid base.
-__device__ __forceinline__ uint32_t base_valid(uint32_t c) {
-    uint32_t u = (c | 0x20u) - 0x61u;  // 'a' -> 0 ... 't' -> 19
-    return (u < 20u) ? ((0x80045u >> u) & 1u) : 0u;
-}
-
 // Reverse complement of a k-mer code held in the low 2k bits (first base
 // most significant): reverse the 2-bit digits, complement each.
 __device__ __forceinline__ uint32_t revcomp_code(uint32_t fwd, uint32_t k) {
