@@ -261,6 +261,24 @@ int check_cls(const mc_classify_params* p) {
     return MC_OK;
 }
 
+// Kernel view of a finalized database.
+mc::ClassifyDb db_view(const mc_db* db) {
+    mc::ClassifyDb cdb;
+    cdb.table = (const uint4*)db->table.p;
+    cdb.log_t = db->log_t;
+    cdb.max_probe = db->max_probe;
+    cdb.locs = (const uint64_t*)db->locs.p;
+    cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
+    cdb.n_targets = db->n_targets;
+    cdb.lineage = (const uint32_t*)db->lineage.p;
+    cdb.depth = (const uint32_t*)db->depth.p;
+    cdb.lin_stride = db->lin_stride;
+    cdb.n_taxa = db->n_taxa;
+    cdb.sp = db->sp;
+    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
+    return cdb;
+}
+
 }  // namespace
 
 extern "C" {
@@ -531,19 +549,7 @@ static int classify_impl(const mc_db* db, const mc_classify_params* params, uint
     (void)n_seq;
     cudaStream_t s = (cudaStream_t)stream;
     MC_CU(cudaStreamWaitEvent(s, db->ready, 0));
-    mc::ClassifyDb cdb;
-    cdb.table = (const uint4*)db->table.p;
-    cdb.log_t = db->log_t;
-    cdb.max_probe = db->max_probe;
-    cdb.locs = (const uint64_t*)db->locs.p;
-    cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
-    cdb.n_targets = db->n_targets;
-    cdb.lineage = (const uint32_t*)db->lineage.p;
-    cdb.depth = (const uint32_t*)db->depth.p;
-    cdb.lin_stride = db->lin_stride;
-    cdb.n_taxa = db->n_taxa;
-    cdb.sp = db->sp;
-    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
+    const mc::ClassifyDb cdb = db_view(db);
     mc::ClassifyQuery q;
     q.seq = (const uint8_t*)seq;
     q.offs = offs;
@@ -588,18 +594,7 @@ int classify_prepare(const mc_db* db, const mc_classify_params* params, const ch
     if (n_queries && (!seq || !offs || !qoffs || !label || !hits))
         return fail(MC_ERR_ARG, "NULL input or output pointer");
     MC_CU(cudaStreamWaitEvent(stream, db->ready, 0));
-    cdb->table = (const uint4*)db->table.p;
-    cdb->log_t = db->log_t;
-    cdb->max_probe = db->max_probe;
-    cdb->locs = (const uint64_t*)db->locs.p;
-    cdb->taxon_of_target = (const uint32_t*)db->taxon.p;
-    cdb->n_targets = db->n_targets;
-    cdb->lineage = (const uint32_t*)db->lineage.p;
-    cdb->depth = (const uint32_t*)db->depth.p;
-    cdb->lin_stride = db->lin_stride;
-    cdb->n_taxa = db->n_taxa;
-    cdb->sp = db->sp;
-    cdb->jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
+    *cdb = db_view(db);
     q->seq = (const uint8_t*)seq;
     q->offs = offs;
     q->qoffs = qoffs;
@@ -951,22 +946,6 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
 
 namespace {
 
-mc::ClassifyDb db_view(const mc_db* db) {
-    mc::ClassifyDb cdb;
-    cdb.table = (const uint4*)db->table.p;
-    cdb.log_t = db->log_t;
-    cdb.max_probe = db->max_probe;
-    cdb.locs = (const uint64_t*)db->locs.p;
-    cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
-    cdb.n_targets = db->n_targets;
-    cdb.lineage = (const uint32_t*)db->lineage.p;
-    cdb.depth = (const uint32_t*)db->depth.p;
-    cdb.lin_stride = db->lin_stride;
-    cdb.n_taxa = db->n_taxa;
-    cdb.sp = db->sp;
-    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
-    return cdb;
-}
 
 mc::ClassifyQuery batch_query(const mc_db* db, const mc_classify_params* p, uint32_t n_q_cap,
                               const mc::BatchDesc* desc, const uint32_t* bhdr) {
