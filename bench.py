@@ -202,10 +202,10 @@ def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
     n_real = st["n_pairs"]
     if kernel == "sketch_emit":
         return w.n_bp * 1.0 + slots * 8.0  # read each base once, write the pair slots
-    if kernel == "radix_scatter":
+    if kernel == "radix_pass":
         return (slots + 3 * n_real) * 8.0 + 4 * n_real * 8.0  # read every input once, write every real pair
-    if kernel == "radix_hist":
-        return (slots + 3 * n_real) * 8.0
+    if kernel == "radix_totals":
+        return slots * 8.0  # one read of the first pass's input
     if kernel == "fin_count":
         return n_real * 8.0
     if kernel == "fin_emit":
@@ -396,13 +396,23 @@ def run_gpu(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
         t0 = time.perf_counter()
+        step_ms = []
         for _ in range(args.steps):
+            t1 = time.perf_counter()
             e2e_step()
+            step_ms.append(round((time.perf_counter() - t1) * 1e3, 1))
         torch.cuda.synchronize()
         e2e_ms = max_over_ranks([(time.perf_counter() - t0) * 1e3], world, dev)[0]
+        # the host-to-device copy alone (genomes + reads, one stream)
+        t1 = time.perf_counter()
+        with torch.cuda.stream(copy_stream):
+            dg.copy_(hg, non_blocking=True)
+            dr.copy_(hr, non_blocking=True)
+        copy_stream.synchronize()
+        h2d_gbs = (hg.numel() + hr.numel()) / (time.perf_counter() - t1) / 1e9
         e2e = {"value": whole_job_rate(nq, world, args.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": e2e_ms / args.steps}
+               "ms_per_step": e2e_ms / args.steps, "step_ms": step_ms, "h2d_alone_gbs": round(h2d_gbs, 1)}
 
     # roofline of the dominant kernel
     kernels = {k: {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)} for k, (n, ms) in trace.items()}

@@ -7,8 +7,8 @@
 //   1. sketch + emit: one warp per window computes its sketch (shared with
 //      the query path, mc_sketch.cuh) and writes (h2(feature) << 32 |
 //      global window) pairs in window order;
-//   2. a stable LSD radix sort (4 passes of 8 bits over the upper word)
-//      groups the pairs by feature while keeping them in window order,
+//   2. a stable LSD radix sort (4 single-pass digits of 8 bits over the
+//      upper word) groups the pairs by feature while keeping them in window order,
 //      which is (target, window) order, so every bucket comes out sorted;
 //   3. finalize keeps the first `cap` pairs of each feature (Section 4.1:
 //      at most 254 locations per feature; the smallest are kept, as in the
@@ -288,79 +288,152 @@ cudaError_t emit_pairs(const SketchParams& p, uint32_t n_targets, const uint8_t*
 }
 
 // ------------------------------------------------------------ radix sort
+// Single-pass LSD radix sort (one kernel per 8-bit digit; Merrill and
+// Garland's decoupled look-back, as in "Onesweep", Adinets and Merrill
+// 2022).  One streaming read computes the digit totals of all four passes;
+// then every pass reads each pair once and writes it once.  A tile
+// (4,096 pairs) ranks its pairs by digit, publishes its per-digit counts,
+// looks back over earlier tiles' published counts for its global offsets,
+// and writes each digit's run with consecutive threads on consecutive
+// addresses.
 namespace {
 constexpr int RS_ITEMS = 16;
 constexpr uint64_t RS_TILE = (uint64_t)BT * RS_ITEMS;  // 4096 pairs
+constexpr int RS_BLOCKS_PER_SM = 3;
+constexpr int RS_LOOKBACK = 4;  // earlier tiles read per look-back step
 // element of (warp w, round i, lane l) in a tile: w*32*RS_ITEMS + i*32 + l
 
-__global__ void __launch_bounds__(BT) k_radix_hist(const uint64_t* __restrict__ in, uint64_t n, uint32_t shift,
-                                                   int filter, uint64_t* __restrict__ hist, uint64_t n_tiles) {
-    __shared__ uint32_t sh[NWARP][256];
-    const int w = threadIdx.x >> 5;
-    const uint32_t lane = lane_id();
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < NWARP * 256; i += BT) (&sh[0][0])[i] = 0;
-        __syncthreads();
-        uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
-#pragma unroll 4
-        for (int i = 0; i < RS_ITEMS; ++i) {
-            uint64_t e = base + (uint64_t)i * 32;
-            if (e < n) {
-                uint64_t v = in[e];
-                if (!(filter && v == SENTINEL_PAIR)) atomicAdd(&sh[w][(uint32_t)(v >> shift) & 255u], 1u);
-            }
-        }
-        __syncthreads();
-        uint32_t sum = 0;
-#pragma unroll
-        for (int i = 0; i < NWARP; ++i) sum += sh[i][threadIdx.x];
-        hist[(uint64_t)threadIdx.x * n_tiles + tile] = sum;
-        __syncthreads();
-    }
+// Look-back status word of (tile, digit): kind (2 bits: 1 = this tile's
+// count, 2 = inclusive prefix over tiles 0..tile), pass tag (4 bits: pass +
+// 1, so that one zeroing serves all four passes), value (58 bits).
+constexpr uint64_t ST_COUNT = 1ull << 62;
+constexpr uint64_t ST_PREFIX = 2ull << 62;
+constexpr uint64_t ST_VALUE = (1ull << 58) - 1;
+constexpr uint64_t LOOKBACK_LIMIT_NS = 2000000000ull;  // a wait longer than this is an error
+
+__device__ __forceinline__ uint64_t ld_relaxed_gpu(const uint64_t* p) {
+    uint64_t v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_gpu(uint64_t* p, uint64_t v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
-// Stable scatter of one pass.  Each tile ranks its elements by digit
-// (warp match + per-warp counters keep input order among equal digits),
-// stages them in shared memory in digit order, and writes every digit's run
-// to its global offset with consecutive threads on consecutive addresses.
-__global__ void __launch_bounds__(BT) k_radix_scatter(const uint64_t* __restrict__ in, uint64_t* __restrict__ out,
-                                                      uint64_t n, uint32_t shift, int filter,
-                                                      const uint64_t* __restrict__ offs, uint64_t n_tiles) {
-    __shared__ uint32_t wc[NWARP][257];
-    __shared__ uint32_t dstart[256];
-    __shared__ uint64_t gbase[256];
-    __shared__ uint64_t staged[RS_TILE];
-    __shared__ uint64_t sm[NWARP];
+// Digit totals of the four passes (sentinels excluded): totals[pass][digit].
+__global__ void __launch_bounds__(BT) k_radix_totals(const uint64_t* __restrict__ in, uint64_t n,
+                                                     unsigned long long* __restrict__ totals) {
+    __shared__ uint32_t sh[NWARP][4][256];
+    for (int i = threadIdx.x; i < NWARP * 1024; i += BT) (&sh[0][0][0])[i] = 0;
+    __syncthreads();
     const int w = threadIdx.x >> 5;
-    const uint32_t lane = lane_id();
-    const uint32_t lt = lanemask_lt();
-    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        for (int i = threadIdx.x; i < NWARP * 257; i += BT) (&wc[0][0])[i] = 0;
-        gbase[threadIdx.x] = offs[(uint64_t)threadIdx.x * n_tiles + tile];
-        __syncthreads();
-        uint64_t v[RS_ITEMS];
-        uint32_t dr[RS_ITEMS];
-        const uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
+    const uint64_t stride = (uint64_t)gridDim.x * BT * 4;
+    for (uint64_t e0 = (uint64_t)blockIdx.x * BT * 4 + threadIdx.x; e0 < n; e0 += stride) {
+        uint64_t v[4];
 #pragma unroll
-        for (int i = 0; i < RS_ITEMS; ++i) {
-            const uint64_t e = base + (uint64_t)i * 32;
+        for (int i = 0; i < 4; ++i) {
+            const uint64_t e = e0 + (uint64_t)i * BT;
             v[i] = e < n ? in[e] : SENTINEL_PAIR;
         }
 #pragma unroll
-        for (int i = 0; i < RS_ITEMS; ++i) {
-            const uint64_t e = base + (uint64_t)i * 32;
-            const bool ok = e < n;
-            const uint32_t d = (!ok || (filter && v[i] == SENTINEL_PAIR)) ? 256u : ((uint32_t)(v[i] >> shift) & 255u);
-            const uint32_t peers = __match_any_sync(FULL_MASK, d);
-            const uint32_t rank = __popc(peers & lt);
-            const uint32_t before = wc[w][d];
-            __syncwarp();
-            if (rank == 0) wc[w][d] = before + __popc(peers);
-            __syncwarp();
-            dr[i] = (d << 16) | (before + rank);
+        for (int i = 0; i < 4; ++i) {
+            if (v[i] == SENTINEL_PAIR) continue;
+            const uint32_t k = (uint32_t)(v[i] >> 32);
+            atomicAdd(&sh[w][0][k & 255u], 1u);
+            atomicAdd(&sh[w][1][(k >> 8) & 255u], 1u);
+            atomicAdd(&sh[w][2][(k >> 16) & 255u], 1u);
+            atomicAdd(&sh[w][3][k >> 24], 1u);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 1024; i += BT) {
+        uint32_t c = 0;
+#pragma unroll
+        for (int j = 0; j < NWARP; ++j) c += (&sh[j][0][0])[i];
+        if (c) atomicAdd(totals + i, (unsigned long long)c);
+    }
+}
+
+// Rank of one round of a warp's 32 pairs: the lanes holding the same digit
+// (every third round by match, the others by eight ballots, which spreads
+// the work over two execution pipes) and the warp's running count of that
+// digit in shared memory.  Invalid lanes carry digit 256 and are not counted.
+__device__ __forceinline__ uint32_t rank_round(int i, bool valid, uint32_t d, uint32_t lt, uint32_t* wcount) {
+    uint32_t peers;
+    if (i % 3 == 0) {
+        peers = __match_any_sync(FULL_MASK, d);
+    } else {
+        peers = __ballot_sync(FULL_MASK, valid);
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const uint32_t bb = __ballot_sync(FULL_MASK, (d >> b) & 1u);
+            peers &= ((d >> b) & 1u) ? bb : ~bb;
+        }
+    }
+    const uint32_t rank = __popc(peers & lt);
+    const uint32_t leader = (__ffs(peers) - 1) & 31u;
+    uint32_t before = 0;
+    if (valid && rank == 0) before = atomicAdd(&wcount[d], (uint32_t)__popc(peers));
+    return __shfl_sync(FULL_MASK, before, leader) + rank;
+}
+
+// One pass over digit `pass` (bits 32 + 8 pass ..).  Persistent blocks take
+// tiles in order from *tile_ctr, so a tile only ever waits for tiles that
+// running blocks hold.  FILTER drops sentinel pairs (first pass).
+template <bool FILTER>
+__global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
+    k_radix_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint32_t pass,
+                 const unsigned long long* __restrict__ totals, uint64_t* status, uint32_t* tile_ctr,
+                 uint64_t n_tiles, uint32_t* err) {
+    __shared__ uint32_t wc[NWARP][257];  // per-warp digit counts, then tile offsets
+    __shared__ uint64_t gdelta[256];     // global position of a digit's run minus its tile offset
+    __shared__ uint64_t staged[RS_TILE];
+    __shared__ uint64_t sm[NWARP];
+    __shared__ uint32_t s_tile;
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    const uint32_t sel = 0x4440u + pass;  // __byte_perm selector of byte `pass` of the key
+    const uint64_t tag = (uint64_t)(pass + 1) << 58;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
+    uint64_t all;
+    const uint64_t dbase = block_exclusive((uint64_t)totals[threadIdx.x], (uint64_t)0, OpSum(), sm, &all);
+    uint64_t tile = s_tile;
+    while (tile < n_tiles) {
+        for (int i = threadIdx.x; i < NWARP * 257; i += BT) (&wc[0][0])[i] = 0;
+        __syncthreads();
+        uint64_t v[RS_ITEMS];
+        uint32_t dr[RS_ITEMS];  // digit << 16 | rank within the warp's pairs of that digit
+        const uint64_t base = tile * RS_TILE + (uint64_t)w * 32 * RS_ITEMS + lane;
+        if ((tile + 1) * RS_TILE <= n) {
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; ++i) v[i] = in[base + (uint64_t)i * 32];
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; ++i) {
+                const bool valid = !FILTER || v[i] != SENTINEL_PAIR;
+                const uint32_t d = valid ? __byte_perm((uint32_t)(v[i] >> 32), 0, sel) : 256u;
+                dr[i] = (d << 16) | rank_round(i, valid, d, lt, wc[w]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; ++i) {
+                const uint64_t e = base + (uint64_t)i * 32;
+                v[i] = e < n ? in[e] : SENTINEL_PAIR;
+            }
+#pragma unroll
+            for (int i = 0; i < RS_ITEMS; ++i) {
+                const bool valid = base + (uint64_t)i * 32 < n && (!FILTER || v[i] != SENTINEL_PAIR);
+                const uint32_t d = valid ? __byte_perm((uint32_t)(v[i] >> 32), 0, sel) : 256u;
+                dr[i] = (d << 16) | rank_round(i, valid, d, lt, wc[w]);
+            }
         }
         __syncthreads();
-        // per digit: exclusive prefix over warps, then digit starts in the tile
+        // thread d: exclusive offsets of digit d over the warps, tile count
         uint32_t run = 0;
 #pragma unroll
         for (int i = 0; i < NWARP; ++i) {
@@ -368,55 +441,120 @@ __global__ void __launch_bounds__(BT) k_radix_scatter(const uint64_t* __restrict
             wc[i][threadIdx.x] = run;
             run += c;
         }
+        // publish, then look back for the count of digit d in earlier tiles
+        uint64_t excl = 0;
+        uint64_t* mine = status + tile * 256 + threadIdx.x;
+        if (tile == 0) {
+            st_relaxed_gpu(mine, ST_PREFIX | tag | run);
+        } else {
+            st_relaxed_gpu(mine, ST_COUNT | tag | run);
+            int64_t t = (int64_t)tile - 1;
+            uint64_t t0 = 0;
+            uint32_t polls = 0;
+            while (true) {
+                uint64_t st[RS_LOOKBACK];
+#pragma unroll
+                for (int k = 0; k < RS_LOOKBACK; ++k)
+                    st[k] = t - k >= 0 ? ld_relaxed_gpu(status + (uint64_t)(t - k) * 256 + threadIdx.x)
+                                       : ST_PREFIX | tag;
+                uint32_t used = 0;
+                bool stop = false, done = false;
+#pragma unroll
+                for (int k = 0; k < RS_LOOKBACK; ++k) {
+                    if (!stop) {
+                        if ((st[k] & (15ull << 58)) != tag || (st[k] >> 62) == 0) {
+                            stop = true;  // not published in this pass yet
+                        } else {
+                            excl += st[k] & ST_VALUE;
+                            ++used;
+                            if ((st[k] >> 62) == 2) stop = done = true;
+                        }
+                    }
+                }
+                if (done) break;
+                t -= used;
+                if (used == 0 && (++polls & 255u) == 0) {
+                    const uint64_t now = globaltimer_ns();
+                    if (t0 == 0) {
+                        t0 = now;
+                    } else if (now - t0 > LOOKBACK_LIMIT_NS) {
+                        atomicMax(err, 1u);
+                        break;
+                    }
+                }
+            }
+            st_relaxed_gpu(mine, ST_PREFIX | tag | (excl + run));
+        }
         uint64_t tot;
         const uint32_t ds = (uint32_t)block_exclusive((uint64_t)run, (uint64_t)0, OpSum(), sm, &tot);
-        dstart[threadIdx.x] = ds;
+        gdelta[threadIdx.x] = dbase + excl - ds;
+#pragma unroll
+        for (int i = 0; i < NWARP; ++i) wc[i][threadIdx.x] += ds;
         __syncthreads();
+        // stage in digit order, then write each digit's run
 #pragma unroll
         for (int i = 0; i < RS_ITEMS; ++i) {
             const uint32_t d = dr[i] >> 16;
-            if (d < 256u) staged[dstart[d] + wc[w][d] + (dr[i] & 0xFFFFu)] = v[i];
+            if (d < 256u) staged[wc[w][d] + (dr[i] & 0xFFFFu)] = v[i];
         }
         __syncthreads();
         const uint32_t count = (uint32_t)tot;
         for (uint32_t j = threadIdx.x; j < count; j += BT) {
             const uint64_t x = staged[j];
-            const uint32_t d = (uint32_t)(x >> shift) & 255u;
-            out[gbase[d] + (j - dstart[d])] = x;
+            out[gdelta[__byte_perm((uint32_t)(x >> 32), 0, sel)] + j] = x;
         }
+        if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
         __syncthreads();
+        tile = s_tile;
     }
 }
 }  // namespace
 
 cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_total, uint64_t n_real, cudaStream_t s) {
     if (n_total == 0) return cudaSuccess;
-    uint64_t max_tiles = (n_total + RS_TILE - 1) / RS_TILE;
-    Tmp<uint64_t> hist(mem, 256 * max_tiles + 1, s);
-    if (!hist.ok()) return cudaErrorMemoryAllocation;
+    const uint64_t max_tiles = (n_total + RS_TILE - 1) / RS_TILE;
+    // control block: totals[4][256], tile counters[4], error word
+    constexpr size_t CTRL_WORDS = 4 * 256 + 3;
+    Tmp<uint64_t> ctrl(mem, CTRL_WORDS, s);
+    Tmp<uint64_t> status(mem, max_tiles * 256, s);
+    if (!ctrl.ok() || !status.ok()) return cudaErrorMemoryAllocation;
+    unsigned long long* totals = (unsigned long long*)ctrl.ptr;
+    uint32_t* tile_ctr = (uint32_t*)(ctrl.ptr + 4 * 256);
+    uint32_t* err = tile_ctr + 4;
+    cudaError_t e = cudaMemsetAsync(ctrl.ptr, 0, CTRL_WORDS * 8, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(status.ptr, 0, max_tiles * 256 * 8, s);
+    if (e != cudaSuccess) return e;
+    MC_LAUNCH("radix_totals", s,
+              k_radix_totals<<<grid_for((n_total + 4 * BT - 1) / (4 * BT), 4), BT, 0, s>>>(a, n_total, totals));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
     uint64_t* src = a;
     uint64_t* dst = b;
-    for (int pass = 0; pass < 4; ++pass) {
-        uint64_t n = pass == 0 ? n_total : n_real;
+    for (uint32_t pass = 0; pass < 4; ++pass) {
+        const uint64_t n = pass == 0 ? n_total : n_real;
         if (n == 0) break;
-        uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
-        uint32_t shift = 32 + 8 * pass;
-        int filter = pass == 0;
-        uint32_t g = grid_for(tiles);
-        MC_LAUNCH("radix_hist", s, k_radix_hist<<<g, BT, 0, s>>>(src, n, shift, filter, hist.ptr, tiles));
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        e = scan_exclusive_sum(mem, hist.ptr, hist.ptr, 256 * tiles, s);
-        if (e != cudaSuccess) return e;
-        MC_LAUNCH("radix_scatter", s, k_radix_scatter<<<g, BT, 0, s>>>(src, dst, n, shift, filter, hist.ptr, tiles));
+        const uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
+        const uint32_t g = grid_for(tiles, RS_BLOCKS_PER_SM);
+        const unsigned long long* tp = totals + 256 * pass;
+        if (pass == 0)
+            MC_LAUNCH("radix_pass", s,
+                      k_radix_pass<true><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles, err));
+        else
+            MC_LAUNCH("radix_pass", s,
+                      k_radix_pass<false><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles, err));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t* t = src;
         src = dst;
         dst = t;
     }
-    // after 4 passes the data is back in `a`
-    return cudaSuccess;
+    // after 4 passes the data is back in `a`; a look-back that gave up
+    // leaves a wrong order, which is reported as a timeout
+    uint32_t h_err = 0;
+    e = cudaMemcpyAsync(&h_err, err, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return e;
+    return h_err ? cudaErrorTimeout : cudaSuccess;
 }
 
 // --------------------------------------------------------------- finalize
