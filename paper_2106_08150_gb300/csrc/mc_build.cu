@@ -359,26 +359,26 @@ __global__ void __launch_bounds__(BT) k_radix_totals(const uint64_t* __restrict_
     }
 }
 
-// Rank of one round of a warp's 32 pairs: the lanes holding the same digit
-// (every third round by match, the others by eight ballots, which spreads
-// the work over two execution pipes) and the warp's running count of that
-// digit in shared memory.  Invalid lanes carry digit 256 and are not counted.
-__device__ __forceinline__ uint32_t rank_round(int i, bool valid, uint32_t d, uint32_t lt, uint32_t* wcount) {
-    uint32_t peers;
-    if (i % 3 == 0) {
-        peers = __match_any_sync(FULL_MASK, d);
-    } else {
-        peers = __ballot_sync(FULL_MASK, valid);
-#pragma unroll
-        for (int b = 0; b < 8; ++b) {
-            const uint32_t bb = __ballot_sync(FULL_MASK, (d >> b) & 1u);
-            peers &= ((d >> b) & 1u) ? bb : ~bb;
-        }
-    }
+// Rank of round i of a warp's 32 pairs: the lanes holding the same digit
+// (each lane sets its bit in the digit's word of a per-warp mask table in
+// shared memory, then reads the word back; two tables alternate so that a
+// table's reset is ordered before its next use by the warp barriers of the
+// round in between) and the warp's running count of that digit.  Invalid
+// lanes carry digit 256, which is neither counted nor reset.
+__device__ __forceinline__ uint32_t rank_round(int i, bool valid, uint32_t d, uint32_t lane, uint32_t lt,
+                                               uint32_t* wcount, uint32_t* mask0, uint32_t* mask1) {
+    uint32_t* mask = (i & 1) ? mask1 : mask0;
+    atomicOr(&mask[d], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = mask[d];
+    __syncwarp();
     const uint32_t rank = __popc(peers & lt);
     const uint32_t leader = (__ffs(peers) - 1) & 31u;
     uint32_t before = 0;
-    if (valid && rank == 0) before = atomicAdd(&wcount[d], (uint32_t)__popc(peers));
+    if (valid && rank == 0) {
+        before = atomicAdd(&wcount[d], (uint32_t)__popc(peers));
+        mask[d] = 0;
+    }
     return __shfl_sync(FULL_MASK, before, leader) + rank;
 }
 
@@ -390,8 +390,9 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
     k_radix_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint32_t pass,
                  const unsigned long long* __restrict__ totals, uint64_t* status, uint32_t* tile_ctr,
                  uint64_t n_tiles, uint32_t* err) {
-    __shared__ uint32_t wc[NWARP][257];  // per-warp digit counts, then tile offsets
-    __shared__ uint64_t gdelta[256];     // global position of a digit's run minus its tile offset
+    __shared__ uint32_t wc[NWARP][257];       // per-warp digit counts, then tile offsets
+    __shared__ uint32_t peer_mask[2][NWARP][257];
+    __shared__ uint64_t gdelta[256];          // global position of a digit's run minus its tile offset
     __shared__ uint64_t staged[RS_TILE];
     __shared__ uint64_t sm[NWARP];
     __shared__ uint32_t s_tile;
@@ -400,6 +401,7 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
     const uint32_t lt = lanemask_lt();
     const uint32_t sel = 0x4440u + pass;  // __byte_perm selector of byte `pass` of the key
     const uint64_t tag = (uint64_t)(pass + 1) << 58;
+    for (int i = threadIdx.x; i < 2 * NWARP * 257; i += BT) (&peer_mask[0][0][0])[i] = 0;
     if (threadIdx.x == 0) s_tile = atomicAdd(tile_ctr, 1u);
     uint64_t all;
     const uint64_t dbase = block_exclusive((uint64_t)totals[threadIdx.x], (uint64_t)0, OpSum(), sm, &all);
@@ -417,7 +419,7 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
             for (int i = 0; i < RS_ITEMS; ++i) {
                 const bool valid = !FILTER || v[i] != SENTINEL_PAIR;
                 const uint32_t d = valid ? __byte_perm((uint32_t)(v[i] >> 32), 0, sel) : 256u;
-                dr[i] = (d << 16) | rank_round(i, valid, d, lt, wc[w]);
+                dr[i] = (d << 16) | rank_round(i, valid, d, lane, lt, wc[w], peer_mask[0][w], peer_mask[1][w]);
             }
         } else {
 #pragma unroll
@@ -429,7 +431,7 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
             for (int i = 0; i < RS_ITEMS; ++i) {
                 const bool valid = base + (uint64_t)i * 32 < n && (!FILTER || v[i] != SENTINEL_PAIR);
                 const uint32_t d = valid ? __byte_perm((uint32_t)(v[i] >> 32), 0, sel) : 256u;
-                dr[i] = (d << 16) | rank_round(i, valid, d, lt, wc[w]);
+                dr[i] = (d << 16) | rank_round(i, valid, d, lane, lt, wc[w], peer_mask[0][w], peer_mask[1][w]);
             }
         }
         __syncthreads();
