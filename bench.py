@@ -359,6 +359,8 @@ def run_gpu(args, rank, world, local_rank):
         d2h = 2 * nq * 4
         copy_stream = torch.cuda.Stream(device=dev)
 
+        phases = []
+
         def e2e_step():
             evs = []
             with torch.cuda.stream(copy_stream):
@@ -374,6 +376,7 @@ def run_gpu(args, rank, world, local_rank):
                 dqo.copy_(hqo, non_blocking=True)
                 ev_reads = torch.cuda.Event()
                 ev_reads.record(copy_stream)
+            tp = [time.perf_counter()]
             db = mc.Database.create(w.parent, stream=stream, **w.db_params)
             if tuned is not None:
                 mc.mc_db_set_tuning(db.handle, tuned)
@@ -381,7 +384,9 @@ def run_gpu(args, rank, world, local_rank):
                 stream.wait_event(ev)
                 lo = int(w.goffs[a])
                 db.add_targets(dg[lo:], do, w.taxon_of_target[a:b])
+            tp.append(time.perf_counter())
             db.finalize()
+            tp.append(time.perf_counter())
             stream.wait_event(ev_reads)
             mc.mc_classify(db.handle, cp, w.n_seq, dr, dro, nq, dqo, label, hits, top, stream=stream)
             with torch.cuda.stream(stream):
@@ -389,6 +394,8 @@ def run_gpu(args, rank, world, local_rank):
                 hh.copy_(hits, non_blocking=True)
             db.free()
             stream.synchronize()
+            tp.append(time.perf_counter())
+            phases.append([round((b_ - a_) * 1e3, 1) for a_, b_ in zip(tp[:-1], tp[1:])])
 
         for _ in range(args.warmup):
             e2e_step()
@@ -412,7 +419,8 @@ def run_gpu(args, rank, world, local_rank):
         h2d_gbs = (hg.numel() + hr.numel()) / (time.perf_counter() - t1) / 1e9
         e2e = {"value": whole_job_rate(nq, world, args.steps, e2e_ms), "unit": UNIT,
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": e2e_ms / args.steps, "step_ms": step_ms, "h2d_alone_gbs": round(h2d_gbs, 1)}
+               "ms_per_step": e2e_ms / args.steps, "step_ms": step_ms, "h2d_alone_gbs": round(h2d_gbs, 1),
+               "phase_ms_add_finalize_classify": phases[-args.steps:]}
 
     # roofline of the dominant kernel
     kernels = {k: {"launches": n, "total_ms": ms, "avg_ms": ms / max(n, 1)} for k, (n, ms) in trace.items()}

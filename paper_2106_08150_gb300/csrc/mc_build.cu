@@ -563,7 +563,7 @@ cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_tota
 namespace {
 constexpr int FIN_ITEMS = 8;
 constexpr uint64_t FIN_TILE = (uint64_t)BT * FIN_ITEMS;  // warp w: [base + 256 w, base + 256 (w+1))
-constexpr uint32_t WBASE_SMEM = 12288;                   // targets whose window bases fit shared memory
+constexpr uint32_t FIN_BUCKETS = 4096;  // window ranges of the target lookup table
 
 __device__ __forceinline__ uint32_t hk_of(uint64_t v) { return (uint32_t)(v >> 32); }
 
@@ -612,22 +612,35 @@ __global__ void __launch_bounds__(BT) k_fin_count(const uint64_t* __restrict__ a
 // Writes the condensed outputs at the scanned positions: locations of kept
 // pairs (global window -> (target, window)), and per feature its h2 value,
 // the position of its first location and the index of its first pair.
+// The target of a global window gw is the last t with wbase[t] <= gw; a
+// block first tabulates that target for the first window of each of
+// FIN_BUCKETS equal window ranges, which narrows every search to the
+// targets that overlap gw's range (one or two for genome-sized targets).
 __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
                                                  const uint64_t* __restrict__ tkept, const uint64_t* __restrict__ tkeys,
                                                  uint64_t n_tiles, const uint32_t* __restrict__ wbase,
                                                  uint32_t n_targets, uint64_t* __restrict__ locs,
                                                  uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
                                                  uint64_t* __restrict__ kstart, unsigned long long* overflow) {
-    extern __shared__ uint32_t wb_sm[];
+    __shared__ uint32_t first_target[FIN_BUCKETS + 1];
     __shared__ uint32_t wk[NWARP], wsx[NWARP];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
-    const bool wb_in_smem = n_targets + 1 <= WBASE_SMEM;
-    if (wb_in_smem)
-        for (uint32_t i = threadIdx.x; i <= n_targets; i += BT) wb_sm[i] = wbase[i];
+    const uint32_t* wb = wbase;
+    const uint64_t n_win = wb[n_targets];
+    uint32_t bshift = 0;
+    while ((n_win >> bshift) >= FIN_BUCKETS) ++bshift;
+    for (uint32_t b = threadIdx.x; b <= FIN_BUCKETS; b += BT) {
+        const uint64_t x = (uint64_t)b << bshift;
+        uint32_t lo = 0, hi = n_targets;  // last t with wb[t] <= x
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (wb[mid] <= x) lo = mid; else hi = mid;
+        }
+        first_target[b] = lo;
+    }
     __syncthreads();
-    const uint32_t* wb = wb_in_smem ? wb_sm : wbase;
     unsigned long long n_over = 0;
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const uint64_t base = tile * FIN_TILE + (uint64_t)w * 32 * FIN_ITEMS + lane;
@@ -663,7 +676,9 @@ __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a,
             const uint64_t my_k = kpos + __popc(bk & lt);
             if (kept) {
                 const uint32_t gw = (uint32_t)v[i];
-                uint32_t lo = 0, hi = n_targets;  // last t with wb[t] <= gw
+                const uint32_t rng = gw >> bshift;  // < FIN_BUCKETS since gw < n_win
+                uint32_t lo = first_target[rng];    // last t with wb[t] <= gw lies in [lo, hi)
+                uint32_t hi = min(first_target[rng + 1] + 1, n_targets);
                 while (hi - lo > 1) {
                     const uint32_t mid = (lo + hi) >> 1;
                     if (wb[mid] <= gw) lo = mid; else hi = mid;
@@ -809,12 +824,8 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     Tmp<uint32_t> khk(mem, n_keys, s);
     if (!locs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
-        const size_t wb_smem = n_targets + 1 <= WBASE_SMEM ? (size_t)(n_targets + 1) * 4 : 0;
-        if ((e = cudaFuncSetAttribute(k_fin_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(WBASE_SMEM * 4))) !=
-            cudaSuccess)
-            return e;
         MC_LAUNCH("fin_emit", s,
-                  k_fin_emit<<<g, BT, wb_smem, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets,
+                  k_fin_emit<<<g, BT, 0, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets,
                                                      locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
