@@ -451,9 +451,10 @@ __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const Classif
             const uint32_t idx = base + b * 32 + lane;
             hk[b] = idx < F ? hash_h2(S.feat[idx]) : 0u;
             pos[b] = db.log_t >= 32 ? hk[b] : (hk[b] >> (32 - db.log_t));
-            // the home slot and the next one (the table has 2 slots of padding)
+            // the home slot, and the next one when both lie in the same 64-byte
+            // segment (the table has 2 slots of padding)
             e[b] = idx < F ? __ldg(db.table + pos[b]) : make_uint4(0, 0, 0, 0);
-            e2[b] = idx < F ? __ldg(db.table + pos[b] + 1) : make_uint4(0, 0, 0, 0);
+            e2[b] = (idx < F && (pos[b] & 3) != 3) ? __ldg(db.table + pos[b] + 1) : make_uint4(0, 0, 0, 0);
         }
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
@@ -462,7 +463,8 @@ __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const Classif
             uint64_t off = 0;
             if (idx < F) {
                 uint4 x = e[b];
-                if (x.y != 0 && x.x < hk[b] && db.max_probe >= 1) x = e2[b];
+                if (x.y != 0 && x.x < hk[b] && db.max_probe >= 1)
+                    x = (pos[b] & 3) != 3 ? e2[b] : __ldg(db.table + pos[b] + 1);
                 for (uint32_t d = 2; x.y != 0 && x.x < hk[b] && d <= db.max_probe; ++d) x = __ldg(db.table + pos[b] + d);
                 if (x.y != 0 && x.x == hk[b]) {
                     c = x.y;
