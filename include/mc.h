@@ -92,10 +92,13 @@ typedef struct mc_classify_params {
                                 0..MC_MAX_INSERT */
 } mc_classify_params;
 
-/* Device memory provider.  alloc returns device memory of at least `bytes`
- * usable in stream order on `stream` (NULL on failure); free releases it in
- * stream order.  A provider such as PyTorch's caching allocator can back
- * every allocation of the library. */
+/* Device memory provider.  alloc returns device memory of at least `bytes`,
+ * aligned to 256 bytes (as cudaMallocAsync and PyTorch's caching allocator
+ * align), usable in stream order on `stream` (NULL on failure); free
+ * releases it in stream order.  A block that is not 256-byte aligned is
+ * handed back to free and the call fails with MC_ERR_OOM.  A provider such
+ * as PyTorch's caching allocator can back every allocation of the
+ * library. */
 typedef struct mc_allocator {
     void* (*alloc)(void* ctx, size_t bytes, void* stream);
     void (*free)(void* ctx, void* ptr, size_t bytes, void* stream);

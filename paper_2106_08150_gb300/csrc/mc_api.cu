@@ -128,7 +128,16 @@ TraceScope::~TraceScope() {
     if (slot < (int)g_trace_pending.size()) cudaEventRecord(g_trace_pending[slot].b, stream);
 }
 
-void* Mem::alloc(size_t bytes, cudaStream_t s) const { return a.alloc(a.ctx, bytes, (void*)s); }
+// Kernels use 16- and 32-byte vector accesses from the start of a block:
+// a provider's block must be 256-byte aligned (else it is returned).
+void* Mem::alloc(size_t bytes, cudaStream_t s) const {
+    void* p = a.alloc(a.ctx, bytes, (void*)s);
+    if (p && ((uintptr_t)p & 255u)) {
+        a.free(a.ctx, p, bytes, (void*)s);
+        return nullptr;
+    }
+    return p;
+}
 void Mem::free(void* p, size_t bytes, cudaStream_t s) const {
     if (p) a.free(a.ctx, p, bytes, (void*)s);
 }
