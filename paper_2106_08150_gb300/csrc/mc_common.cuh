@@ -1,6 +1,6 @@
-// Shared device helpers of the sm_103a MetaCache-GPU kernels: base encoding,
-// k-mer hashing (h1) and table-slot hashing (h2), warp helpers and the
-// internal launch interface between the translation units.
+// Shared device helpers of the sm_103a MetaCache-GPU kernels: k-mer hashing
+// (h1) and table-slot hashing (h2), window counts, warp helpers and the
+// parameters shared by the translation units.
 #pragma once
 
 #include <cstdint>
@@ -76,16 +76,8 @@ __host__ __device__ __forceinline__ uint32_t hash_h2_inverse(uint32_t y) {
     return y;
 }
 
-// ------------------------------------------------------------- encoding
-// Reverse complement of a k-mer code held in the low 2k bits (first base
-// most significant): reverse the 2-bit digits, complement each.
-__device__ __forceinline__ uint32_t revcomp_code(uint32_t fwd, uint32_t k) {
-    uint32_t r = __brev(fwd);
-    r = ((r >> 1) & 0x55555555u) | ((r & 0x55555555u) << 1);  // restore bit order inside digits
-    r = ~r;
-    return r >> (32 - 2 * k);
-}
-
+// ------------------------------------------------------ windows, lanes
+// Windows of a sequence of length L (k-mer starts 0, stride, 2 stride, ...).
 __host__ __device__ __forceinline__ uint64_t num_windows(uint64_t L, uint32_t k, uint32_t stride) {
     return L < k ? 0 : (L - k + stride) / stride;
 }

@@ -10,7 +10,8 @@
 //     the k-mers starting at R*l .. R*l+R-1 (Section 5.3 does the same with
 //     4-base loads and sub-warp shuffles; here the window start is any base,
 //     the stride need not be a multiple of 4);
-//  3. canonical code = min(forward, reverse complement), hashed by h1;
+//  3. canonical code = min(forward, reverse complement), hashed by h1
+//     (the reverse complement of all the lane's bases is formed once);
 //  4. the s smallest distinct hashes (Section 2: repeated k-mers count
 //     once) are selected by a cutoff + warp bitonic sort, with an exact
 //     min-reduction fallback (see warp_sketch_multi).
@@ -139,15 +140,20 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
             comb = (comb << (2 * R)) | __shfl_down_sync(FULL_MASK, code, e);
             combinv = (combinv << R) | __shfl_down_sync(FULL_MASK, inv, e);
         }
-        // 3. canonical k-mers and h1
+        // 3. canonical k-mers and h1; the reverse complement of the lane's T
+        // bases is formed once (reverse the 2-bit digits, complement), and
+        // the k-mer starting at base r reads as its digits 2r .. 2r + 2k - 1
         vmask[w] = 0;
+        uint64_t rcomb = __brevll(comb);
+        rcomb = ((rcomb >> 1) & 0x5555555555555555ull) | ((rcomb & 0x5555555555555555ull) << 1);
+        rcomb = ~rcomb >> (64 - 2 * T);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             const uint32_t shift = (uint32_t)(T - r) - k;  // >= 0 since T >= R + k - 1
             const uint32_t fwd = (uint32_t)((comb >> (2 * shift)) & cmask);
             const bool bad = ((combinv >> shift) & imask) != 0;
             const bool ok = ((uint32_t)R * lane + r < n_k) && !bad;
-            const uint32_t rc = revcomp_code(fwd, k);
+            const uint32_t rc = (uint32_t)((rcomb >> (2 * r)) & cmask);
             h[w][r] = ok ? hash_h1(fwd < rc ? fwd : rc) : 0xFFFFFFFFu;
             vmask[w] |= (ok ? 1u : 0u) << r;
         }
