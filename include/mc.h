@@ -145,7 +145,13 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
  * (Section 4.2 / 5.1: all buckets in one contiguous array, a single-value
  * hash table from feature to bucket).  Each feature keeps its bucket_cap
  * smallest locations, sorted ascending.  Idempotent; required before
- * mc_classify.  Synchronises the database stream. */
+ * mc_classify.  Synchronises the database stream.  MC_ERR_OOM if the sort
+ * buffers cannot be allocated: nothing has changed and the call can be
+ * repeated.  A failure after the sort has run (MC_ERR_OOM for the layout
+ * buffers, MC_ERR_CUDA on a CUDA error, including a sort whose tiles
+ * waited more than 2 s for earlier tiles' counts) keeps the previous
+ * layout published for mc_classify, and later mc_db_add_targets and
+ * mc_db_finalize calls return MC_ERR_STATE. */
 int mc_db_finalize(mc_db* db);
 
 /* Classifies queries (Section 4.2 query phase, Section 5.2 query steps 1-8).

@@ -168,6 +168,10 @@ struct mc_db {
     uint64_t n_kept = 0, n_keys = 0, table_len = 0, overflow_keys = 0, n_pairs = 0;
     uint32_t log_t = 1, max_probe = 0;
     bool dirty = false, has_table = false;
+    // a finalize failed after its sort had consumed the pending pairs: the
+    // last published layout still serves classification, but nothing can
+    // be added or finalized any more
+    bool failed = false;
     uint64_t epoch = 0;  // finalizes so far (plans re-capture when it changes)
     cudaEvent_t ready = nullptr;
     DevBuf status;  // u32 device status word
@@ -434,6 +438,7 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
                       uint32_t* first_target_id) {
     g_err[0] = 0;
     if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    if (db->failed) return fail(MC_ERR_STATE, "the database cannot grow after a failed mc_db_finalize");
     if (first_target_id) *first_target_id = db->n_targets;
     if (n_targets == 0) return MC_OK;
     if (!seq || !offs || !taxon) return fail(MC_ERR_ARG, "seq, offs and taxon must not be NULL");
@@ -487,44 +492,56 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
 int mc_db_finalize(mc_db* db) {
     g_err[0] = 0;
     if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    if (db->failed) return fail(MC_ERR_STATE, "an earlier mc_db_finalize failed after consuming the added targets");
     if (!db->dirty && db->has_table) return MC_OK;
     cudaStream_t s = db->stream;
     const uint64_t n_old = db->n_kept;
     const uint64_t n_total = n_old + db->pending_n;
     const uint64_t n_real = n_old + db->pending_real;
-    // sort input: previously kept pairs (sorted) followed by the new pairs
+    // sort input: previously kept pairs (sorted) followed by the new pairs;
+    // without previous pairs the pending buffer itself is sorted in place.
+    // Until the sort starts a failure leaves the pending pairs as they were.
     DevBuf a, b;
-    if (n_old == 0) {
+    const bool a_is_pending = n_old == 0;
+    if (a_is_pending) {
         a = db->pending;
-        db->pending = DevBuf();
     } else {
         if (!within_budget(db, n_total * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
         if (!grab(db, a, n_total * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
-        MC_CU(mc::reconstruct_pairs((const uint4*)db->table.p, db->table_len, (const uint64_t*)db->locs.p,
-                                    (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s));
-        if (db->pending_n)
-            MC_CU(cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s));
-        release(db, db->pending);
+        cudaError_t e = mc::reconstruct_pairs((const uint4*)db->table.p, db->table_len, (const uint64_t*)db->locs.p,
+                                              (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s);
+        if (e == cudaSuccess && db->pending_n)
+            e = cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) {
+            release(db, a);
+            return cuda_fail(e, "finalize: gather of the stored pairs");
+        }
     }
-    auto cleanup = [&]() {
-        release(db, a);
+    auto release_tmp = [&]() {
+        if (!a_is_pending) release(db, a);
         release(db, b);
     };
     if (!grab(db, b, n_total * 8)) {
-        cleanup();
+        release_tmp();
         return fail(MC_ERR_OOM, "finalize: allocation failed");
     }
     cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)a.p, (uint64_t*)b.p, n_total, n_real, s);
     if (e != cudaSuccess) {
-        cleanup();
+        release_tmp();
+        // the sort allocates its scratch before it touches the pairs
+        if (e != cudaErrorMemoryAllocation) db->failed = true;
         return cuda_fail(e, "finalize: sort");
     }
     release(db, b);
     mc::FinalizeOut fo;
     e = mc::finalize_pairs(db->mem, (const uint64_t*)a.p, n_real, db->cap, (const uint32_t*)db->wbase.p,
                            db->n_targets, &fo, s);
-    cleanup();
-    if (e != cudaSuccess) return cuda_fail(e, "finalize: layout");
+    release_tmp();
+    if (e != cudaSuccess) {
+        db->failed = true;
+        return cuda_fail(e, "finalize: layout");
+    }
+    release(db, db->pending);
     retire(db, db->locs);
     retire(db, db->table);
     db->locs = DevBuf{fo.locs, fo.n_kept * 8};

@@ -82,8 +82,9 @@ cudaError_t emit_pairs(const SketchParams& p, uint32_t n_targets, const uint8_t*
 // Stable LSD radix sort of pairs by their upper 32 bits (4 passes of 8
 // bits).  The first pass drops sentinel pairs.  in holds n_total entries
 // on entry, the n_real sorted real pairs on return; tmp has n_total room.
-// Synchronizes the stream; cudaErrorTimeout if a tile's wait for earlier
-// tiles' counts gave up (the order is then wrong).
+// Synchronizes the stream; cudaErrorMemoryAllocation (before any pair is
+// touched) if its scratch cannot be allocated; cudaErrorTimeout if a tile's
+// wait for earlier tiles' counts gave up (the order is then wrong).
 cudaError_t sort_pairs(const Mem& mem, uint64_t* in, uint64_t* tmp, uint64_t n_total, uint64_t n_real,
                        cudaStream_t s);
 
