@@ -183,9 +183,9 @@ constexpr int SK_NW = 2;  // windows sketched together by a warp
 
 // One warp per window; a warp takes WINDOWS_PER_TASK consecutive windows
 // and walks the sequences they belong to.  EMIT = build pairs, else the
-// debug sketch export.
+// debug sketch export.  Five resident blocks per SM (48 registers).
 template <int R, int KC, bool EMIT>
-__global__ void __launch_bounds__(BT) k_sketch(SketchParams p, uint32_t n_seq, const uint8_t* __restrict__ seq,
+__global__ void __launch_bounds__(BT, 5) k_sketch(SketchParams p, uint32_t n_seq, const uint8_t* __restrict__ seq,
                                                const uint64_t* __restrict__ offs,
                                                const uint64_t* __restrict__ win_offs, uint64_t n_windows,
                                                uint32_t gw_base, uint64_t* __restrict__ pairs,
