@@ -224,6 +224,21 @@ def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
     return None
 
 
+def build_random_roofline(n_bp: int, n_pairs: int, n_locations: int, read32_gbs: float, copy_gbs: float,
+                          achieved_gbps: float) -> dict:
+    """The build against the HBM random-access roofline, with the method's
+    insert model: per pair a 32-byte key-slot update and a 32-byte value
+    write at random positions, served at the measured random 32-byte read
+    rate; the bases read once and every stored location read and written
+    once (16 bytes), streamed at the copy peak."""
+    rand_b = 64.0 * n_pairs / n_bp
+    stream_b = 1.0 + 16.0 * n_locations / n_bp
+    roof = 1.0 / (rand_b / (read32_gbs * 1e9) + stream_b / (copy_gbs * 1e9)) / 1e9
+    return {"achieved_gbps": round(achieved_gbps, 2), "roofline_gbps": round(roof, 1),
+            "frac": round(achieved_gbps / roof, 4), "random_bytes_per_bp": round(rand_b, 3),
+            "stream_bytes_per_bp": round(stream_b, 3), "unit": "Gbp/s"}
+
+
 def load_traffic():
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
@@ -460,19 +475,8 @@ def run_gpu(args, rank, world, local_rank):
             if b is not None and per:
                 ach = b / per / (kernels[kname]["avg_ms"] * 1e-3) / 1e9
                 rand_roof[kname] = {"achieved_gbs": round(ach, 1), "frac_of_read32": round(ach / rand[32], 4)}
-    # build against the same roofline: the insert model of the method (per
-    # pair a 32-byte key-slot update and a 32-byte value write at random
-    # positions, served at the measured random 32-byte rate; the bases read
-    # once and every stored location read and written once, streamed at the
-    # copy peak)
-    pairs_per_bp = st["n_pairs"] / w.n_bp
-    rand_b = 64.0 * pairs_per_bp
-    stream_b = 1.0 + 16.0 * st["n_locations"] / w.n_bp
-    build_roof = 1.0 / (rand_b / (rand[32] * 1e9) + stream_b / (peak * 1e9)) / 1e9
     build_ach = world * w.n_bp * args.steps / (build_ms * 1e-3) / 1e9
-    rand_roof["build"] = {"achieved_gbps": round(build_ach, 2), "roofline_gbps": round(build_roof, 1),
-                          "frac": round(build_ach / build_roof, 4), "random_bytes_per_bp": round(rand_b, 3),
-                          "stream_bytes_per_bp": round(stream_b, 3), "unit": "Gbp/s"}
+    rand_roof["build"] = build_random_roofline(w.n_bp, st["n_pairs"], st["n_locations"], rand[32], peak, build_ach)
 
     value = whole_job_rate(nq, world, args.steps, total_ms)
     out = {

@@ -63,3 +63,26 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "Mreads/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_build_random_roofline_arithmetic():
+    import bench
+    # every base a pair (64 random bytes) and a location (16 streamed bytes
+    # + the base): 1 / (64 / 100 + 17 / 1000) Gbp/s at 100 and 1000 GB/s
+    r = bench.build_random_roofline(10**9, 10**9, 10**9, 100.0, 1000.0, 0.5)
+    assert r["random_bytes_per_bp"] == 64.0 and r["stream_bytes_per_bp"] == 17.0
+    assert abs(r["roofline_gbps"] - round(1.0 / (0.64 + 0.017), 1)) < 1e-9
+    assert abs(r["frac"] - round(0.5 / (1.0 / 0.657), 4)) < 1e-9
+    # the mid workload's counts at the measured rates give about 155 Gbp/s
+    m = bench.build_random_roofline(3_680_156_920, 521_089_020, 521_089_020, 1517.0, 6801.0, 93.7)
+    assert 150.0 < m["roofline_gbps"] < 160.0 and 0.55 < m["frac"] < 0.65
+
+
+def test_algorithmic_bytes_of_the_sort_kernels():
+    import types
+    import bench
+    w = types.SimpleNamespace(db_params={"sketch_size": 16}, n_bp=1000)
+    st = {"n_windows": 10, "n_pairs": 150}
+    # 160 pair slots in the first pass, 150 real pairs in the other three
+    assert bench.algorithmic_bytes("radix_totals", w, st, None) == 160 * 8
+    assert bench.algorithmic_bytes("radix_pass", w, st, None) == (160 + 3 * 150) * 8 + 4 * 150 * 8
