@@ -4,13 +4,19 @@
 One step = the whole hot path over one batch of synthetic input: build the
 database from the reference genomes (sketch, sort, cap, condensed layout)
 and classify every read pair against it (the paper's on-the-fly mode,
-Section 6.3).  The default workload is the mid-size configuration: 1,000
-genomes (~3.4 Gbp) in 100 genera, 10M paired-end 2x150 bp reads.
+Section 6.3).  The default workload is the large single-GPU database:
+10,000 genomes (about 14.3 Gbp: 980 genera of bacterial-like genomes plus 200
+repeat-rich eukaryote-like genomes that overfill buckets) and 50M
+paired-end 2x150 bp reads.  `--workload mid` is the 1,000-genome / 10M-pair
+configuration.
 
 Prints one JSON line.  `value` is read pairs classified per second over the
 whole step (build included); `build_gbps` and `classify_mreads_s` split it.
-`--impl reference` times the CPU oracle (the reference arm of this build) on
-a bounded sample of the same workload, in the same unit.
+The batched mixed-length section and the served section (an offered-load
+sweep of the request loop against the plain one-job-per-launch path) run
+against the same database.  `--impl reference` times the CPU oracle (the
+reference arm of this build) on a bounded sample of the same workload, in
+the same unit.
 
 Multi-GPU: the path shards by reads with a replicated database (no data-path
 collective), so N ranks run independent replicas (weak scaling).
@@ -44,28 +50,30 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["mid", "small", "tiny"], default="mid",
-                    help="mid = 1,000 genomes / 10M pairs (the measured configuration); small/tiny for profiling")
+    ap.add_argument("--workload", choices=["large", "mid", "small", "tiny"], default="large",
+                    help="large = 10,000 genomes (~14.3 Gbp, repeat-rich) / 50M pairs (the measured configuration); "
+                         "mid = 1,000 genomes / 10M pairs; small/tiny for profiling")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-genera", type=int, default=2)
     ap.add_argument("--cpu-sample-pairs", type=int, default=20000)
     ap.add_argument("--batches", type=int, default=256,
                     help="mixed-length query batches of the batched-classification section (0 = skip)")
-    ap.add_argument("--serve-seconds", type=float, default=60.0,
-                    help="length of the served-loop section (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="seconds of arrivals at each offered load of the served section (0 = skip)")
+    ap.add_argument("--serve-loads", type=str, default="0.5,0.7,0.9,1.1,1.3",
+                    help="offered loads of the served section, as fractions of the tuned batched throughput")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct jobs the served section cycles through")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape for the classify kernels")
-    ap.add_argument("--sections-db", choices=["main", "large"], default="main",
-                    help="database of the batched and served sections: the main workload's, or the large "
-                         "repeat-rich recipe (scaled, about 15 Gbp)")
     return ap.parse_args()
 
 
 # ----------------------------------------------------------------- workload
 def make_workload(name: str, rank: int):
     import synth
-    if name == "mid":
+    if name == "large":
+        w = synth.large_workload(seed=1002, scaled=True, held_genera=5, held_per_genus=10)
+    elif name == "mid":
         w = synth.mid_workload(seed=1001)
     elif name == "small":
         w = synth.mid_workload(seed=1001, n_families=1, genera_per_family=10, n_pairs=1_000_000)
@@ -93,7 +101,8 @@ def workload_config(w, args, n_gpus):
         "lca_band_pct": w.cls_params["lca_band_pct"], "max_insert": w.cls_params["max_insert"],
         "step": "build database from all genomes + classify all read pairs (on-the-fly)",
         "parallelism": f"replicas{n_gpus}" if n_gpus > 1 else "single",
-        "l2": "inputs larger than L2 (genomes 3.4 GB, reads 3 GB)" if args.workload == "mid" else "small workload",
+        "l2": (f"inputs larger than L2 (genomes {w.n_bp / 1e9:.1f} GB, reads {w.reads.size / 1e9:.1f} GB)"
+               if w.n_bp > (1 << 30) else "small workload"),
         "recipe": w.recipe,
     }
 
@@ -237,6 +246,23 @@ def build_random_roofline(n_bp: int, n_pairs: int, n_locations: int, read32_gbs:
     return {"achieved_gbps": round(achieved_gbps, 2), "roofline_gbps": round(roof, 1),
             "frac": round(achieved_gbps / roof, 4), "random_bytes_per_bp": round(rand_b, 3),
             "stream_bytes_per_bp": round(stream_b, 3), "unit": "Gbp/s"}
+
+
+def build_rooflines(n_bp: int, st: dict, read32_gbs: float, copy_gbs: float, achieved_gbps: float) -> dict:
+    """The build against both rooflines: the sector model (every algorithmic
+    byte at the copy peak: 1 B per base read once, per pair a 32-byte
+    key-slot update and a 32-byte value write, per stored location 16 B read
+    and written once) and the random-access model (the pair bytes at the
+    measured random 32-byte read rate, the rest at the copy peak)."""
+    sector_b = 1.0 + 64.0 * st["n_pairs"] / n_bp + 16.0 * st["n_locations"] / n_bp
+    sector_roof = copy_gbs / sector_b
+    return {
+        "sector_model": {"bytes_per_bp": round(sector_b, 3), "roofline_gbps": round(sector_roof, 1),
+                         "frac": round(achieved_gbps / sector_roof, 4), "peak_gbs": copy_gbs},
+        "random_access_model": build_random_roofline(n_bp, st["n_pairs"], st["n_locations"], read32_gbs, copy_gbs,
+                                                     achieved_gbps),
+        "achieved_gbps": round(achieved_gbps, 2), "unit": "Gbp/s",
+    }
 
 
 def load_traffic():
@@ -464,7 +490,8 @@ def run_gpu(args, rank, world, local_rank):
     # random-access roofline: the feature-table probes and bucket gathers
     # read 16-32 bytes at random positions, which HBM serves far below the
     # copy bandwidth; measured here on this GPU (8 GiB buffer, 2^28 reads)
-    rand = {w_: round(mc.mc_measure_random_read(8 << 30, w_, 1 << 28, stream), 1) for w_ in (16, 32)}
+    import membench
+    rand = {w_: round(membench.random_read_gbs(8 << 30, w_, 1 << 28, stream.cuda_stream), 1) for w_ in (16, 32)}
     rand_roof = {"read16_gbs": rand[16], "read32_gbs": rand[32], "unit": "GB/s",
                  "note": "best of 6 shapes of random aligned reads of 16 / 32 bytes, 8 GiB buffer; the classify "
                          "kernels' algorithmic bytes count 32-byte sectors, so they are compared with read32_gbs"}
@@ -484,12 +511,13 @@ def run_gpu(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
         "config": workload_config(w, args, world),
-        "build_gbps": round(world * w.n_bp * args.steps / (build_ms * 1e-3) / 1e9, 3),
+        "build_gbps": round(build_ach, 3),
         "classify_mreads_s": round(world * nq * args.steps / (cls_ms * 1e-3) / 1e6, 3),
         "classify_mates_mreads_s": round(world * w.n_seq * args.steps / (cls_ms * 1e-3) / 1e6, 3),
         "build_ms_per_step": round(build_ms / args.steps, 3), "classify_ms_per_step": round(cls_ms / args.steps, 3),
-        "db": {k: st[k] for k in ["n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys", "table_slots",
-                                  "max_probe", "load_factor"]},
+        "db": {k: st[k] for k in ["n_targets", "n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys",
+                                  "dropped_locations", "table_slots", "max_probe", "load_factor", "device_bytes"]},
+        "build_roofline": build_rooflines(w.n_bp, st, rand[32], peak, build_ach),
         "classify_counters": {"features": int(ctr[0]), "locations": int(ctr[1]), "distinct_locations": int(ctr[2]),
                               "large_path_queries": int(ctr[3]), "medium_path_queries": int(ctr[6]),
                               "features_found": int(ctr[4]),
@@ -498,23 +526,18 @@ def run_gpu(args, rank, world, local_rank):
         "random_access_roofline": rand_roof,
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4)} for k, v in kernels.items()},
+        "kernels": {k: {"launches": v["launches"], "avg_ms": round(v["avg_ms"], 4),
+                        "share": round(v["total_ms"] / max(sum(x["total_ms"] for x in kernels.values()), 1e-9), 4)}
+                    for k, v in kernels.items()},
         "clocks": clk,
         "generation_s": round(t_gen, 1),
         "classify_tuning": tuned.as_dict() if tuned is not None else "default",
     }
-    ws = w
-    if args.sections_db == "large" and world == 1 and (args.batches or args.serve_seconds > 0):
-        import synth
-        t0 = time.time()
-        ws = synth.large_workload(seed=1002, scaled=True, n_pairs=1000, held_genera=5, held_per_genus=10)
-        out["sections_db"] = {"workload": ws.name, "genomes": ws.n_targets, "genome_bp": ws.n_bp,
-                              "recipe": ws.recipe, "generation_s": round(time.time() - t0, 1)}
     if args.batches and world == 1:
-        out["batched"] = run_batched(args, ws, dev, stream)
-    if args.serve_seconds > 0 and world == 1 and ws.held is not None:
+        out["batched"] = run_batched(args, w, dev, stream)
+    if args.serve_seconds > 0 and world == 1 and w.held is not None:
         rate = out.get("batched", {}).get("graph_tuned", {}).get("mreads_s")
-        out["served"] = run_served(args, ws, dev, stream, rate)
+        out["served"] = run_served_sweep(args, w, dev, stream, rate, tuned)
     return out, w
 
 
@@ -560,20 +583,24 @@ def run_batched(args, w, dev, stream):
             if nq:
                 mc.mc_classify(db.handle, cp, n_seq, seq, offs, nq, qo, *o, stream=stream)
 
+    # each variant: warm-up runs, then timed runs (fewer than the main step's
+    # counts, so that the section stays short on the large database)
+    n_warm, n_time = max(1, min(args.warmup, 2)), max(1, min(args.steps, 5))
+
     def timed(fn):
-        for _ in range(args.warmup):
+        for _ in range(n_warm):
             fn()
         torch.cuda.synchronize()
         n0 = mc.mc_kernel_launches()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        for _ in range(args.steps):
+        for _ in range(n_time):
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / args.steps
+        ms = a.elapsed_time(b) / n_time
         return {"mreads_s": round(total_q / (ms * 1e-3) / 1e6, 3), "ms": round(ms, 3),
-                "launches": (mc.mc_kernel_launches() - n0) // args.steps}
+                "launches": (mc.mc_kernel_launches() - n0) // n_time, "runs": n_time}
 
     def same():
         mc.mc_classify_status(db.handle, stream)
@@ -635,14 +662,15 @@ def run_batched(args, w, dev, stream):
 
 
 # ------------------------------------------------------------ served loop
-def run_served(args, w, dev, stream, batched_rate_mreads_s: float | None):
-    """Request loop over the resident database (mc_server): Poisson job
-    arrivals at 70% of the batched throughput, job sizes lognormal (median
-    1e5, sigma 1.5) in [1e3, 5e6], read lengths U(75, 250), half single-end
-    half pairs, 5% of reads from not-yet-inserted species; the held-out
-    species are inserted live in two extensions during the run.  The same
-    arrival sequence is then replayed through the plain path (one
-    mc_classify call per job, copies in and out, one job at a time)."""
+def run_served_sweep(args, w, dev, stream, batched_rate_mreads_s: float | None, tuned):
+    """Request loop over the resident database (mc_server) at several
+    offered loads (fractions of the tuned batched throughput): Poisson job
+    arrivals, job sizes lognormal (median 1e5, sigma 1.5) in [1e3, 5e6], read
+    lengths U(75, 250), half single-end half pairs, 5% of reads from
+    not-yet-inserted species; the held-out species are inserted live in two
+    extensions during each run.  The same arrival sequence is then replayed
+    in full through the plain path (one mc_classify call per job, copies in
+    and out, one job at a time)."""
     import torch
     import synth
     from paper_2106_08150_gb300 import mc
@@ -660,104 +688,122 @@ def run_served(args, w, dev, stream, batched_rate_mreads_s: float | None):
     mean_q = float(np.mean(sizes))
     ring = 64
     outs = [[torch.empty(max_q, dtype=torch.int32).pin_memory() for _ in range(3)] for _ in range(ring)]
-    rate_q = 0.7 * (batched_rate_mreads_s or 50.0) * 1e6
-    rate_jobs = rate_q / mean_q
-    dur = args.serve_seconds
-    n_arr = int(rng.poisson(rate_jobs * dur))
-    arrivals = np.sort(rng.uniform(0, dur, n_arr))
-    which = rng.integers(0, len(jobs), n_arr)
     hblob, hoffs, htaxon = w.held
     n_held = len(htaxon)
     ext_cut = [0, n_held // 2, n_held]
-    ext_at = [dur / 3, 2 * dur / 3]
-
-    db = mc.Database.create(w.parent, stream=stream, **w.db_params)
-    db.add_targets(torch.from_numpy(w.genomes).to(dev), torch.from_numpy(w.goffs.view(np.int64)).to(dev),
-                   w.taxon_of_target)
-    db.finalize()
     cp = mc.classify_params(**dict(w.cls_params, max_insert=0))
-    srv = mc.Server(db.handle, cp, n_streams=3)
-    n0 = mc.mc_kernel_launches()
-    ids, epochs, next_ext = [], [], 0
-    t_start = time.perf_counter()
-    for k, (ta, jb) in enumerate(zip(arrivals, which)):
-        while next_ext < 2 and time.perf_counter() - t_start >= ext_at[next_ext]:
-            a, b = ext_cut[next_ext], ext_cut[next_ext + 1]
-            lo, hi = int(hoffs[a]), int(hoffs[b])
-            srv.extend(hblob[lo:hi], hoffs[a:b + 1] - np.uint64(lo), htaxon[a:b])
-            next_ext += 1
-        delay = ta - (time.perf_counter() - t_start)
-        if delay > 0:
-            time.sleep(delay)
-        if k >= ring:
-            srv.wait(ids[k - ring])  # the output slot is free again
-        n_seq, nq, seq, offs, qo = jobs[jb]
-        o = outs[k % ring]
-        ids.append(srv.submit(n_seq, seq, offs, qo, o[0], o[1], o[2]))
-    while next_ext < 2:
-        a, b = ext_cut[next_ext], ext_cut[next_ext + 1]
+    base_rate = batched_rate_mreads_s or 50.0
+    d_g, d_go = torch.from_numpy(w.genomes).to(dev), torch.from_numpy(w.goffs.view(np.int64)).to(dev)
+    d_out = [torch.empty(max_q, dtype=torch.int32, device=dev) for _ in range(3)]
+    dur = args.serve_seconds
+
+    def fresh_db():
+        db = mc.Database.create(w.parent, stream=stream, **w.db_params)
+        if tuned is not None:
+            mc.mc_db_set_tuning(db.handle, tuned)
+        db.add_targets(d_g, d_go, w.taxon_of_target)
+        db.finalize()
+        return db
+
+    def extend(srv, i):
+        a, b = ext_cut[i], ext_cut[i + 1]
         lo, hi = int(hoffs[a]), int(hoffs[b])
         srv.extend(hblob[lo:hi], hoffs[a:b + 1] - np.uint64(lo), htaxon[a:b])
-        next_ext += 1
-    srv.drain()
-    wall = time.perf_counter() - t_start
-    st = srv.stats()
-    launches = mc.mc_kernel_launches() - n0
-    # the last jobs ran on the final database: replay them alone and compare
-    last = [(k, ids[k]) for k in range(max(0, len(ids) - 3), len(ids))]
-    infos = {k: srv.wait(i) for k, i in last}
-    srv.free()
-    same = True
-    for k, info in infos.items():
-        if info["epoch"] != 2:
-            continue
-        n_seq, nq, seq, offs, qo = jobs[which[k]]
-        out = [torch.empty(nq, dtype=torch.int32, device=dev) for _ in range(3)]
-        mc.mc_classify(db.handle, cp, n_seq, seq.to(dev), offs.to(dev), nq, qo.to(dev), *out, stream=stream)
-        stream.synchronize()
-        same = same and all(bool(torch.equal(x.cpu(), y[:nq])) for x, y in zip(out, outs[k % ring]))
 
-    # plain path over the same arrivals on the final database, one job at a time
-    plain_dur = min(dur, 20.0)
-    lat, q_done = [], 0
-    t_start = time.perf_counter()
-    d_out = [torch.empty(max_q, dtype=torch.int32, device=dev) for _ in range(3)]
-    for ta, jb in zip(arrivals, which):
-        if ta > plain_dur:
-            break
-        delay = ta - (time.perf_counter() - t_start)
-        if delay > 0:
-            time.sleep(delay)
-        n_seq, nq, seq, offs, qo = jobs[jb]
-        with torch.cuda.stream(stream):
-            ds, do, dq = seq.to(dev, non_blocking=True), offs.to(dev, non_blocking=True), qo.to(dev, non_blocking=True)
-            mc.mc_classify(db.handle, cp, n_seq, ds, do, nq, dq, *d_out, stream=stream)
-            for x, y in zip(outs[0], d_out):
-                x[:nq].copy_(y[:nq], non_blocking=True)
-        stream.synchronize()
-        lat.append(time.perf_counter() - t_start - ta)
-        q_done += nq
-    plain_wall = time.perf_counter() - t_start
-    db.free()
-    lat = np.sort(np.array(lat)) if lat else np.zeros(1)
+    def one_load(frac, seed):
+        r = np.random.default_rng(seed)
+        rate_q = frac * base_rate * 1e6
+        rate_jobs = rate_q / mean_q
+        n_arr = max(1, int(r.poisson(rate_jobs * dur)))
+        arrivals = np.sort(r.uniform(0, dur, n_arr))
+        which = r.integers(0, len(jobs), n_arr)
+        ext_at = [dur / 3, 2 * dur / 3]
+        db = fresh_db()
+        srv = mc.Server(db.handle, cp, n_streams=3)
+        n0 = mc.mc_kernel_launches()
+        ids, next_ext = [], 0
+        t_start = time.perf_counter()
+        for k, (ta, jb) in enumerate(zip(arrivals, which)):
+            while next_ext < 2 and time.perf_counter() - t_start >= ext_at[next_ext]:
+                extend(srv, next_ext)
+                next_ext += 1
+            delay = ta - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            if k >= ring:
+                srv.wait(ids[k - ring])  # the output slot is free again
+            n_seq, nq, seq, offs, qo = jobs[jb]
+            o = outs[k % ring]
+            ids.append(srv.submit(n_seq, seq, offs, qo, o[0], o[1], o[2]))
+        while next_ext < 2:
+            extend(srv, next_ext)
+            next_ext += 1
+        srv.drain()
+        wall = time.perf_counter() - t_start
+        st = srv.stats()
+        launches = mc.mc_kernel_launches() - n0
+        # the last jobs ran on the final database: replay them alone and compare
+        last = [(k, ids[k]) for k in range(max(0, len(ids) - 3), len(ids))]
+        infos = {k: srv.wait(i) for k, i in last}
+        srv.free()
+        same, checked = True, 0
+        for k, info in infos.items():
+            if info["epoch"] != 2:
+                continue
+            n_seq, nq, seq, offs, qo = jobs[which[k]]
+            out = [torch.empty(nq, dtype=torch.int32, device=dev) for _ in range(3)]
+            mc.mc_classify(db.handle, cp, n_seq, seq.to(dev), offs.to(dev), nq, qo.to(dev), *out, stream=stream)
+            stream.synchronize()
+            same = same and all(bool(torch.equal(x.cpu(), y[:nq])) for x, y in zip(out, outs[k % ring]))
+            checked += 1
+        # plain path: the same arrivals on the final database, one job at a time
+        lat, q_done = [], 0
+        t_start = time.perf_counter()
+        for ta, jb in zip(arrivals, which):
+            delay = ta - (time.perf_counter() - t_start)
+            if delay > 0:
+                time.sleep(delay)
+            n_seq, nq, seq, offs, qo = jobs[jb]
+            with torch.cuda.stream(stream):
+                ds, do, dq = (seq.to(dev, non_blocking=True), offs.to(dev, non_blocking=True),
+                              qo.to(dev, non_blocking=True))
+                mc.mc_classify(db.handle, cp, n_seq, ds, do, nq, dq, *d_out, stream=stream)
+                for x, y in zip(outs[0], d_out):
+                    x[:nq].copy_(y[:nq], non_blocking=True)
+            stream.synchronize()
+            lat.append(time.perf_counter() - t_start - ta)
+            q_done += nq
+        plain_wall = time.perf_counter() - t_start
+        db.free()
+        lat = np.sort(np.array(lat))
+        return {
+            "offered_load": frac, "offered_mreads_s": round(rate_q / 1e6, 3), "offered_jobs_s": round(rate_jobs, 2),
+            "jobs": int(st["jobs_done"]), "queries": int(st["queries_done"]),
+            "served": {"throughput_mreads_s": round(st["queries_done"] / max(st["busy_s"], 1e-9) / 1e6, 3),
+                       "wall_s": round(wall, 2), "p50_latency_s": round(st["p50_latency_s"], 4),
+                       "p99_latency_s": round(st["p99_latency_s"], 4),
+                       "max_latency_s": round(st["max_latency_s"], 4), "launch_sets": int(st["launch_sets"]),
+                       "gpu_launches": int(launches), "extensions": int(st["extensions"]),
+                       "hbm_peak_bytes": int(st["hbm_peak"]), "hbm_limit_bytes": int(st["hbm_limit"])},
+            "plain_one_job_per_launch": {
+                "throughput_mreads_s": round(q_done / plain_wall / 1e6, 3), "wall_s": round(plain_wall, 2),
+                "p50_latency_s": round(float(lat[len(lat) // 2]), 4),
+                "p99_latency_s": round(float(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))]), 4)},
+            "final_epoch_jobs_identical_alone": bool(same), "final_epoch_jobs_checked": checked,
+        }
+
+    loads = [float(x) for x in args.serve_loads.split(",") if x.strip()]
+    curve = [one_load(f, 1004 + i) for i, f in enumerate(loads)]
+    sat_served = max(c["served"]["throughput_mreads_s"] for c in curve)
+    sat_plain = max(c["plain_one_job_per_launch"]["throughput_mreads_s"] for c in curve)
     return {
         "workload": f"Poisson job arrivals, job size lognormal(median 1e5, sigma 1.5) in [1e3, 5e6], read length "
                     f"U(75,250), half single-end half pairs, 5% from held-out species; {n_held} held-out species "
-                    f"genomes inserted live in 2 extensions; database {w.name}",
-        "seconds": dur, "offered_jobs_s": round(rate_jobs, 2), "offered_mreads_s": round(rate_q / 1e6, 3),
-        "jobs": int(st["jobs_done"]), "queries": int(st["queries_done"]),
-        "throughput_mreads_s": round(st["queries_done"] / max(st["busy_s"], 1e-9) / 1e6, 3),
-        "wall_s": round(wall, 2), "p50_latency_s": round(st["p50_latency_s"], 4),
-        "p99_latency_s": round(st["p99_latency_s"], 4), "max_latency_s": round(st["max_latency_s"], 4),
-        "launch_sets": int(st["launch_sets"]), "gpu_launches": int(launches), "extensions": int(st["extensions"]),
-        "hbm_peak_bytes": int(st["hbm_peak"]), "hbm_limit_bytes": int(st["hbm_limit"]),
-        "final_epoch_jobs_identical_alone": bool(same), "pool_jobs": len(jobs), "generation_s": round(gen_s, 1),
-        "plain_one_job_per_launch": {
-            "seconds_of_arrivals": plain_dur, "jobs": len(lat), "queries": int(q_done),
-            "throughput_mreads_s": round(q_done / plain_wall / 1e6, 3),
-            "p50_latency_s": round(float(lat[len(lat) // 2]), 4),
-            "p99_latency_s": round(float(lat[min(len(lat) - 1, int(0.99 * (len(lat) - 1) + 0.5))]), 4),
-        },
+                    f"genomes inserted live in 2 extensions per run; database {w.name}",
+        "seconds_per_load": dur, "base_rate_mreads_s": round(base_rate, 3),
+        "base_rate_source": "batched graph_tuned throughput" if batched_rate_mreads_s else "fixed 50 Mreads/s",
+        "curve": curve, "saturation_mreads_s": {"served": sat_served, "plain_one_job_per_launch": sat_plain},
+        "pool_jobs": len(jobs), "generation_s": round(gen_s, 1),
     }
 
 

@@ -148,8 +148,8 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
  * mc_classify.  Synchronises the database stream.  MC_ERR_OOM if the sort
  * buffers cannot be allocated: nothing has changed and the call can be
  * repeated.  A failure after the sort has run (MC_ERR_OOM for the layout
- * buffers, MC_ERR_CUDA on a CUDA error, including a sort whose tiles
- * waited more than 2 s for earlier tiles' counts) keeps the previous
+ * buffers, MC_ERR_CUDA on a CUDA error, MC_ERR_TIMEOUT for a sort whose
+ * tiles waited more than 2 s for earlier tiles' counts) keeps the previous
  * layout published for mc_classify, and later mc_db_add_targets and
  * mc_db_finalize calls return MC_ERR_STATE. */
 int mc_db_finalize(mc_db* db);
@@ -173,14 +173,19 @@ int mc_db_finalize(mc_db* db);
  * Asynchronous: returns after enqueueing.  The call waits (on the device)
  * for the last mc_db_finalize.  Device-detected errors of a call are
  * reported by mc_classify_status.  The database must not be changed while
- * calls are in flight. */
+ * calls are in flight.
+ * Reads of seq are made in whole 16-byte aligned chunks: the bytes of a
+ * query's chunks that lie before its first or after its last base (at most
+ * 15 on each side, never outside those aligned chunks) are read and
+ * ignored. */
 int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                 const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                 uint32_t* hits, uint32_t* top_target, void* stream);
 
 /* Allocation-free classification (this library's addition; the paper has
- * no counterpart).  Same arguments, results and asynchronous behaviour as
- * mc_classify, for callers that cannot allocate device memory during the
+ * no counterpart).  Same arguments, results, launch shape (the database's
+ * tuning, mc_db_set_tuning) and asynchronous behaviour as mc_classify, for
+ * callers that cannot allocate device memory during the
  * call -- for example a server whose GPU memory is entirely reserved by
  * another allocator, or a latency-critical loop that must avoid the
  * allocation path.  mc_classify takes its per-call scratch from the
@@ -191,7 +196,9 @@ int mc_classify(const mc_db* db, const mc_classify_params* params, uint32_t n_se
  *    MC_ERR_CAPACITY (split the batch).
  *  - The first call on each device looks up the device address of the
  *    scratch array (cudaGetSymbolAddress, with that device current); make
- *    that first call before any stream capture.
+ *    that first call before any stream capture.  The address is kept for
+ *    the life of the process: resetting the device (cudaDeviceReset) after
+ *    that first call is not supported.
  *  - All calls on a device share the one scratch array: calls whose work
  *    overlaps on the GPU (other streams, other threads) race and corrupt
  *    each other.  Serialise them, e.g. on one stream.
@@ -476,19 +483,6 @@ int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,
                       void* stream);
 
-/* Random-access read bandwidth of the current device (the roofline of the
- * feature-table probes and bucket gathers, which read 16-32 bytes at
- * random positions): n_reads reads of `width` bytes (16 or 32, aligned) at
- * uniformly random positions of a fresh device buffer of buf_bytes
- * (>= 1 MiB; take it much larger than L2), 8 reads in flight per thread,
- * at 16, 32 and 64 warps per SM and two index generators, each timed with
- * CUDA events after a warm-up launch.  *gbs receives the best
- * width x reads / time in GB/s (more requests in flight can lower random
- * DRAM throughput, so the best shape is the roofline).  The buffer comes from
- * cudaMallocAsync on `stream` and is freed before the call returns
- * (synchronises `stream`).  Not part of the method: a measurement aid. */
-int mc_measure_random_read(uint64_t buf_bytes, uint32_t width, uint64_t n_reads, void* stream, double* gbs);
-
 /* ---------------------------------------------------------------------
  * Tracing and launch accounting (no counterpart in the paper beyond its
  * per-stage breakdown, Section 6.4).
@@ -506,6 +500,19 @@ int mc_trace_report(char* buf, size_t len, int reset);
 
 /* Number of kernel launches the library has issued in this process. */
 uint64_t mc_kernel_launches(void);
+
+/* Test export: arms a one-shot stall of the next database sort in this
+ * process (any database), to exercise the bounded wait of its single-pass
+ * radix sort (decoupled look-back: each tile of 4,096 pairs waits for the
+ * digit counts of the tiles before it).  The last of the sort's four passes
+ * then skips its first tile, whose counts are therefore never published;
+ * the next tile's wait gives up after limit_ns (1e6..2e9) and the
+ * mc_db_finalize that ran the sort fails with MC_ERR_TIMEOUT, keeping the
+ * previous layout published (as documented there).  Every write of the
+ * disturbed pass stays inside its buffer.  If the last pass has fewer than
+ * two tiles the stall is dropped and the sort runs normally.  MC_ERR_ARG
+ * for a limit outside the range. */
+int mc_debug_stall_next_sort(uint64_t limit_ns);
 
 /* Message of the last error on the calling thread ("" if none). */
 const char* mc_last_error_string(void);

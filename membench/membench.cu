@@ -1,13 +1,21 @@
-// Random-access read bandwidth of the device (the roofline of the feature
-// table probes and bucket gathers of classification): every thread reads
-// items of `width` bytes (16 or 32, aligned) at uniformly random positions
-// of a buffer much larger than L2, several reads in flight, and folds them
-// into one word so that no read can be dropped.
+// Random-access read bandwidth of the device: the roofline of the feature
+// table probes and bucket gathers of classification, which read 16-32 bytes
+// at random positions.  Every thread reads items of `width` bytes (16 or 32,
+// aligned) at uniformly random positions of a buffer much larger than L2,
+// several reads in flight, and folds them into one word so that no read can
+// be dropped.
+//
+// A measurement aid of the benchmark, built into its own library
+// (libmembench.so); it is not part of the classification library's ABI.
 #include <algorithm>
-
-#include "mc_internal.h"
+#include <cstdint>
+#include <cstdio>
+#include <cuda_runtime.h>
 
 namespace {
+
+thread_local char g_err[256] = "";
+constexpr int NUM_SMS_HINT = 152;
 
 __device__ __forceinline__ uint64_t mix64(uint64_t x) {
     // splitmix64 finaliser (Steele, Lea, Flood 2014)
@@ -47,12 +55,26 @@ __global__ void __launch_bounds__(MB_THREADS) k_random_read(const uint4* __restr
 
 }  // namespace
 
-extern "C" int mc_measure_random_read(uint64_t buf_bytes, uint32_t width, uint64_t n_reads, void* stream,
-                                      double* gbs) {
-    if (!gbs || (width != 16 && width != 32) || buf_bytes < (1u << 20) || n_reads == 0)
-        return mc::report_error(MC_ERR_ARG, "mc_measure_random_read: width 16 or 32, buffer >= 1 MiB, reads > 0");
+// Message of the last failed call on this thread.
+extern "C" const char* membench_last_error(void) { return g_err; }
+
+// n_reads reads of `width` bytes (16 or 32) at uniformly random positions of
+// a fresh device buffer of buf_bytes (>= 1 MiB; take it much larger than
+// L2), 8 reads in flight per thread, at 16, 32 and 64 warps per SM and two
+// index generators, each timed with CUDA events after a warm-up launch.
+// *gbs receives the best width x reads / time in GB/s (more requests in
+// flight can lower random DRAM throughput, so the best shape is the
+// roofline).  The buffer comes from cudaMallocAsync on `stream` and is freed
+// before the call returns (synchronises `stream`).  Returns 0, 1 for a bad
+// argument, 6 for a CUDA error (message: membench_last_error).
+extern "C" int membench_random_read(uint64_t buf_bytes, uint32_t width, uint64_t n_reads, void* stream,
+                                    double* gbs) {
+    if (!gbs || (width != 16 && width != 32) || buf_bytes < (1u << 20) || n_reads == 0) {
+        snprintf(g_err, sizeof g_err, "membench_random_read: width 16 or 32, buffer >= 1 MiB, reads > 0");
+        return 1;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    int dev = 0, sms = mc::NUM_SMS_HINT;
+    int dev = 0, sms = NUM_SMS_HINT;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint64_t max_threads = (uint64_t)sms * 64 * 32;
@@ -94,8 +116,9 @@ extern "C" int mc_measure_random_read(uint64_t buf_bytes, uint32_t width, uint64
     if (b) cudaEventDestroy(b);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return mc::report_error(MC_ERR_CUDA, "mc_measure_random_read: %s", cudaGetErrorString(e));
+        snprintf(g_err, sizeof g_err, "membench_random_read: %s", cudaGetErrorString(e));
+        return 6;
     }
     *gbs = best;
-    return MC_OK;
+    return 0;
 }

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB = os.path.join(HERE, "libmc.so")
 BUILD_DIR = os.path.join(HERE, "_build")
-SOURCES = ["mc_api.cu", "mc_build.cu", "mc_classify.cu", "mc_noalloc.cu", "mc_server.cpp", "mc_membench.cu"]
+SOURCES = ["mc_api.cu", "mc_build.cu", "mc_classify.cu", "mc_noalloc.cu", "mc_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

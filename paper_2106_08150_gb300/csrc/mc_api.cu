@@ -30,6 +30,7 @@ int fail(int code, const char* fmt, ...) {
 int cuda_fail(cudaError_t e, const char* what) {
     cudaGetLastError();  // clear sticky-free errors
     if (e == cudaErrorMemoryAllocation) return fail(MC_ERR_OOM, "%s: out of device memory", what);
+    if (e == cudaErrorTimeout) return fail(MC_ERR_TIMEOUT, "%s: a bounded device wait gave up", what);
     return fail(MC_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
@@ -640,6 +641,8 @@ int classify_prepare(const mc_db* db, const mc_classify_params* params, const ch
     return MC_OK;
 }
 
+Tuning db_tuning(const mc_db* db) { return db->tuning; }
+
 int classify_done(const mc_db* db, cudaStream_t stream) {
     cudaError_t e = note_use(db, stream);
     if (e != cudaSuccess) {
@@ -664,6 +667,14 @@ int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters, void* stream) {
     return classify_impl(db, params, n_seq, seq, offs, n_queries, qoffs, label, hits, top_target, cands, counters,
                          stream);
+}
+
+int mc_debug_stall_next_sort(uint64_t limit_ns) {
+    g_err[0] = 0;
+    if (limit_ns < 1000000ull || limit_ns > 2000000000ull)
+        return fail(MC_ERR_ARG, "mc_debug_stall_next_sort: limit must be in 1e6..2e9 ns");
+    mc::arm_sort_stall(limit_ns);
+    return MC_OK;
 }
 
 int mc_classify_status(const mc_db* db, void* stream) {

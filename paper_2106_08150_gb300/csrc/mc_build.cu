@@ -20,6 +20,7 @@
 //      slot(k-1)+1) = k + max_{k'<=k}(home(k') - k'), a max-scan.
 // Every step reads and writes HBM in coalesced streams; the only random
 // accesses of the whole database life are the lookups of the query path.
+#include <atomic>
 #include <cstdio>
 
 #include "mc_internal.h"
@@ -389,7 +390,7 @@ template <bool FILTER>
 __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
     k_radix_pass(const uint64_t* __restrict__ in, uint64_t* __restrict__ out, uint64_t n, uint32_t pass,
                  const unsigned long long* __restrict__ totals, uint64_t* status, uint32_t* tile_ctr,
-                 uint64_t n_tiles, uint32_t* err) {
+                 uint64_t n_tiles, uint64_t limit_ns, uint32_t* err) {
     __shared__ uint32_t wc[NWARP][257];       // per-warp digit counts, then tile offsets
     __shared__ uint32_t peer_mask[2][NWARP][257];
     __shared__ uint64_t gdelta[256];          // global position of a digit's run minus its tile offset
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
                     const uint64_t now = globaltimer_ns();
                     if (t0 == 0) {
                         t0 = now;
-                    } else if (now - t0 > LOOKBACK_LIMIT_NS) {
+                    } else if (now - t0 > limit_ns) {
                         atomicMax(err, 1u);
                         break;
                     }
@@ -510,10 +511,22 @@ __global__ void __launch_bounds__(BT, RS_BLOCKS_PER_SM)
         tile = s_tile;
     }
 }
+// One-shot stall of the next sort's last pass (mc_debug_stall_next_sort):
+// the wait limit of that pass in ns, 0 = not armed.
+std::atomic<uint64_t> g_stall_limit_ns{0};
 }  // namespace
+
+void arm_sort_stall(uint64_t limit_ns) { g_stall_limit_ns.store(limit_ns); }
 
 cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_total, uint64_t n_real, cudaStream_t s) {
     if (n_total == 0) return cudaSuccess;
+    // An armed stall makes the last pass start at tile 1: tile 0's counts are
+    // never published, so tile 1's look-back wait gives up after the armed
+    // limit.  Every look-back sum stays a sum over a subset of earlier tiles'
+    // counts, so every write stays inside the pass's output; only the last
+    // pass is disturbed, because an earlier one would hand the next pass
+    // data whose digits disagree with the digit totals.
+    const uint64_t stall_ns = g_stall_limit_ns.exchange(0);
     const uint64_t max_tiles = (n_total + RS_TILE - 1) / RS_TILE;
     // control block: totals[4][256], tile counters[4], error word
     constexpr size_t CTRL_WORDS = 4 * 256 + 3;
@@ -538,12 +551,20 @@ cudaError_t sort_pairs(const Mem& mem, uint64_t* a, uint64_t* b, uint64_t n_tota
         const uint64_t tiles = (n + RS_TILE - 1) / RS_TILE;
         const uint32_t g = grid_for(tiles, RS_BLOCKS_PER_SM);
         const unsigned long long* tp = totals + 256 * pass;
+        uint64_t limit = LOOKBACK_LIMIT_NS;
+        if (stall_ns && pass == 3 && tiles >= 2) {
+            limit = stall_ns;
+            e = cudaMemsetAsync(tile_ctr + pass, 1, 1, s);  // the counter's low byte: tiles are taken from 1
+            if (e != cudaSuccess) return e;
+        }
         if (pass == 0)
             MC_LAUNCH("radix_pass", s,
-                      k_radix_pass<true><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles, err));
+                      k_radix_pass<true><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles,
+                                                          limit, err));
         else
             MC_LAUNCH("radix_pass", s,
-                      k_radix_pass<false><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles, err));
+                      k_radix_pass<false><<<g, BT, 0, s>>>(src, dst, n, pass, tp, status.ptr, tile_ctr + pass, tiles,
+                                                           limit, err));
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         uint64_t* t = src;

@@ -1031,11 +1031,11 @@ struct ScratchLayout {
     uint32_t chunk;
 };
 
-ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, uint32_t large_warps) {
-    ScratchLayout L;
+constexpr ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, uint32_t large_warps) {
+    ScratchLayout L{};
     const size_t list_cap = (size_t)WIN_A * sketch_size;
     const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
-    L.chunk = std::min(n_q_cap, CHUNK);
+    L.chunk = n_q_cap < CHUNK ? n_q_cap : CHUNK;
     L.ovf = 0;
     L.meta = align256(L.ovf + ((size_t)n_q_cap + 8) * 4);
     L.mid = align256(L.meta + (size_t)L.chunk * sizeof(uint4));
@@ -1170,17 +1170,22 @@ cudaError_t classify_launch(const Mem& mem, const ClassifyDb& db, const Classify
 
 // Number of large-path warps of the allocation-free launch.
 constexpr uint32_t NOALLOC_LARGE_WARPS = 8;
+// The documented per-call maximum of the allocation-free entry point must
+// fit its fixed scratch array at the largest sketch size.
+static_assert(scratch_layout(MC_NOALLOC_MAX_QUERIES, MC_MAX_SKETCH, NOALLOC_LARGE_WARPS).total <=
+                  MC_NOALLOC_SCRATCH_BYTES,
+              "MC_NOALLOC_MAX_QUERIES queries at MC_MAX_SKETCH do not fit MC_NOALLOC_SCRATCH_BYTES");
 
 size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size) {
     return classify_scratch_bytes(n_q, sketch_size, NOALLOC_LARGE_WARPS);
 }
 
-cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, unsigned char* scratch,
-                                   size_t scratch_len, cudaStream_t s) {
+cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& Q, const Tuning& t,
+                                   unsigned char* scratch, size_t scratch_len, cudaStream_t s) {
     if (Q.n_q == 0) return cudaSuccess;
     if (classify_noalloc_bytes(Q.n_q, db.sp.s) > scratch_len) return cudaErrorInvalidValue;
     const ClassifyScratch sc = classify_scratch_carve(scratch, Q.n_q, db.sp.s, NOALLOC_LARGE_WARPS);
-    return classify_enqueue(db, Q, DEFAULT_TUNING, sc, s, nullptr);
+    return classify_enqueue(db, Q, t, sc, s, nullptr);
 }
 
 cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc, uint32_t reps,

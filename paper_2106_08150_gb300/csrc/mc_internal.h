@@ -87,6 +87,12 @@ cudaError_t emit_pairs(const SketchParams& p, uint32_t n_targets, const uint8_t*
 // wait for earlier tiles' counts gave up (the order is then wrong).
 cudaError_t sort_pairs(const Mem& mem, uint64_t* in, uint64_t* tmp, uint64_t n_total, uint64_t n_real,
                        cudaStream_t s);
+// Arms a one-shot stall of the next sort_pairs call's last pass (a test of
+// the bounded look-back wait): that pass skips its tile 0, so tile 1 waits
+// for counts that are never published and gives up after limit_ns; the sort
+// then returns cudaErrorTimeout.  Dropped (the sort runs normally) when the
+// last pass has fewer than two tiles.
+void arm_sort_stall(uint64_t limit_ns);
 
 struct FinalizeOut {
     uint64_t n_keys = 0;
@@ -223,8 +229,8 @@ constexpr uint32_t CLASSIFY_CHUNK = 1u << 20;  // queries per lookup/score round
 // of `scratch` (scratch_len bytes, 256-byte aligned).  classify_noalloc_bytes
 // is the size a call with n_q queries needs.
 size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size);
-cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& q, unsigned char* scratch,
-                                   size_t scratch_len, cudaStream_t s);
+cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& q, const Tuning& t,
+                                   unsigned char* scratch, size_t scratch_len, cudaStream_t s);
 
 // ------------------------------------------------------------- mc_api.cu
 // Records an error message for mc_last_error_string and returns `code`.
@@ -237,5 +243,7 @@ int classify_prepare(const mc_db* db, const mc_classify_params* params, const ch
 // Records that classify work on `stream` reads the database's current
 // layout (a later finalize frees that layout only after this work).
 int classify_done(const mc_db* db, cudaStream_t stream);
+// The launch shape later classify calls of the database use (mc_db_set_tuning).
+Tuning db_tuning(const mc_db* db);
 
 }  // namespace mc

@@ -26,7 +26,9 @@ void* g_scratch_addr[MAX_DEVICES] = {};
 // Device address of the scratch array on the current device, looked up once
 // per device (with that device current) and cached.  In host code the
 // array's name is only a host-side stand-in, so kernels must get this
-// address instead.
+// address instead.  The cache is never invalidated: the address stays valid
+// for the life of the device's primary context (a cudaDeviceReset after the
+// first call is not supported).
 int scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -69,7 +71,7 @@ extern "C" int mc_classify_noalloc(const mc_db* db, const mc_classify_params* pa
     void* scratch = nullptr;
     rc = scratch_address(&scratch);
     if (rc != MC_OK) return rc;
-    cudaError_t e = mc::classify_launch_noalloc(cdb, q, static_cast<unsigned char*>(scratch),
+    cudaError_t e = mc::classify_launch_noalloc(cdb, q, mc::db_tuning(db), static_cast<unsigned char*>(scratch),
                                                 MC_NOALLOC_SCRATCH_BYTES, s);
     if (e != cudaSuccess) {
         cudaGetLastError();

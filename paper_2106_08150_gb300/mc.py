@@ -142,7 +142,7 @@ _SIGS = {
     "mc_server_drain": ([_vp, ctypes.c_double], _i),
     "mc_server_stats_get": ([_vp, ctypes.POINTER(mc_server_stats)], _i),
     "mc_server_free": ([_vp], None),
-    "mc_measure_random_read": ([_u64, _u32, _u64, _vp, ctypes.POINTER(ctypes.c_double)], _i),
+    "mc_debug_stall_next_sort": ([_u64], _i),
     "mc_trace_enable": ([_i], _i),
     "mc_trace_report": ([ctypes.c_char_p, ctypes.c_size_t, _i], _i),
     "mc_kernel_launches": ([], _u64),
@@ -444,11 +444,10 @@ class Server:
             self._keep.clear()
 
 
-def mc_measure_random_read(buf_bytes: int, width: int, n_reads: int, stream=None) -> float:
-    """GB/s of `width`-byte reads at random positions of a buf_bytes buffer."""
-    v = ctypes.c_double()
-    _check(_lib.mc_measure_random_read(buf_bytes, width, n_reads, _stream(stream), ctypes.byref(v)))
-    return v.value
+def mc_debug_stall_next_sort(limit_ns: int):
+    """Test export: the next database sort's last pass skips its first tile,
+    so its bounded look-back wait gives up after limit_ns (MC_ERR_TIMEOUT)."""
+    _check(_lib.mc_debug_stall_next_sort(limit_ns))
 
 
 def mc_trace_enable(on: bool = True):

@@ -4,8 +4,12 @@ can be repeated and gives the same database as an undisturbed build; a
 failure after the sort keeps the previously published layout serving
 classification and refuses further growth with MC_ERR_STATE.
 
-The failures come from a device memory provider that refuses one chosen
-allocation (host side; no kernel is disturbed)."""
+The allocation failures come from a device memory provider that refuses one
+chosen allocation (host side; no kernel is disturbed).  The sort's bounded
+wait is made to run out by a test export that makes the last radix pass
+skip its first tile, whose counts the next tile then waits for in vain: the
+wait gives up after its limit, the kernel records the timeout in a status
+word and returns, and the host reports MC_ERR_TIMEOUT (no fault, no hang)."""
 import ctypes
 
 import numpy as np
@@ -122,3 +126,45 @@ def test_failure_after_the_sort_keeps_the_published_layout(env):
             assert (x == y).all()
     finally:
         db.free()
+
+
+def test_sort_wait_that_runs_out_keeps_the_published_layout(env):
+    mc, w, prov = env
+    prov.arm(None)
+    n = len(w.goffs) - 1
+    half = n // 2
+    ref = gpu_build(mc, w.genomes[: int(w.goffs[half])], w.goffs[: half + 1], w.parent, w.taxon_of_target[:half],
+                    **w.db_params)
+    want = _classify(mc, ref, w)
+    ref.free()
+
+    with pytest.raises(mc.McError) as e:
+        mc.mc_debug_stall_next_sort(10)  # below the allowed range
+    assert e.value.code == mc.MC_ERR_ARG
+    db = mc.Database.create(w.parent, **w.db_params)
+    try:
+        _add(mc, db, w, 0, half)
+        db.finalize()
+        _add(mc, db, w, half, n)
+        mc.mc_debug_stall_next_sort(50_000_000)  # 50 ms
+        with pytest.raises(mc.McError) as e:
+            db.finalize()
+        assert e.value.code == mc.MC_ERR_TIMEOUT
+        with pytest.raises(mc.McError) as e:
+            db.finalize()
+        assert e.value.code == mc.MC_ERR_STATE
+        with pytest.raises(mc.McError) as e:
+            _add(mc, db, w, 0, 1)
+        assert e.value.code == mc.MC_ERR_STATE
+        for x, y in zip(_classify(mc, db, w), want):
+            assert (x == y).all()
+    finally:
+        db.free()
+    # the stall is one-shot: the next build is undisturbed
+    again = gpu_build(mc, w.genomes[: int(w.goffs[half])], w.goffs[: half + 1], w.parent, w.taxon_of_target[:half],
+                      **w.db_params)
+    try:
+        for x, y in zip(_classify(mc, again, w), want):
+            assert (x == y).all()
+    finally:
+        again.free()

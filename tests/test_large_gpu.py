@@ -1,9 +1,15 @@
 """The large-database recipe: genera of bacterial-like genomes plus
 repeat-rich eukaryote-like genomes whose repeated segments overfill buckets
 (bucket cap, overflow counts).  A reduced instance is checked against the
-oracle in full; the scaled instance (about 15 Gbp) is built at full size and
-checked on a key range against buckets recomputed on the host from the
-sketches of all windows."""
+oracle in full.  The full-size instance (10,000 genomes, about 14.3 Gbp,
+50M read pairs) is built and classified in the launch configuration
+bench.py times, and checked against the oracle on sampled outputs: the
+oracle builds the buckets of every feature of 2,000 sampled queries (a
+quarter of them from the repeat-rich genomes) plus every feature of one key
+range, which are then complete, so the dump of that key range and the
+labels, hit counts and top targets of the sampled queries must be equal."""
+import os
+
 import numpy as np
 import pytest
 
@@ -46,58 +52,78 @@ def test_repeat_rich_database_and_classification_match_oracle(mc):
         db.free()
 
 
-def test_scaled_large_database_key_range(mc):
-    """Full-size build of the scaled recipe; the buckets of one key range
-    must equal those recomputed on the host from every window's sketch
-    (sorted locations, the cap smallest kept)."""
+def _sub_queries(w, qs):
+    """Reads, read offsets and query offsets of the queries qs of w."""
+    sub_reads, sub_roffs, sub_qoffs = [], [0], [0]
+    for q in qs:
+        a, b = int(w.qoffs[q]), int(w.qoffs[q + 1])
+        for i in range(a, b):
+            sub_reads.append(w.reads[int(w.roffs[i]):int(w.roffs[i + 1])])
+            sub_roffs.append(sub_roffs[-1] + int(w.roffs[i + 1] - w.roffs[i]))
+        sub_qoffs.append(sub_qoffs[-1] + (b - a))
+    return (np.concatenate(sub_reads), np.array(sub_roffs, dtype=np.uint64), np.array(sub_qoffs, dtype=np.uint32))
+
+
+def test_fullsize_large_database_matches_oracle_on_samples(mc):
     import torch
-    w = synth.large_workload(seed=1002, scaled=True, n_pairs=1000)
+    w = synth.large_workload(seed=1002, scaled=True)
     p = w.db_params
-    d_g, d_o = dev(w.genomes), dev(w.goffs)
+    n_threads = os.cpu_count() or 1
     db = mc.Database.create(w.parent, **p)
     try:
-        db.add_targets(d_g, d_o, w.taxon_of_target)
+        db.add_targets(dev(w.genomes), dev(w.goffs), w.taxon_of_target)
         db.finalize()
         st = db.stats()
         lens = np.diff(w.goffs).astype(np.int64)
         k, stride = p["k"], p["window_stride"]
-        nw = np.where(lens >= k, (lens - k + stride) // stride, 0)
-        assert st["n_windows"] == int(nw.sum())
+        assert st["n_windows"] == int(np.where(lens >= k, (lens - k + stride) // stride, 0).sum())
         assert st["overflow_keys"] > 0 and st["n_locations"] + st["dropped_locations"] == st["n_pairs"]
         assert 0 < st["load_factor"] <= 0.5
-        # sketches of all windows, selected on the device for one key range
+
+        # every pair classified in one call, with the autotuner's launch shape (as the bench does)
+        nq = w.n_queries
+        label = torch.empty(nq, dtype=torch.int32, device="cuda")
+        hits = torch.empty(nq, dtype=torch.int32, device="cuda")
+        top = torch.empty(nq, dtype=torch.int32, device="cuda")
+        cp = mc.classify_params(**w.cls_params)
+        d_reads, d_roffs, d_qoffs = dev(w.reads), dev(w.roffs), dev(w.qoffs)
+        n_s = 1 << 20
+        tuned, _ = mc.mc_autotune(db.handle, cp, [mc.batch(int(w.qoffs[n_s]), d_reads, d_roffs, d_qoffs[: n_s + 1],
+                                                           label, hits, top)], reps=1)
+        mc.mc_db_set_tuning(db.handle, tuned)
+        mc.mc_classify(db.handle, cp, w.n_seq, d_reads, d_roffs, nq, d_qoffs, label, hits, top)
+        mc.mc_classify_status(db.handle)
+        g_label, g_hits, g_top = host_u32(label), host_u32(hits), host_u32(top)
+        del d_reads, d_roffs, d_qoffs, label, hits, top
+
+        # sampled queries: uniform ones plus queries from the repeat-rich genomes
+        rng = np.random.default_rng(11)
+        n_bact = len(w.taxon_of_target) - 200
+        euk = np.nonzero((w.truth >= n_bact) & (w.truth != synth.NO_GENOME))[0]
+        qs = np.unique(np.concatenate([rng.choice(nq, size=1500, replace=False),
+                                       rng.choice(euk, size=500, replace=False)]))
+        sub_reads, sub_roffs, sub_qoffs = _sub_queries(w, qs)
+        _, sk, cnt = oracle.sketch(sub_reads, sub_roffs, **p)
+        feats = np.unique(np.concatenate([sk[i][:cnt[i]] for i in range(len(cnt))]))
         lo, hi = 0, (1 << 32) // 4096
-        n_seq = len(w.goffs) - 1
-        prm = mc.db_params(**p)
-        win = torch.zeros(n_seq + 1, dtype=torch.int64, device="cuda")
-        mc.mc_window_offsets(prm, n_seq, d_o, win)
-        n_win = int(win[-1].item())
-        s = p["sketch_size"]
-        sk = torch.zeros(n_win * s, dtype=torch.int32, device="cuda")
-        cnt = torch.zeros(n_win, dtype=torch.int32, device="cuda")
-        mc.mc_sketch(prm, n_seq, d_g, d_o, win, n_win, sk, cnt)
-        torch.cuda.synchronize()
-        pos = torch.arange(s, device="cuda").repeat(n_win)
-        valid = pos < cnt.repeat_interleave(s)
-        u = sk.to(torch.int64) & 0xFFFFFFFF
-        sel = valid & (u >= lo) & (u < hi)
-        idx = torch.nonzero(sel).squeeze(1)
-        feats = u[idx].cpu().numpy().astype(np.uint32)
-        gwin = (idx // s).cpu().numpy().astype(np.int64)
-        del sk, cnt, u, sel, idx, pos, valid
-        wb = win.cpu().numpy().astype(np.int64)
-        tgt = np.searchsorted(wb, gwin, side="right") - 1
-        loc = (tgt.astype(np.uint64) << np.uint64(32)) | (gwin - wb[tgt]).astype(np.uint64)
-        order = np.lexsort((loc, feats))
-        feats, loc = feats[order], loc[order]
-        keys, first, counts = np.unique(feats, return_index=True, return_counts=True)
-        cap = p["bucket_cap"]
-        keep = np.concatenate([np.arange(f, f + min(c, cap)) for f, c in zip(first, counts)])
+        keys = np.unique(np.concatenate([feats, np.arange(lo, hi, dtype=np.uint32)]))
+        odb = oracle.DB(w.genomes, w.goffs, key_filter=keys, n_threads=n_threads, **p)
+        ost = odb.stats()
+        assert st["n_pairs"] == ost["n_pairs"] and st["n_windows"] == ost["n_windows"]
+
+        # database dump of the key range, including overflowing buckets
         gk, gc, gl = db.dump(lo, hi)
-        assert len(gk) == len(keys) > 1000
-        assert (gk == keys).all()
-        assert (gc == np.minimum(counts, cap)).all()
-        assert (gl == loc[keep]).all()
-        assert (counts > cap).any()
+        ok, oc, ol = odb.dump(lo, hi)
+        assert len(gk) == len(ok) > 1000
+        assert (gk == ok).all() and (gc == oc).all() and (gl == ol).all()
+        assert (gc == p["bucket_cap"]).any()
+
+        # classification of the sampled queries
+        ol_, oh_, ot_ = odb.classify(w.parent, w.taxon_of_target, sub_reads, sub_roffs, sub_qoffs,
+                                     n_threads=n_threads, **w.cls_params)
+        assert (g_hits[qs] == oh_).all()
+        assert (g_top[qs] == ot_).all()
+        assert (g_label[qs] == ol_).all()
+        assert (g_label[qs] != oracle.NO_TAXON).mean() > 0.8
     finally:
         db.free()
