@@ -50,9 +50,10 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["large", "mid", "small", "tiny"], default="large",
+    ap.add_argument("--workload", choices=["large", "mid", "large_small", "small", "tiny"], default="large",
                     help="large = 10,000 genomes (~14.3 Gbp, repeat-rich) / 50M pairs (the measured configuration); "
-                         "mid = 1,000 genomes / 10M pairs; small/tiny for profiling")
+                         "mid = 1,000 genomes / 10M pairs; large_small (the large recipe at 1/10: ~1.4 Gbp, 2M "
+                         "pairs), small and tiny for profiling")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-genera", type=int, default=2)
@@ -73,6 +74,9 @@ def make_workload(name: str, rank: int):
     import synth
     if name == "large":
         w = synth.large_workload(seed=1002, scaled=True, held_genera=5, held_per_genus=10)
+    elif name == "large_small":
+        w = synth.large_workload(seed=1002, scaled=True, n_families=10, n_euk=20, n_pairs=2_000_000, held_genera=1,
+                                 held_per_genus=10)
     elif name == "mid":
         w = synth.mid_workload(seed=1001)
     elif name == "small":

@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define MC_API_VERSION 1
+#define MC_API_VERSION 2
 
 /* Status codes returned by every entry point. */
 typedef enum mc_status {
@@ -235,20 +235,31 @@ typedef struct mc_batch {
 
 /* Launch shape of the classification kernels.  Every setting gives the same
  * results; only the speed differs.  Zero fields take the defaults.
- *  hist_slots  : shared-memory histogram slots per query (the on-chip tile
- *                that replaces the paper's sort tile): 256, 512 (default)
- *                or 1024.  Queries whose distinct locations do not fit go
- *                to the large path.
+ *  score_mode  : how a query's gathered locations are counted and scored
+ *                (the paper's segmented sort, Section 5.5, and window
+ *                scoring, Section 5.6): 1 = sort path (default): one warp
+ *                gathers the query's locations into registers and sorts
+ *                them; 2 = hash path: per-warp hash histogram in shared
+ *                memory.  The sort path needs 32-bit locations (mc_db_stats
+ *                loc_bytes == 4) and histogram keys of that width
+ *                (wide_keys 0); otherwise the hash path is used.
+ *  sort_max    : sort path: largest number of gathered locations a query
+ *                may have to be sorted, 256, 512 or 1024 (default); each
+ *                size class up to it has its own kernel; larger queries go
+ *                to the hash path's medium and large kernels.
+ *  hist_slots  : hash path: shared-memory histogram slots per query: 256,
+ *                512 (default) or 1024.  Queries whose distinct locations
+ *                do not fit go to the medium (2,048 slots) and large paths.
  *  probe_batch : feature-table probes in flight per lane (32 lanes probe
  *                together): 2, 4 (default) or 8.
- *  gather_batch: bucket-location loads in flight per lane: 4, 8 (default)
- *                or 16.
+ *  gather_batch: hash path: bucket-location loads in flight per lane: 4, 8
+ *                (default) or 16.
  *  lookup_warps: warps per CTA of the lookup kernel: 4 or 8 (default).
- *  score_warps : warps per CTA of the score kernel: 2 or 4 (default).
+ *  score_warps : warps per CTA of the hash path's score kernel: 2 or 4 (default).
  *  wide_keys   : 0 (default) = the shared-memory histograms key a location
  *                by 32 bits (target << b | window) when every target and
  *                window id of the database fits 32 bits, else by 64; 1 =
- *                always 64-bit keys.
+ *                always 64-bit keys (hash path).
  * One warp carries one query in every kernel. */
 typedef struct mc_tuning {
     uint32_t hist_slots;
@@ -257,6 +268,8 @@ typedef struct mc_tuning {
     uint32_t lookup_warps;
     uint32_t score_warps;
     uint32_t wide_keys;
+    uint32_t score_mode;
+    uint32_t sort_max;
 } mc_tuning;
 
 /* Sets the launch shape used by later classify calls on this database that
@@ -289,8 +302,10 @@ int mc_plan_kernels(const mc_plan* plan);  /* kernel launches per run (graph ker
 void mc_plan_free(mc_plan* plan);
 
 /* Autotuner: times every lookup setting (probe_batch x lookup_warps) and
- * every score setting (hist_slots x gather_batch x score_warps, with the
- * large path it leaves) on the given sample batches (at most 2^20 queries
+ * every score setting (the hash path's hist_slots x gather_batch x
+ * score_warps, and, for databases with 32-bit locations, the sort path's
+ * sort_max, each with the medium and large paths it leaves) on the given
+ * sample batches (at most 2^20 queries
  * in total), `reps` times each, and writes the fastest setting to *best.
  * If `times` is not NULL it receives up to max_times records
  * {setting, kernel ms (mean over reps)} in the order tried; *n_times (if
@@ -435,12 +450,15 @@ typedef struct mc_db_stats_t {
                                    live extension: counted over the kept locations of the
                                    earlier targets plus those of the new ones) */
     uint64_t dropped_locations; /* n_pairs - n_locations */
-    uint64_t table_slots;       /* slots of the feature table */
+    uint64_t table_slots;       /* slots of the feature table (8 bytes each) */
     uint64_t max_probe;         /* longest probe distance in the feature table */
     uint64_t device_bytes;      /* bytes held on the device */
     double load_factor;         /* n_keys / table_slots */
     uint32_t finalized;         /* 1 if no additions are pending */
     uint32_t max_depth;         /* deepest taxonomy level */
+    uint32_t loc_bytes;         /* bytes per stored location: 4 when every (target, window)
+                                   fits 32 bits as target << b | window, else 8 */
+    uint32_t reserved;
 } mc_db_stats_t;
 
 /* Fills *out (host) with the database's counters (no synchronisation). */

@@ -164,10 +164,12 @@ struct mc_db {
     // additions not yet finalized
     DevBuf pending;  // u64 pairs
     uint64_t pending_n = 0, pending_real = 0;
-    // published condensed layout
+    // published condensed layout: locations in the loc_jbits encoding
+    // (mc::loc_bytes), packed feature-table words in format fmt
     DevBuf locs, table;
     uint64_t n_kept = 0, n_keys = 0, table_len = 0, overflow_keys = 0, n_pairs = 0;
-    uint32_t log_t = 1, max_probe = 0;
+    mc::TableFmt fmt{1, 1};
+    uint32_t max_probe = 0, loc_jbits = 0;
     bool dirty = false, has_table = false;
     // a finalize failed after its sort had consumed the pending pairs: the
     // last published layout still serves classification, but nothing can
@@ -278,10 +280,10 @@ int check_cls(const mc_classify_params* p) {
 // Kernel view of a finalized database.
 mc::ClassifyDb db_view(const mc_db* db) {
     mc::ClassifyDb cdb;
-    cdb.table = (const uint4*)db->table.p;
-    cdb.log_t = db->log_t;
+    cdb.table = (const uint64_t*)db->table.p;
+    cdb.fmt = db->fmt;
     cdb.max_probe = db->max_probe;
-    cdb.locs = (const uint64_t*)db->locs.p;
+    cdb.locs = db->locs.p;
     cdb.taxon_of_target = (const uint32_t*)db->taxon.p;
     cdb.n_targets = db->n_targets;
     cdb.lineage = (const uint32_t*)db->lineage.p;
@@ -289,7 +291,7 @@ mc::ClassifyDb db_view(const mc_db* db) {
     cdb.lin_stride = db->lin_stride;
     cdb.n_taxa = db->n_taxa;
     cdb.sp = db->sp;
-    cdb.jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
+    cdb.jbits = db->loc_jbits;
     return cdb;
 }
 
@@ -509,8 +511,8 @@ int mc_db_finalize(mc_db* db) {
     } else {
         if (!within_budget(db, n_total * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
         if (!grab(db, a, n_total * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
-        cudaError_t e = mc::reconstruct_pairs((const uint4*)db->table.p, db->table_len, (const uint64_t*)db->locs.p,
-                                              (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s);
+        cudaError_t e = mc::reconstruct_pairs((const uint64_t*)db->table.p, db->table_len, db->fmt, db->locs.p,
+                                              db->loc_jbits, (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s);
         if (e == cudaSuccess && db->pending_n)
             e = cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) {
@@ -535,24 +537,31 @@ int mc_db_finalize(mc_db* db) {
     }
     release(db, b);
     mc::FinalizeOut fo;
+    const uint32_t jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
     e = mc::finalize_pairs(db->mem, (const uint64_t*)a.p, n_real, db->cap, (const uint32_t*)db->wbase.p,
-                           db->n_targets, &fo, s);
+                           db->n_targets, jbits, &fo, s);
     release_tmp();
     if (e != cudaSuccess) {
         db->failed = true;
         return cuda_fail(e, "finalize: layout");
     }
+    if (fo.table_full) {
+        db->failed = true;
+        return fail(MC_ERR_TABLE_FULL, "finalize: %llu features and %llu locations fit no feature-table format",
+                    (unsigned long long)fo.n_keys, (unsigned long long)fo.n_kept);
+    }
     release(db, db->pending);
     retire(db, db->locs);
     retire(db, db->table);
-    db->locs = DevBuf{fo.locs, fo.n_kept * 8};
+    db->locs = DevBuf{fo.locs, fo.n_kept * mc::loc_bytes(jbits)};
     db->table = DevBuf{fo.table, fo.table_bytes};
+    db->loc_jbits = jbits;
     db->n_pairs += db->pending_real;
     db->pending_n = db->pending_real = 0;
     db->n_kept = fo.n_kept;
     db->n_keys = fo.n_keys;
     db->table_len = fo.table_len;
-    db->log_t = fo.log_t;
+    db->fmt = fo.fmt;
     db->max_probe = fo.max_probe;
     db->overflow_keys = fo.overflow_keys;
     db->dirty = false;
@@ -709,11 +718,13 @@ void mc_db_free(mc_db* db) {
 
 namespace {
 const char MAGIC[8] = {'M', 'C', 'G', 'B', '3', 'D', 'B', '1'};
-const uint32_t FILE_VERSION = 1;
+const uint32_t FILE_VERSION = 2;
 
+// Format 2: 8-byte feature-table words (log_t, cbits) and locations in the
+// loc_jbits encoding.
 struct FileHeader {
     char magic[8];
-    uint32_t version, k, s, w, stride, cap, n_taxa, n_targets, log_t, max_probe;
+    uint32_t version, k, s, w, stride, cap, n_taxa, n_targets, log_t, max_probe, cbits, loc_jbits;
     uint64_t n_windows, n_pairs, n_keys, n_kept, table_len, overflow_keys;
 };
 
@@ -758,7 +769,9 @@ int mc_db_save(const mc_db* db, const char* path) {
     h.cap = db->cap;
     h.n_taxa = db->n_taxa;
     h.n_targets = db->n_targets;
-    h.log_t = db->log_t;
+    h.log_t = db->fmt.log_t;
+    h.cbits = db->fmt.cbits;
+    h.loc_jbits = db->loc_jbits;
     h.max_probe = db->max_probe;
     h.n_windows = db->n_windows;
     h.n_pairs = db->n_pairs;
@@ -772,8 +785,8 @@ int mc_db_save(const mc_db* db, const char* path) {
         rc = fail(MC_ERR_ARG, "mc_db_save: write failed");
     if (!rc) rc = write_device(f, db->taxon.p, (size_t)db->n_targets * 4, db->stream, stage);
     if (!rc) rc = write_device(f, db->wbase.p, ((size_t)db->n_targets + 1) * 4, db->stream, stage);
-    if (!rc) rc = write_device(f, db->locs.p, db->n_kept * 8, db->stream, stage);
-    if (!rc) rc = write_device(f, db->table.p, db->table_len * sizeof(uint4), db->stream, stage);
+    if (!rc) rc = write_device(f, db->locs.p, db->n_kept * mc::loc_bytes(db->loc_jbits), db->stream, stage);
+    if (!rc) rc = write_device(f, db->table.p, db->table_len * sizeof(uint64_t), db->stream, stage);
     if (fclose(f) != 0 && !rc) rc = fail(MC_ERR_ARG, "mc_db_save: close failed");
     return rc;
 }
@@ -812,8 +825,14 @@ int mc_db_load(const char* path, void* stream, mc_db** out) {
         return rc;
     }
     std::vector<char> stage(64u << 20);
+    if (h.log_t < 1 || h.log_t > 32 || h.cbits != mc::count_bits(h.cap) || h.loc_jbits > 31 || h.max_probe > mc::TAB_MAX_DISP) {
+        fclose(f);
+        mc_db_free(db);
+        return fail(MC_ERR_ARG, "mc_db_load: %s has an invalid table format", path);
+    }
+    const size_t loc_b = mc::loc_bytes(h.loc_jbits);
     if (!grab(db, db->taxon, std::max<size_t>((size_t)h.n_targets * 4, 4)) ||
-        !grab(db, db->locs, h.n_kept * 8) || !grab(db, db->table, h.table_len * sizeof(uint4))) {
+        !grab(db, db->locs, h.n_kept * loc_b) || !grab(db, db->table, h.table_len * sizeof(uint64_t))) {
         fclose(f);
         mc_db_free(db);
         return fail(MC_ERR_OOM, "mc_db_load: allocation failed");
@@ -826,8 +845,8 @@ int mc_db_load(const char* path, void* stream, mc_db** out) {
     }
     rc = read_device(f, db->taxon.p, (size_t)h.n_targets * 4, db->stream, stage);
     if (!rc) rc = read_device(f, db->wbase.p, ((size_t)h.n_targets + 1) * 4, db->stream, stage);
-    if (!rc) rc = read_device(f, db->locs.p, h.n_kept * 8, db->stream, stage);
-    if (!rc) rc = read_device(f, db->table.p, h.table_len * sizeof(uint4), db->stream, stage);
+    if (!rc) rc = read_device(f, db->locs.p, h.n_kept * loc_b, db->stream, stage);
+    if (!rc) rc = read_device(f, db->table.p, h.table_len * sizeof(uint64_t), db->stream, stage);
     fclose(f);
     if (rc) {
         mc_db_free(db);
@@ -839,7 +858,8 @@ int mc_db_load(const char* path, void* stream, mc_db** out) {
     db->n_keys = h.n_keys;
     db->n_kept = h.n_kept;
     db->table_len = h.table_len;
-    db->log_t = h.log_t;
+    db->fmt = mc::TableFmt{h.log_t, h.cbits};
+    db->loc_jbits = h.loc_jbits;
     db->max_probe = h.max_probe;
     db->overflow_keys = h.overflow_keys;
     {
@@ -876,12 +896,13 @@ int mc_db_stats(const mc_db* db, mc_db_stats_t* out) {
     out->n_locations = db->n_kept;
     out->overflow_keys = db->overflow_keys;
     out->dropped_locations = out->n_pairs - db->n_kept;
-    out->table_slots = db->has_table ? (1ull << db->log_t) : 0;
+    out->table_slots = db->has_table ? (1ull << db->fmt.log_t) : 0;
     out->max_probe = db->max_probe;
     out->device_bytes = held_bytes(db);
     out->load_factor = out->table_slots ? (double)db->n_keys / (double)out->table_slots : 0.0;
     out->finalized = db->dirty ? 0 : 1;
     out->max_depth = db->max_depth;
+    out->loc_bytes = db->has_table ? mc::loc_bytes(db->loc_jbits) : 0;
     return MC_OK;
 }
 
@@ -897,8 +918,8 @@ int mc_db_dump(const mc_db* db, uint64_t key_lo, uint64_t key_hi, uint64_t max_k
     mc::Tmp<unsigned long long> dn(db->mem, 1, s);
     if (!dkeys.ok() || !dcnt.ok() || !doff.ok() || !dn.ok()) return fail(MC_ERR_OOM, "dump: allocation failed");
     MC_CU(cudaMemsetAsync(dn.ptr, 0, 8, s));
-    MC_CU(mc::dump_select((const uint4*)db->table.p, db->table_len, key_lo, key_hi, dkeys.ptr, doff.ptr, dcnt.ptr, cap,
-                          dn.ptr, s));
+    MC_CU(mc::dump_select((const uint64_t*)db->table.p, db->table_len, db->fmt, key_lo, key_hi, dkeys.ptr, doff.ptr,
+                          dcnt.ptr, cap, dn.ptr, s));
     unsigned long long nsel = 0;
     MC_CU(cudaMemcpyAsync(&nsel, dn.ptr, 8, cudaMemcpyDeviceToHost, s));
     MC_CU(cudaStreamSynchronize(s));
@@ -939,7 +960,7 @@ int mc_db_dump(const mc_db* db, uint64_t key_lo, uint64_t key_hi, uint64_t max_k
         MC_CU(cudaMemcpyAsync(dsrc.ptr, src.data(), nsel * 8, cudaMemcpyHostToDevice, s));
         MC_CU(cudaMemcpyAsync(ddst.ptr, dst.data(), nsel * 8, cudaMemcpyHostToDevice, s));
         MC_CU(cudaMemcpyAsync(dc.ptr, cnt.data(), nsel * 4, cudaMemcpyHostToDevice, s));
-        MC_CU(mc::dump_gather((const uint64_t*)db->locs.p, dsrc.ptr, dc.ptr, ddst.ptr, nsel, dout.ptr, s));
+        MC_CU(mc::dump_gather(db->locs.p, db->loc_jbits, dsrc.ptr, dc.ptr, ddst.ptr, nsel, dout.ptr, s));
         MC_CU(cudaMemcpyAsync(locs, dout.ptr, total * 8, cudaMemcpyDeviceToHost, s));
         MC_CU(cudaStreamSynchronize(s));
     }
@@ -1011,13 +1032,16 @@ int tuning_from(const mc_tuning* t, const mc::Tuning& dflt, mc::Tuning* out) {
     if (t->lookup_warps) x.lookup_warps = t->lookup_warps;
     if (t->score_warps) x.score_warps = t->score_warps;
     if (t->wide_keys) x.wide_keys = t->wide_keys;
+    if (t->score_mode) x.score_mode = t->score_mode;
+    if (t->sort_max) x.sort_max = t->sort_max;
     if (!mc::tuning_valid(x)) return fail(MC_ERR_ARG, "tuning: a value is outside its allowed set");
     *out = x;
     return MC_OK;
 }
 
 mc_tuning to_public(const mc::Tuning& t) {
-    return mc_tuning{t.hist_slots, t.probe_batch, t.gather_batch, t.lookup_warps, t.score_warps, t.wide_keys};
+    return mc_tuning{t.hist_slots, t.probe_batch, t.gather_batch, t.lookup_warps,
+                     t.score_warps, t.wide_keys,  t.score_mode,   t.sort_max};
 }
 
 // Host image of the batch header + descriptors (layout of ClassifyQuery's

@@ -631,7 +631,8 @@ __global__ void __launch_bounds__(BT) k_fin_count(const uint64_t* __restrict__ a
 }
 
 // Writes the condensed outputs at the scanned positions: locations of kept
-// pairs (global window -> (target, window)), and per feature its h2 value,
+// pairs (global window -> (target, window), 32-bit target << jbits | window
+// when jbits > 0, else 64-bit target << 32 | window), and per feature its h2 value,
 // the position of its first location and the index of its first pair.
 // The target of a global window gw is the last t with wbase[t] <= gw; a
 // block first tabulates that target for the first window of each of
@@ -640,7 +641,7 @@ __global__ void __launch_bounds__(BT) k_fin_count(const uint64_t* __restrict__ a
 __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
                                                  const uint64_t* __restrict__ tkept, const uint64_t* __restrict__ tkeys,
                                                  uint64_t n_tiles, const uint32_t* __restrict__ wbase,
-                                                 uint32_t n_targets, uint64_t* __restrict__ locs,
+                                                 uint32_t n_targets, uint32_t jbits, void* __restrict__ locs,
                                                  uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
                                                  uint64_t* __restrict__ kstart, unsigned long long* overflow) {
     __shared__ uint32_t first_target[FIN_BUCKETS + 1];
@@ -704,7 +705,10 @@ __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a,
                     const uint32_t mid = (lo + hi) >> 1;
                     if (wb[mid] <= gw) lo = mid; else hi = mid;
                 }
-                locs[my_k] = ((uint64_t)lo << 32) | (gw - wb[lo]);
+                if (jbits)
+                    static_cast<uint32_t*>(locs)[my_k] = (lo << jbits) | (gw - wb[lo]);
+                else
+                    static_cast<uint64_t*>(locs)[my_k] = ((uint64_t)lo << 32) | (gw - wb[lo]);
             }
             if (st) {
                 const uint64_t my_s = kidx + __popc(bs & lt);
@@ -722,17 +726,29 @@ __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a,
 
 // Pairs (h2 << 32 | global window) of a finalized layout, in layout order:
 // the input of the next finalize after an extension.
-__global__ void k_reconstruct_pairs(const uint4* __restrict__ table, uint64_t table_len,
-                                    const uint64_t* __restrict__ locs, const uint32_t* __restrict__ wbase,
-                                    uint64_t* __restrict__ out) {
+__global__ void k_reconstruct_pairs(const uint64_t* __restrict__ table, uint64_t table_len, TableFmt fmt,
+                                    const void* __restrict__ locs, uint32_t jbits,
+                                    const uint32_t* __restrict__ wbase, uint64_t* __restrict__ out) {
+    const uint32_t jmask = jbits ? (1u << jbits) - 1u : 0u;
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < table_len;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint4 e = table[i];
-        if (e.y == 0) continue;
-        const uint64_t off = (uint64_t)e.z | ((uint64_t)e.w << 32);
-        for (uint32_t j = 0; j < e.y; ++j) {
-            const uint64_t loc = locs[off + j];
-            out[off + j] = ((uint64_t)e.x << 32) | (uint32_t)(wbase[(uint32_t)(loc >> 32)] + (uint32_t)loc);
+        const uint64_t e = table[i];
+        if (e == 0) continue;
+        const uint64_t off = fmt.offset(e);
+        const uint32_t cnt = fmt.count(e);
+        const uint64_t hk = (uint64_t)fmt.key(e, i) << 32;
+        for (uint32_t j = 0; j < cnt; ++j) {
+            uint32_t t, w;
+            if (jbits) {
+                const uint32_t x = static_cast<const uint32_t*>(locs)[off + j];
+                t = x >> jbits;
+                w = x & jmask;
+            } else {
+                const uint64_t x = static_cast<const uint64_t*>(locs)[off + j];
+                t = (uint32_t)(x >> 32);
+                w = (uint32_t)x;
+            }
+            out[off + j] = hk | (uint32_t)(wbase[t] + w);
         }
     }
 }
@@ -774,11 +790,14 @@ __global__ void __launch_bounds__(BT) k_tab_dispmax(const uint32_t* __restrict__
     }
 }
 
-// slot(k) = k + max(prefix, inclusive max of home - k); writes the entry.
+// slot(k) = k + max(prefix, inclusive max of home - k); writes the packed
+// word.  A displacement beyond the word's field sets *too_far (the host then
+// retries with a larger table).
 __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ khk, const uint64_t* __restrict__ koff,
                                                  const uint64_t* __restrict__ kstart, uint64_t n, uint32_t cap,
-                                                 uint32_t log_t, const int64_t* __restrict__ tpre, uint64_t n_tiles,
-                                                 uint4* __restrict__ table, unsigned int* max_disp) {
+                                                 TableFmt fmt, const int64_t* __restrict__ tpre, uint64_t n_tiles,
+                                                 uint64_t* __restrict__ table, unsigned int* max_disp,
+                                                 unsigned int* too_far) {
     __shared__ int64_t sm[NWARP];
     __shared__ uint64_t smu[NWARP];
     for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -789,7 +808,7 @@ __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ kh
             uint64_t e = base + (uint64_t)i * BT + threadIdx.x;
             bool in_range = e < n;
             uint32_t hk = in_range ? khk[e] : 0;
-            uint64_t home = home_slot(hk, log_t);
+            uint64_t home = fmt.home(hk);
             int64_t a = in_range ? (int64_t)home - (int64_t)e : INT64_MIN;
             int64_t tot;
             int64_t ex = block_exclusive(a, (int64_t)INT64_MIN, OpMaxI(), sm, &tot);
@@ -799,9 +818,10 @@ __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ kh
                 uint64_t slot = (uint64_t)((int64_t)e + inc);
                 uint64_t len = kstart[e + 1] - kstart[e];
                 uint32_t cnt = (uint32_t)(len < cap ? len : cap);
-                uint64_t off = koff[e];
-                table[slot] = make_uint4(hk, cnt, (uint32_t)off, (uint32_t)(off >> 32));
-                dmax = max(dmax, slot - home);
+                const uint64_t disp = slot - home;
+                if (disp > TAB_MAX_DISP) atomicMax(too_far, 1u);
+                table[slot] = fmt.pack(koff[e], hk, (uint32_t)(disp & TAB_MAX_DISP), cnt);
+                dmax = max(dmax, disp);
             }
         }
         uint64_t dm = block_reduce(dmax, (uint64_t)0, OpMaxU(), smu);
@@ -810,21 +830,23 @@ __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ kh
 }
 }  // namespace
 
-cudaError_t reconstruct_pairs(const uint4* table, uint64_t table_len, const uint64_t* locs, const uint32_t* wbase,
-                              uint64_t* out, cudaStream_t s) {
+cudaError_t reconstruct_pairs(const uint64_t* table, uint64_t table_len, TableFmt fmt, const void* locs, uint32_t jbits,
+                              const uint32_t* wbase, uint64_t* out, cudaStream_t s) {
     if (table_len == 0) return cudaSuccess;
     MC_LAUNCH("reconstruct_pairs", s,
-              k_reconstruct_pairs<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, locs, wbase, out));
+              k_reconstruct_pairs<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, fmt, locs, jbits,
+                                                                                     wbase, out));
     return cudaGetLastError();
 }
 
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
-                           uint32_t n_targets, FinalizeOut* out, cudaStream_t s) {
+                           uint32_t n_targets, uint32_t jbits, FinalizeOut* out, cudaStream_t s) {
     cudaError_t e;
     *out = FinalizeOut();
     const uint64_t tiles = (n + FIN_TILE - 1) / FIN_TILE;
     const uint32_t g = grid_for(tiles ? tiles : 1);
-    // counters: [0] overflow keys, [1] max displacement (u32 in low word)
+    // counters: [0] overflow keys, [1] max displacement (u32 in low word),
+    // [2] displacement beyond the word's field
     Tmp<unsigned long long> ctr(mem, 4, s);
     if (!ctr.ok()) return cudaErrorMemoryAllocation;
     if ((e = cudaMemsetAsync(ctr.ptr, 0, 4 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
@@ -841,58 +863,79 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     }
     const uint64_t n_kept = host_tot[0], n_keys = host_tot[1];
-    Tmp<uint64_t> locs(mem, n_kept, s), koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
+    // table format: slots = 2^log_t >= 2 n_keys (load factor <= 1/2), and
+    // enough offset bits for every location; a larger table is taken when
+    // a displacement does not fit the word's field
+    TableFmt fmt{1, count_bits(cap)};
+    while ((1ull << fmt.log_t) < 2 * n_keys) ++fmt.log_t;
+    while (fmt.log_t <= 32 && fmt.obits() < 64 && (n_kept >> fmt.obits()) != 0) ++fmt.log_t;
+    if (fmt.log_t > 32) {
+        out->table_full = true;
+        return cudaSuccess;
+    }
+    Tmp<unsigned char> locs(mem, n_kept * loc_bytes(jbits), s);
+    Tmp<uint64_t> koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
     Tmp<uint32_t> khk(mem, n_keys, s);
     if (!locs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
         MC_LAUNCH("fin_emit", s,
-                  k_fin_emit<<<g, BT, 0, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets,
-                                                     locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
+                  k_fin_emit<<<g, BT, 0, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets, jbits,
+                                              locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     }
-    // feature table: T = power of two >= 4 * n_keys (load factor <= 1/4, so
-    // almost every probe is answered by the home slot)
-    uint32_t log_t = 1;
-    while ((1ull << log_t) < 4 * n_keys) ++log_t;
-    const uint64_t T = 1ull << log_t;
     const uint64_t ktiles = (n_keys + FIN_TILE - 1) / FIN_TILE;
-    int64_t host_maxa = INT64_MIN;
     Tmp<int64_t> kt_max(mem, ktiles + 1, s), kt_pre(mem, ktiles + 1, s);
     if (!kt_max.ok() || !kt_pre.ok()) return cudaErrorMemoryAllocation;
-    if (n_keys > 0) {
-        MC_LAUNCH("tab_dispmax", s,
-                  k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, log_t, kt_max.ptr, ktiles));
-        MC_LAUNCH("exclusive_max_i64", s,
-                  k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if ((e = cudaMemcpyAsync(&host_maxa, kt_pre.ptr + ktiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    unsigned long long host_ctr[3] = {0, 0, 0};
+    for (;;) {
+        const uint64_t T = 1ull << fmt.log_t;
+        int64_t host_maxa = INT64_MIN;
+        if (n_keys > 0) {
+            MC_LAUNCH("tab_dispmax", s,
+                      k_tab_dispmax<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, n_keys, fmt.log_t, kt_max.ptr, ktiles));
+            MC_LAUNCH("exclusive_max_i64", s,
+                      k_exclusive_max_i64<<<1, BT, 0, s>>>(kt_max.ptr, kt_pre.ptr, ktiles, kt_pre.ptr + ktiles));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            if ((e = cudaMemcpyAsync(&host_maxa, kt_pre.ptr + ktiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+                return e;
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        }
+        const uint64_t last_slot = n_keys ? (uint64_t)((int64_t)(n_keys - 1) + host_maxa) : 0;
+        // two empty words past the last key or the home slots, rounded to whole 32-byte sectors
+        const uint64_t table_len = (((last_slot + 1 > T ? last_slot + 1 : T) + 2) + 3) & ~3ull;
+        Tmp<uint64_t> table(mem, table_len, s);
+        if (!table.ok()) return cudaErrorMemoryAllocation;
+        if ((e = cudaMemsetAsync(table.ptr, 0, table_len * sizeof(uint64_t), s)) != cudaSuccess) return e;
+        if ((e = cudaMemsetAsync(ctr.ptr + 1, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
+        if (n_keys > 0) {
+            MC_LAUNCH("tab_emit", s,
+                      k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, fmt,
+                                                                 kt_pre.ptr, ktiles, table.ptr,
+                                                                 (unsigned int*)(ctr.ptr + 1),
+                                                                 (unsigned int*)(ctr.ptr + 2)));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        if ((e = cudaMemcpyAsync(host_ctr, ctr.ptr, 24, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if (host_ctr[2]) {  // a displacement beyond the word's field: twice the slots
+            if (++fmt.log_t > 32) {
+                out->table_full = true;
+                return cudaSuccess;
+            }
+            continue;
+        }
+        out->table_len = table_len;
+        out->table_bytes = table_len * sizeof(uint64_t);
+        out->table = table.release();
+        break;
     }
-    const uint64_t last_slot = n_keys ? (uint64_t)((int64_t)(n_keys - 1) + host_maxa) : 0;
-    const uint64_t table_len = (last_slot + 1 > T ? last_slot + 1 : T) + 2;
-    Tmp<uint4> table(mem, table_len, s);
-    if (!table.ok()) return cudaErrorMemoryAllocation;
-    if ((e = cudaMemsetAsync(table.ptr, 0, table_len * sizeof(uint4), s)) != cudaSuccess) return e;
-    if (n_keys > 0) {
-        MC_LAUNCH("tab_emit", s,
-                  k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, log_t,
-                                                             kt_pre.ptr, ktiles, table.ptr,
-                                                             (unsigned int*)(ctr.ptr + 1)));
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    unsigned long long host_ctr[2] = {0, 0};
-    if ((e = cudaMemcpyAsync(host_ctr, ctr.ptr, 16, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     out->n_keys = n_keys;
     out->n_kept = n_kept;
     out->overflow_keys = host_ctr[0];
     out->max_probe = (uint32_t)(host_ctr[1] & 0xFFFFFFFFull);
-    out->log_t = log_t;
-    out->table_len = table_len;
-    out->table_bytes = table_len * sizeof(uint4);
+    out->fmt = fmt;
     out->locs = locs.release();
-    out->table = table.release();
     return cudaSuccess;
 }
 
@@ -941,43 +984,55 @@ cudaError_t taxonomy_lineage(const uint32_t* parent, uint32_t n_taxa, const uint
 
 // ------------------------------------------------------------------ dump
 namespace {
-__global__ void k_dump_select(const uint4* __restrict__ table, uint64_t len, uint64_t lo, uint64_t hi,
-                              uint32_t* keys, uint64_t* offs, uint32_t* counts, uint64_t cap,
+__global__ void k_dump_select(const uint64_t* __restrict__ table, uint64_t len, TableFmt fmt, uint64_t lo,
+                              uint64_t hi, uint32_t* keys, uint64_t* offs, uint32_t* counts, uint64_t cap,
                               unsigned long long* n_sel) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < len; i += (uint64_t)gridDim.x * blockDim.x) {
-        uint4 e = table[i];
-        if (e.y == 0) continue;
-        uint64_t key = hash_h2_inverse(e.x);
+        const uint64_t e = table[i];
+        if (e == 0) continue;
+        uint64_t key = hash_h2_inverse(fmt.key(e, i));
         if (key < lo || key >= hi) continue;
         unsigned long long idx = atomicAdd(n_sel, 1ull);
         if (idx < cap) {
             keys[idx] = (uint32_t)key;
-            offs[idx] = (uint64_t)e.z | ((uint64_t)e.w << 32);
-            counts[idx] = e.y;
+            offs[idx] = fmt.offset(e);
+            counts[idx] = fmt.count(e);
         }
     }
 }
 
-__global__ void k_dump_gather(const uint64_t* __restrict__ locs, const uint64_t* __restrict__ src_off,
+__global__ void k_dump_gather(const void* __restrict__ locs, uint32_t jbits, const uint64_t* __restrict__ src_off,
                               const uint32_t* __restrict__ counts, const uint64_t* __restrict__ dst_off, uint64_t n,
                               uint64_t* __restrict__ out) {
     for (uint64_t i = blockIdx.x; i < n; i += gridDim.x)
-        for (uint32_t j = threadIdx.x; j < counts[i]; j += blockDim.x) out[dst_off[i] + j] = locs[src_off[i] + j];
+        for (uint32_t j = threadIdx.x; j < counts[i]; j += blockDim.x) {
+            uint64_t v;
+            if (jbits) {
+                const uint32_t x = static_cast<const uint32_t*>(locs)[src_off[i] + j];
+                v = ((uint64_t)(x >> jbits) << 32) | (x & ((1u << jbits) - 1u));
+            } else {
+                v = static_cast<const uint64_t*>(locs)[src_off[i] + j];
+            }
+            out[dst_off[i] + j] = v;
+        }
 }
 }  // namespace
 
-cudaError_t dump_select(const uint4* table, uint64_t table_len, uint64_t lo, uint64_t hi, uint32_t* keys,
-                        uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel, cudaStream_t s) {
+cudaError_t dump_select(const uint64_t* table, uint64_t table_len, TableFmt fmt, uint64_t lo, uint64_t hi,
+                        uint32_t* keys, uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel,
+                        cudaStream_t s) {
     if (table_len == 0) return cudaSuccess;
-    MC_LAUNCH("dump_select", s, k_dump_select<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, lo, hi, keys, offs, counts,
-                                                                      cap, n_sel));
+    MC_LAUNCH("dump_select", s,
+              k_dump_select<<<grid_for((table_len + BT - 1) / BT), BT, 0, s>>>(table, table_len, fmt, lo, hi, keys,
+                                                                               offs, counts, cap, n_sel));
     return cudaGetLastError();
 }
 
-cudaError_t dump_gather(const uint64_t* locs, const uint64_t* src_off, const uint32_t* counts, const uint64_t* dst_off,
-                        uint64_t n, uint64_t* out, cudaStream_t s) {
+cudaError_t dump_gather(const void* locs, uint32_t jbits, const uint64_t* src_off, const uint32_t* counts,
+                        const uint64_t* dst_off, uint64_t n, uint64_t* out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    MC_LAUNCH("dump_gather", s, k_dump_gather<<<grid_for(n, 32), 128, 0, s>>>(locs, src_off, counts, dst_off, n, out));
+    MC_LAUNCH("dump_gather", s,
+              k_dump_gather<<<grid_for(n, 32), 128, 0, s>>>(locs, jbits, src_off, counts, dst_off, n, out));
     return cudaGetLastError();
 }
 

@@ -61,16 +61,19 @@ __device__ __forceinline__ uint32_t loc_slot(uint32_t key, uint32_t mask) {
     return (h ^ (h >> 15)) & mask;
 }
 
-// Histogram keys: the location (target << 32 | window) as is, or, when the
-// database's target and window ids fit 32 bits, packed into 32 bits as
-// target << jbits | window (halves the key memory of the shared-memory
-// histograms).
-template <class KeyT>
+// Histogram keys.  A database stores its locations as 32-bit words target
+// << jbits | window when every id fits, else as 64-bit words target << 32 |
+// window (LocT).  The histogram keys a location by the stored word itself
+// (KeyT == LocT), or, for 32-bit words, optionally by the 64-bit form (the
+// wide-key launch shape).
+template <class KeyT, class LocT = KeyT>
 struct KeyCodec {
+    static_assert(sizeof(KeyT) >= sizeof(LocT), "keys are at least as wide as locations");
     uint32_t jbits;
-    __device__ __forceinline__ KeyT encode(uint64_t loc) const {
-        if (sizeof(KeyT) == 8) return (KeyT)loc;
-        return (KeyT)(((uint32_t)(loc >> 32) << jbits) | (uint32_t)loc);
+    __device__ __forceinline__ KeyT encode(LocT loc) const {
+        if (sizeof(KeyT) == sizeof(LocT)) return (KeyT)loc;
+        const uint32_t x = (uint32_t)loc;
+        return (KeyT)(((uint64_t)(x >> jbits) << 32) | (x & ((1u << jbits) - 1u)));
     }
     __device__ __forceinline__ uint32_t target(KeyT k) const {
         return sizeof(KeyT) == 8 ? (uint32_t)((uint64_t)k >> 32) : (uint32_t)k >> jbits;
@@ -395,7 +398,7 @@ template <int R, int KC, int LB, class CntT>
 __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const ClassifyQuery& Q, const Scratch<CntT>& S,
                                              const uint8_t* buf, const Staged& sq, uint64_t* __restrict__ list,
                                              uint32_t& n_list_out, uint32_t& sws_out, uint32_t& n_feat_out,
-                                             uint32_t& n_sect_out) {
+                                             uint32_t& n_sect_out, uint32_t& n_locs_out) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     const SketchParams& p = db.sp;
@@ -438,23 +441,26 @@ __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const Classif
     }
     __syncwarp();
 
-    // 1c. feature table probes, LB per lane in flight
+    // 1c. feature table probes, LB per lane in flight.  A probe reads the
+    // aligned 16-byte pair of table words holding the home slot, then
+    // follows the ordered probe sequence (stop at an empty slot or a key >=
+    // h) one word at a time; the longest sequence is the table's largest
+    // displacement.
+    const TableFmt fmt = db.fmt;
+    const uint32_t lsz = db.jbits ? 4u : 8u;  // bytes per stored location
     uint32_t n_list = 0;
-    unsigned long long n_sect = 0;
+    unsigned long long n_sect = 0, n_locs = 0;
     for (uint32_t base = 0; base < F; base += 32 * LB) {
         uint32_t hk[LB];
         uint64_t pos[LB];
-        uint4 e[LB];
-        uint4 e2[LB];
+        ulonglong2 pr[LB];
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
             const uint32_t idx = base + b * 32 + lane;
             hk[b] = idx < F ? hash_h2(S.feat[idx]) : 0u;
-            pos[b] = db.log_t >= 32 ? hk[b] : (hk[b] >> (32 - db.log_t));
-            // the home slot, and the next one when both lie in the same 64-byte
-            // segment (the table has 2 slots of padding)
-            e[b] = idx < F ? __ldg(db.table + pos[b]) : make_uint4(0, 0, 0, 0);
-            e2[b] = (idx < F && (pos[b] & 3) != 3) ? __ldg(db.table + pos[b] + 1) : make_uint4(0, 0, 0, 0);
+            pos[b] = fmt.home(hk[b]);
+            pr[b] = idx < F ? __ldg(reinterpret_cast<const ulonglong2*>(db.table + (pos[b] & ~1ull)))
+                            : make_ulonglong2(0, 0);
         }
 #pragma unroll
         for (int b = 0; b < LB; ++b) {
@@ -462,19 +468,27 @@ __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const Classif
             uint32_t c = 0;
             uint64_t off = 0;
             if (idx < F) {
-                uint4 x = e[b];
-                if (x.y != 0 && x.x < hk[b] && db.max_probe >= 1)
-                    x = (pos[b] & 3) != 3 ? e2[b] : __ldg(db.table + pos[b] + 1);
-                for (uint32_t d = 2; x.y != 0 && x.x < hk[b] && d <= db.max_probe; ++d) x = __ldg(db.table + pos[b] + d);
-                if (x.y != 0 && x.x == hk[b]) {
-                    c = x.y;
-                    off = (uint64_t)x.z | ((uint64_t)x.w << 32);
+                uint64_t slot = pos[b];
+                uint64_t e = (slot & 1) ? pr[b].y : pr[b].x;
+                for (uint32_t d = 0; e != 0; ) {
+                    const uint32_t k = fmt.key(e, slot);
+                    if (k >= hk[b]) {
+                        if (k == hk[b]) {
+                            c = fmt.count(e);
+                            off = fmt.offset(e);
+                        }
+                        break;
+                    }
+                    if (++d > db.max_probe) break;
+                    ++slot;
+                    e = (slot == (pos[b] | 1ull)) ? pr[b].y : __ldg(db.table + slot);
                 }
             }
             const uint32_t found = __ballot_sync(FULL_MASK, c > 0);
             if (c > 0) {
                 list[n_list + __popc(found & lt)] = (off << 16) | c;
-                n_sect += ((off * 8 + (uint64_t)c * 8 - 1) >> 5) - ((off * 8) >> 5) + 1;
+                n_sect += ((off * lsz + (uint64_t)c * lsz - 1) >> 5) - ((off * lsz) >> 5) + 1;
+                n_locs += c;
             }
             n_list += __popc(found);
         }
@@ -482,6 +496,7 @@ __device__ __forceinline__ void sketch_probe(const ClassifyDb& db, const Classif
     __syncwarp();
     n_feat_out = F;
     n_sect_out = (uint32_t)warp_sum_u64(n_sect);
+    n_locs_out = (uint32_t)warp_sum_u64(n_locs);  // <= 2048 features x 65535
     const uint64_t span = (nm <= 1) ? span_sum : (span_sum > Q.max_insert ? span_sum : (uint64_t)Q.max_insert);
     sws_out = span >= p.k ? (uint32_t)((span - p.k + p.stride - 1) / p.stride + 1) : 0;
     n_list_out = n_list;
@@ -495,7 +510,8 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
                                             uint32_t& sws_out, uint32_t& n_feat_out, uint32_t& n_sect_out) {
     const Staged st = stage_query<false>(db, Q, q, S.buf, S.buf_cap, S.win_cap);
     if (st.status != Q_DONE) return st.status;
-    sketch_probe<R, KC, LB>(db, Q, S, S.buf, st, list, n_list_out, sws_out, n_feat_out, n_sect_out);
+    uint32_t n_locs = 0;
+    sketch_probe<R, KC, LB>(db, Q, S, S.buf, st, list, n_list_out, sws_out, n_feat_out, n_sect_out, n_locs);
     return Q_DONE;
 }
 
@@ -503,14 +519,16 @@ __device__ __forceinline__ int query_lookup(const ClassifyDb& db, const Classify
 // working memory: gather, window count statistic, sliding-window scores,
 // top m, label.  Writes the outputs and returns Q_DONE, or Q_ESCALATE if the
 // histogram does not fit the working memory.
-template <int GB, class CntT, class KeyT>
+template <int GB, class LocT, class CntT, class KeyT>
 __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
                                            const Scratch<CntT, KeyT>& S, uint32_t n_list, uint32_t sws,
                                            Counters& ctr) {
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
-    const KeyCodec<KeyT> kc{db.jbits};
+    const KeyCodec<KeyT, LocT> kc{db.jbits};
     constexpr KeyT EMPTY = KeyCodec<KeyT>::empty();
+    constexpr LocT NO_LOC = (LocT)~(LocT)0;  // never a stored location
+    const LocT* __restrict__ locs = static_cast<const LocT*>(db.locs);
 
     // 2. exclusive prefix of bucket sizes; H = locations to gather
     uint32_t H = 0;
@@ -554,26 +572,30 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
             if (S.l_pre[mid] <= x0) lo = mid; else hi = mid;
         }
         uint32_t bkt = lo;
-        uint64_t v[GB];
+        LocT v[GB];
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             const uint32_t x = x0 + g;
-            v[g] = EMPTY_LOC;
+            v[g] = NO_LOC;
             if (x < H) {
                 while (S.l_pre[bkt + 1] <= x) ++bkt;
-                v[g] = __ldg(db.locs + (S.list[bkt] >> 16) + (x - S.l_pre[bkt]));
+                v[g] = __ldg(locs + (S.list[bkt] >> 16) + (x - S.l_pre[bkt]));
             }
         }
         bool ok = true;
 #pragma unroll
         for (int g = 0; g < GB; ++g) {
             int slot = -1;
-            if (v[g] != EMPTY_LOC) ok &= hist_insert(S.keys, S.cnts, mask, kc.encode(v[g]), slot);
+            if (v[g] != NO_LOC) ok &= hist_insert(S.keys, S.cnts, mask, kc.encode(v[g]), slot);
             const uint32_t fresh = __ballot_sync(FULL_MASK, slot >= 0);
             if (slot >= 0) S.dense[D + __popc(fresh & lt)] = (uint16_t)slot;
             D += __popc(fresh);
+            // checked after every round, so the table never passes limit + 32
+            // entries: inserts stay cheap and a query that will not fit is
+            // handed on as soon as it is known
+            if (D > limit) return Q_ESCALATE;
         }
-        if (__any_sync(FULL_MASK, !ok) || D > limit) return Q_ESCALATE;
+        if (__any_sync(FULL_MASK, !ok)) return Q_ESCALATE;
     }
     __syncwarp();
     ctr.locations += H;
@@ -659,13 +681,13 @@ __device__ __forceinline__ int query_score(const ClassifyDb& db, const ClassifyQ
 }
 
 // Whole query on one warp with the bucket list in working memory.
-template <int R, int KC, class CntT>
+template <int R, int KC, class LocT, class CntT>
 __device__ __forceinline__ int process_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
                                              const Scratch<CntT>& S, Counters& ctr) {
     uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
     int r = query_lookup<R, KC, LB_DEFAULT>(db, Q, q, S, S.list, n_list, sws, n_feat, n_sect);
     if (r != Q_DONE) return r;
-    r = query_score<GB_DEFAULT>(db, Q, q, S, n_list, sws, ctr);
+    r = query_score<GB_DEFAULT, LocT>(db, Q, q, S, n_list, sws, ctr);
     if (r == Q_DONE) {
         ctr.features += n_feat;
         ctr.found += n_list;
@@ -733,6 +755,14 @@ __host__ __device__ constexpr size_t lookup_warp_bytes(uint32_t list_cap) {
     return scratch_bytes<uint16_t>(0, 0, list_cap, BUF_A) + align16(BUF_A + 16) + 2 * STAGED_BYTES;
 }
 
+// Per-query metadata written by the lookup kernel: {found buckets, sliding
+// window size | features << META_FEAT_SHIFT, locations to gather, 32-byte
+// sectors of those locations}, or x = ESCALATED.  On this path a query has
+// at most WIN_A * MAX_S = 256 features and a sliding window below 2^17.
+constexpr uint32_t META_FEAT_SHIFT = 20;
+__device__ __forceinline__ uint32_t meta_sws(const uint4& m) { return m.y & ((1u << META_FEAT_SHIFT) - 1u); }
+__device__ __forceinline__ uint32_t meta_feat(const uint4& m) { return m.y >> META_FEAT_SHIFT; }
+
 // Main path, part 1 (sketch + lookup): one warp per query of the chunk
 // [q0, q0 + nq), shared memory for the query's bases and features only, so
 // many warps fit on an SM.  Software-pipelined: the bases of the warp's
@@ -770,11 +800,11 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
                         stage_query<true>(db, Q, q0 + nx, cur ? buf0 : buf1, BUF_A, WIN_A));
         const Staged st = load_staged(recs + cur * STAGED_BYTES);
         const uint32_t q = q0 + i;
-        uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0;
+        uint32_t n_list = 0, sws = 0, n_feat = 0, n_sect = 0, n_locs = 0;
         int r = st.status;
         if (r == Q_DONE)
             sketch_probe<R, KC, LB>(db, Q, S, cur ? buf1 : buf0, st, glist + (uint64_t)i * list_cap, n_list, sws, n_feat,
-                                    n_sect);
+                                    n_sect, n_locs);
         if (r == Q_ESCALATE) {
             if (lane_id() == 0) {
                 ovf_list[atomicAdd(ovf_n, 1u)] = q;
@@ -787,7 +817,7 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
                 meta[i] = make_uint4(ESCALATED, 0, 0, 0);
             }
         } else if (lane_id() == 0) {
-            meta[i] = make_uint4(n_list, sws, n_feat, n_sect);
+            meta[i] = make_uint4(n_list, sws | (n_feat << META_FEAT_SHIFT), n_locs, n_sect);
         }
         __syncwarp();
         cur ^= 1;
@@ -798,7 +828,7 @@ __global__ void __launch_bounds__(LK_WARPS * 32, 4) k_classify_lookup(ClassifyDb
 // Main path, part 2 (gather + score + label): one warp per query of the
 // chunk, KA histogram slots per warp in shared memory.  Queries whose
 // histogram does not fit are queued (chunk index) for the medium path.
-template <int KA, int GB, class KeyT>
+template <int KA, int GB, class KeyT, class LocT>
 __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                      uint32_t chunk, uint32_t list_cap,
                                                                      const uint64_t* __restrict__ glist,
@@ -819,14 +849,20 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
     for (uint32_t i = gw; i < nq; i += nwarp) {
         const uint4 mt = meta[i];
         if (mt.x == ESCALATED) continue;
+        // more locations than histogram slots: almost surely more distinct
+        // locations than the histogram holds, so straight to the medium path
+        if (mt.z > (uint32_t)KA) {
+            if (lane == 0) mid_list[atomicAdd(mid_n, 1u)] = i;
+            continue;
+        }
         const uint64_t* src = glist + (uint64_t)i * list_cap;
         for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
         __syncwarp();
         const uint32_t q = q0 + i;
-        if (query_score<GB>(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
+        if (query_score<GB, LocT>(db, Q, q, S, mt.x, meta_sws(mt), ctr) == Q_ESCALATE) {
             if (lane == 0) mid_list[atomicAdd(mid_n, 1u)] = i;
         } else {
-            ctr.features += mt.z;
+            ctr.features += meta_feat(mt);
             ctr.found += mt.x;
             ctr.sectors += mt.w;
         }
@@ -839,7 +875,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
 // path, one warp each (work queue), KM_SLOTS histogram slots per warp in
 // shared memory, the bucket list taken over from the lookup.  Queries that
 // do not fit here either go to the large path.
-template <int GB, class KeyT>
+template <int GB, class KeyT, class LocT>
 __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                    uint32_t list_cap,
                                                                    const uint64_t* __restrict__ glist,
@@ -868,10 +904,10 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
         for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
         __syncwarp();
         const uint32_t q = q0 + i;
-        if (query_score<GB>(db, Q, q, S, mt.x, mt.y, ctr) == Q_ESCALATE) {
+        if (query_score<GB, LocT>(db, Q, q, S, mt.x, meta_sws(mt), ctr) == Q_ESCALATE) {
             if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
         } else {
-            ctr.features += mt.z;
+            ctr.features += meta_feat(mt);
             ctr.found += mt.x;
             ctr.sectors += mt.w;
             ++n_medium;
@@ -882,9 +918,282 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
     if (Q.counters && lane == 0 && n_medium) atomicAdd(Q.counters + 6, n_medium);
 }
 
+// ------------------------------------------------------------------
+// Sort path (databases with 32-bit locations): query steps 5-8 of
+// Section 5.2 for a query of at most 32*E gathered locations, on one warp,
+// by sorting instead of hashing.  The paper compacts the gathered locations
+// and sorts each read's segment (Sections 5.4-5.5); here one warp gathers
+// the query's locations straight into registers (E per lane, all loads in
+// flight at once), sorts them with an in-register bitonic network, and
+// reads off the window count statistic (runs of equal locations) and the
+// sliding-window scores (Section 5.6: elements in [x, x + sws) of the sorted
+// array) without a hash table.  Same outputs as query_score.
+
+// Bitonic sort of 32*E keys held E per lane, element i = lane*E + r, into
+// ascending order of i.
+template <int E>
+__device__ __forceinline__ void warp_bitonic_sort(uint32_t (&k)[E]) {
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int K = 2; K <= 32 * E; K <<= 1) {
+        // direction of this lane's blocks once they span lanes
+        const bool lane_asc = ((lane * (uint32_t)E) & (uint32_t)K) == 0;
+#pragma unroll
+        for (int J = K >> 1; J > 0; J >>= 1) {
+            if (J < E) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if ((r & J) == 0) {
+                        const uint32_t a = k[r], b = k[r | J];
+                        const uint32_t mn = min(a, b), mx = max(a, b);
+                        const bool asc = K < E ? ((r & K) == 0) : lane_asc;
+                        k[r] = asc ? mn : mx;
+                        k[r | J] = asc ? mx : mn;
+                    }
+                }
+            } else {
+                const int lj = J / E;
+                const bool keep_min = ((lane & (uint32_t)lj) == 0) == lane_asc;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const uint32_t o = __shfl_xor_sync(FULL_MASK, k[r], lj);
+                    k[r] = keep_min ? min(k[r], o) : max(k[r], o);
+                }
+            }
+        }
+    }
+}
+
+// Shared-memory index of sorted element i: one padding word per 32, so that
+// lane-major access (i = lane*E + r, for E = 8, 16, 32) and strided access
+// (i = r*32 + lane) both hit 32 distinct banks.
+__device__ __forceinline__ uint32_t spad(uint32_t i) { return i + (i >> 5); }
+
+// Per-warp shared memory of the sort path: bucket list, its prefix, the
+// sorted keys and the scores of run starts (both padded by spad).
+template <int E>
+__host__ __device__ constexpr size_t sort_warp_bytes(uint32_t list_cap) {
+    return align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + 2 * align16((size_t)33 * E * 4);
+}
+
+constexpr int SORT_WARPS = 4;  // warps per CTA of the sort path
+
+// First index in [lo, hi) of sorted a[] (padded by spad) whose value is
+// greater than v (hi if none), galloping from lo (ranges are mostly short).
+__device__ __forceinline__ uint32_t gallop_upper_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t v) {
+    uint32_t step = 1, prev = lo;
+    uint32_t pos = lo;
+    while (pos < hi && a[spad(pos)] <= v) {
+        prev = pos + 1;
+        pos += step;
+        step <<= 1;
+    }
+    uint32_t l = prev, h = pos < hi ? pos : hi;  // a[l-1] <= v, a[h] > v (or h == hi)
+    while (l < h) {
+        const uint32_t mid = (l + h) >> 1;
+        if (a[spad(mid)] <= v) l = mid + 1; else h = mid;
+    }
+    return l;
+}
+
+// One query of at most 32*E locations on the sort path; returns Q_DONE.
+template <int E>
+__device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, uint64_t* list,
+                                          uint32_t* l_pre, uint32_t* A, uint32_t* SC, uint32_t n_list, uint32_t sws,
+                                          uint32_t H, Counters& ctr) {
+    const uint32_t lane = lane_id();
+    const uint32_t jb = db.jbits;
+    const uint32_t* __restrict__ locs = static_cast<const uint32_t*>(db.locs);
+    constexpr uint32_t NO_LOC = 0xFFFFFFFFu;  // never a stored location; sorts last
+
+    // exclusive prefix of the bucket sizes
+    uint32_t tot = 0;
+    for (uint32_t base = 0; base < n_list; base += 32) {
+        const uint32_t idx = base + lane;
+        const uint32_t c = idx < n_list ? (uint32_t)(list[idx] & 0xFFFFu) : 0;
+        uint32_t inc = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL_MASK, inc, d);
+            if ((int)lane >= d) inc += x;
+        }
+        if (idx < n_list) l_pre[idx] = tot + inc - c;
+        tot += __shfl_sync(FULL_MASK, inc, 31);
+    }
+    if (lane == 0) l_pre[n_list] = tot;
+    __syncwarp();
+
+    // gather: element x = r * 32 + lane of the flat location list
+    uint32_t k[E];
+    {
+        uint32_t lo = 0, hi = n_list;  // bucket of x = lane: last b with l_pre[b] <= lane
+        while (hi - lo > 1) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (l_pre[mid] <= lane) lo = mid; else hi = mid;
+        }
+        uint32_t bkt = lo;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const uint32_t x = (uint32_t)r * 32 + lane;
+            k[r] = NO_LOC;
+            if (x < H) {
+                while (l_pre[bkt + 1] <= x) ++bkt;
+                k[r] = __ldg(locs + (list[bkt] >> 16) + (x - l_pre[bkt]));
+            }
+        }
+    }
+    warp_bitonic_sort<E>(k);
+#pragma unroll
+    for (int r = 0; r < E; ++r) A[spad(lane * E + r)] = k[r];
+    __syncwarp();
+
+    // Runs of equal locations (window count statistic) and their
+    // sliding-window scores: score(x) = elements of the sorted array in
+    // [x, hi(x)], hi(x) = x + sws - 1 cut at the last window id of x's
+    // target.  hi grows with x, so each lane's range end only moves forward
+    // (galloping from where it was).  The first top-m round is folded in.
+    const uint32_t jmask = (1u << jb) - 1u;
+    uint32_t n_start = 0, pend = 0;
+    Cand best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
+    for (int r = 0; r < E; ++r) {
+        const uint32_t i = lane * E + r;
+        uint32_t sc = 0;
+        if (i < H) {
+            const uint32_t x = A[spad(i)];
+            if (i == 0 || x != A[spad(i - 1)]) {
+                ++n_start;
+                // no wrap: stays in x's target (sws >= 1 whenever a query has locations)
+                const uint32_t hi = x + min(sws ? sws - 1 : 0u, jmask - (x & jmask));
+                pend = gallop_upper_bound(A, max(pend, i + 1), H, hi);
+                sc = pend - i;
+                const Cand c = Cand{sc, x >> jb, x & jmask, 0};
+                if (better(c, best)) best = c;
+            }
+        }
+        SC[spad(i)] = sc;
+    }
+    const uint32_t D = __reduce_add_sync(FULL_MASK, n_start);
+    ctr.locations += H;
+    ctr.distinct += D;
+
+    // top m with one candidate per target (Section 4.2 / 5.6): rounds of
+    // warp arg-max; the winner's target is excluded from later rounds by
+    // zeroing the scores of its entries; the label is folded as in
+    // query_score.  Unless the full top-m list is requested, later rounds
+    // only matter for "close" candidates, so after the first round every
+    // score below the close threshold is cleared at once.
+    const int m = (int)Q.m;
+    Cand mine = Cand{0, 0xFFFFFFFFu, 0, 0};
+    uint32_t label = NO_TAXON, hits = 0, top = 0xFFFFFFFFu;
+    uint64_t bar = 0;
+    uint32_t prev_t = 0xFFFFFFFFu;
+    for (int rd = 0; rd < m; ++rd) {
+        if (rd) {
+            best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
+            for (int r = 0; r < E; ++r) {
+                const uint32_t i = spad(lane * E + r);
+                const uint32_t sc = SC[i];
+                if (sc == 0) continue;
+                const uint32_t x = A[i];
+                const uint32_t t = x >> jb;
+                if (t == prev_t) {
+                    SC[i] = 0;
+                    continue;
+                }
+                const Cand c = Cand{sc, t, x & jmask, 0};
+                if (better(c, best)) best = c;
+            }
+        }
+        {
+            const uint32_t ms = __reduce_max_sync(FULL_MASK, best.score);
+            const uint32_t mt = __reduce_min_sync(FULL_MASK, best.score == ms ? best.t : 0xFFFFFFFFu);
+            const uint32_t mj =
+                __reduce_min_sync(FULL_MASK, (best.score == ms && best.t == mt) ? best.j0 : 0xFFFFFFFFu);
+            best = Cand{ms, mt, mj, 0};
+        }
+        if (best.score == 0) break;
+        prev_t = best.t;
+        if (Q.cands) {
+            // last window of the range present: the last element <= hi
+            const uint32_t x0 = (best.t << jb) | best.j0;
+            const uint32_t hi = x0 + min(sws ? sws - 1 : 0u, jmask - best.j0);
+            const uint32_t e = gallop_upper_bound(A, 0, H, hi);
+            best.j1 = A[spad(e - 1)] & jmask;
+        }
+        if ((int)lane == rd) mine = best;
+        if (rd == 0) {
+            hits = best.score;
+            top = best.t;
+            bar = (uint64_t)(100 - Q.band) * hits;
+            if (hits >= Q.hits_min) label = top < db.n_targets ? db.taxon_of_target[top] : NO_TAXON;
+            else if (!Q.cands) break;
+            if (!Q.cands) {
+                // smallest score s with 100 s >= bar
+                const uint32_t s_min = (uint32_t)((bar + 99) / 100);
+                for (int r = 0; r < E; ++r) {
+                    const uint32_t i = spad(lane * E + r);
+                    if (SC[i] < s_min) SC[i] = 0;
+                }
+            }
+        } else if (hits >= Q.hits_min && 100ull * best.score >= bar) {
+            const uint32_t tx = best.t < db.n_targets ? db.taxon_of_target[best.t] : NO_TAXON;
+            label = lca2(db, label, tx);
+        } else if (!Q.cands) {
+            break;
+        }
+        __syncwarp();
+    }
+    write_result(Q, q, label, hits, top, mine);
+}
+
+// Sort path over the chunk's queries with h_lo < H <= 32*E gathered
+// locations; with `last`, queries beyond 32*E are queued for the medium path.
+template <int E>
+__global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+                                                                  uint32_t chunk, uint32_t list_cap,
+                                                                  const uint64_t* __restrict__ glist,
+                                                                  const uint4* __restrict__ meta, uint32_t h_lo,
+                                                                  uint32_t last, uint32_t* __restrict__ mid_list,
+                                                                  uint32_t* __restrict__ mid_n) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    unsigned char* p = smem + w * sort_warp_bytes<E>(list_cap);
+    uint64_t* list = reinterpret_cast<uint64_t*>(p);
+    p += align16((size_t)list_cap * 8);
+    uint32_t* l_pre = reinterpret_cast<uint32_t*>(p);
+    p += align16(((size_t)list_cap + 4) * 4);
+    uint32_t* A = reinterpret_cast<uint32_t*>(p);
+    p += align16((size_t)33 * E * 4);
+    uint32_t* SC = reinterpret_cast<uint32_t*>(p);
+    Counters ctr;
+    const uint32_t total = total_queries(Q);
+    if (q0 >= total) return;
+    const uint32_t nq = min(chunk, total - q0);
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t i = gw; i < nq; i += nwarp) {
+        const uint4 mt = meta[i];
+        if (mt.x == ESCALATED || (h_lo && mt.z <= h_lo)) continue;  // a smaller class took it
+        if (mt.z > 32u * E) {
+            if (last && lane == 0) mid_list[atomicAdd(mid_n, 1u)] = i;
+            continue;
+        }
+        const uint64_t* src = glist + (uint64_t)i * list_cap;
+        for (uint32_t j = lane; j < mt.x; j += 32) list[j] = __ldg(src + j);
+        __syncwarp();
+        query_sort<E>(db, Q, q0 + i, list, l_pre, A, SC, mt.x, meta_sws(mt), mt.z, ctr);
+        ctr.features += meta_feat(mt);
+        ctr.found += mt.x;
+        ctr.sectors += mt.w;
+        __syncwarp();
+    }
+    flush_counters(Q, ctr);
+}
+
 // Large path: queries queued by the shared-memory path, one warp each, with
 // working memory in global scratch.
-template <int R, int KC>
+template <int R, int KC, class LocT>
 __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb db, ClassifyQuery Q,
                                                                    const uint32_t* __restrict__ ovf_list,
                                                                    const uint32_t* __restrict__ ovf_n,
@@ -904,7 +1213,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
         if (i >= n) break;
         const uint32_t q = ovf_list[i];
         ++n_large;
-        int r = process_query<R, KC>(db, Q, q, S, ctr);
+        int r = process_query<R, KC, LocT>(db, Q, q, S, ctr);
         if (r != Q_DONE) {
             write_unclassified(Q, q);
             if (lane_id() == 0) atomicMax(Q.status, DEV_ERR_CAPACITY);
@@ -942,41 +1251,75 @@ LookupKernel pick_lookup(const SketchParams& sp, uint32_t lb) {
     return k16 ? lookup_for_lb<16, 16>(lb) : lookup_for_lb<16, 0>(lb);
 }
 
-template <int KA, class KeyT>
+template <int KA, class KeyT, class LocT>
 ScoreKernel score_for_gb(uint32_t gb) {
-    if (gb == 4) return k_classify_score<KA, 4, KeyT>;
-    if (gb == 16) return k_classify_score<KA, 16, KeyT>;
-    return k_classify_score<KA, 8, KeyT>;
+    if (gb == 4) return k_classify_score<KA, 4, KeyT, LocT>;
+    if (gb == 16) return k_classify_score<KA, 16, KeyT, LocT>;
+    return k_classify_score<KA, 8, KeyT, LocT>;
 }
 
-template <class KeyT>
+template <class KeyT, class LocT>
 ScoreKernel score_for_ka(uint32_t ka, uint32_t gb) {
-    if (ka == 256) return score_for_gb<256, KeyT>(gb);
-    if (ka == 1024) return score_for_gb<1024, KeyT>(gb);
-    return score_for_gb<512, KeyT>(gb);
+    if (ka == 256) return score_for_gb<256, KeyT, LocT>(gb);
+    if (ka == 1024) return score_for_gb<1024, KeyT, LocT>(gb);
+    return score_for_gb<512, KeyT, LocT>(gb);
 }
 
-ScoreKernel pick_score(uint32_t ka, uint32_t gb, bool compact) {
-    return compact ? score_for_ka<uint32_t>(ka, gb) : score_for_ka<uint64_t>(ka, gb);
+// Histogram key / location types of a launch: compact = 32-bit keys of
+// 32-bit locations; wide = 64-bit keys of 32-bit locations; otherwise both
+// 64-bit.
+enum class KeyMode { compact, wide32, wide64 };
+
+KeyMode key_mode(const ClassifyDb& db, const Tuning& t) {
+    if (!db.jbits) return KeyMode::wide64;
+    return t.wide_keys ? KeyMode::wide32 : KeyMode::compact;
 }
 
-LargeKernel pick_large(const SketchParams& sp) {
+ScoreKernel pick_score(uint32_t ka, uint32_t gb, KeyMode km) {
+    if (km == KeyMode::compact) return score_for_ka<uint32_t, uint32_t>(ka, gb);
+    if (km == KeyMode::wide32) return score_for_ka<uint64_t, uint32_t>(ka, gb);
+    return score_for_ka<uint64_t, uint64_t>(ka, gb);
+}
+
+MediumKernel pick_medium(KeyMode km) {
+    if (km == KeyMode::compact) return k_classify_medium<GB_DEFAULT, uint32_t, uint32_t>;
+    if (km == KeyMode::wide32) return k_classify_medium<GB_DEFAULT, uint64_t, uint32_t>;
+    return k_classify_medium<GB_DEFAULT, uint64_t, uint64_t>;
+}
+
+template <class LocT>
+LargeKernel pick_large_t(const SketchParams& sp) {
     const int r = sketch_r_for(sp.w);
     const bool k16 = sp.k == 16;
-    if (r == 4) return k16 ? k_classify_large<4, 16> : k_classify_large<4, 0>;
-    if (r == 8) return k16 ? k_classify_large<8, 16> : k_classify_large<8, 0>;
-    return k16 ? k_classify_large<16, 16> : k_classify_large<16, 0>;
+    if (r == 4) return k16 ? k_classify_large<4, 16, LocT> : k_classify_large<4, 0, LocT>;
+    if (r == 8) return k16 ? k_classify_large<8, 16, LocT> : k_classify_large<8, 0, LocT>;
+    return k16 ? k_classify_large<16, 16, LocT> : k_classify_large<16, 0, LocT>;
+}
+
+LargeKernel pick_large(const ClassifyDb& db) {
+    return db.jbits ? pick_large_t<uint32_t>(db.sp) : pick_large_t<uint64_t>(db.sp);
 }
 
 // Kernels and launch shapes of one launch set.
+using SortKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint32_t, const uint64_t*, const uint4*,
+                            uint32_t, uint32_t, uint32_t*, uint32_t*);
+
+// The sort path's size classes: queries of up to 256, 512 and 1024
+// gathered locations, each with its own kernel (E = 8, 16, 32 per lane).
+constexpr int N_SORT_CLASSES = 3;
+constexpr uint32_t SORT_CLASS_MAX[N_SORT_CLASSES] = {256, 512, 1024};
+
 struct Geometry {
     LookupKernel kl;
     ScoreKernel ks;
     MediumKernel km;
     LargeKernel kb;
+    SortKernel kt[N_SORT_CLASSES];
+    bool sort;           // score by the sort path (else the hash path)
+    int n_sort;          // sort classes in use
     uint32_t list_cap;
-    size_t smem_l, smem_s, smem_m, per_warp_b;
-    uint32_t threads_l, threads_s, grid_l, grid_s, grid_m, blocks_b;
+    size_t smem_l, smem_s, smem_m, per_warp_b, smem_t[N_SORT_CLASSES];
+    uint32_t threads_l, threads_s, grid_l, grid_s, grid_m, blocks_b, grid_t[N_SORT_CLASSES];
 };
 
 cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratch& sc, Geometry* g) {
@@ -986,10 +1329,11 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     g->list_cap = WIN_A * db.sp.s;
     g->kl = pick_lookup(db.sp, t.probe_batch);
-    const bool compact = db.jbits != 0 && !t.wide_keys;
-    g->ks = pick_score(t.hist_slots, t.gather_batch, compact);
-    g->kb = pick_large(db.sp);
-    g->km = compact ? k_classify_medium<GB_DEFAULT, uint32_t> : k_classify_medium<GB_DEFAULT, uint64_t>;
+    const KeyMode km = key_mode(db, t);
+    const bool compact = km == KeyMode::compact;
+    g->ks = pick_score(t.hist_slots, t.gather_batch, km);
+    g->kb = pick_large(db);
+    g->km = pick_medium(km);
     g->smem_m = MED_WARPS * (compact ? scratch_bytes<uint16_t, uint32_t>(KM_SLOTS, g->list_cap, 0, 0)
                                      : scratch_bytes<uint16_t, uint64_t>(KM_SLOTS, g->list_cap, 0, 0));
     if ((e = cudaFuncSetAttribute(g->km, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_m)) != cudaSuccess)
@@ -1019,6 +1363,28 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     g->grid_s = (uint32_t)std::min<uint64_t>((c + t.score_warps - 1) / t.score_warps, (uint64_t)sms * occ_s);
     g->per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     g->blocks_b = std::max<uint32_t>(1, sc.large_warps / CLS_WARPS);
+    // sort path: only for 32-bit locations with compact keys
+    g->sort = compact && t.score_mode != SCORE_HASH;
+    g->n_sort = 0;
+    if (g->sort) {
+        const SortKernel kts[N_SORT_CLASSES] = {k_classify_sort<8>, k_classify_sort<16>, k_classify_sort<32>};
+        const size_t bytes[N_SORT_CLASSES] = {sort_warp_bytes<8>(g->list_cap), sort_warp_bytes<16>(g->list_cap),
+                                              sort_warp_bytes<32>(g->list_cap)};
+        for (int c2 = 0; c2 < N_SORT_CLASSES && SORT_CLASS_MAX[c2] <= t.sort_max; ++c2) {
+            g->kt[c2] = kts[c2];
+            g->smem_t[c2] = SORT_WARPS * bytes[c2];
+            if ((e = cudaFuncSetAttribute(kts[c2], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g->smem_t[c2])) !=
+                cudaSuccess)
+                return e;
+            int occ_t = 1;
+            if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_t, kts[c2], SORT_WARPS * 32, g->smem_t[c2])) !=
+                cudaSuccess)
+                return e;
+            g->grid_t[c2] = (uint32_t)std::min<uint64_t>((c + SORT_WARPS - 1) / SORT_WARPS,
+                                                         (uint64_t)sms * std::max(occ_t, 1));
+            g->n_sort = c2 + 1;
+        }
+    }
     return cudaSuccess;
 }
 
@@ -1064,10 +1430,22 @@ cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const Classify
     uint32_t* qc = queue_counters(sc);
     cudaError_t e = cudaMemsetAsync(qc + 2, 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    MC_LAUNCH("classify_score", s,
-              g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, sc.mid,
-                                                          qc + 2));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (g.sort) {
+        static const char* const names[N_SORT_CLASSES] = {"classify_sort256", "classify_sort512", "classify_sort1024"};
+        for (int c = 0; c < g.n_sort; ++c) {
+            const uint32_t h_lo = c ? SORT_CLASS_MAX[c - 1] : 0;
+            const uint32_t last = c == g.n_sort - 1;
+            MC_LAUNCH(names[c], s,
+                      g.kt[c]<<<g.grid_t[c], SORT_WARPS * 32, g.smem_t[c], s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist,
+                                                                                 sc.meta, h_lo, last, sc.mid, qc + 2));
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+    } else {
+        MC_LAUNCH("classify_score", s,
+                  g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta,
+                                                              sc.mid, qc + 2));
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     MC_LAUNCH("classify_medium", s,
               g.km<<<g.grid_m, MED_WARPS * 32, g.smem_m, s>>>(db, Q, q0, g.list_cap, sc.glist, sc.meta, sc.mid, qc + 2,
                                                              qc + 3, sc.ovf, qc));
@@ -1089,6 +1467,7 @@ uint32_t compact_key_bits(uint64_t n_targets, uint64_t max_windows) {
     if (n_targets == 0 || max_windows == 0) return 0;
     const uint32_t jb = std::max(1u, bits(max_windows - 1));
     const uint32_t tb = bits(n_targets - 1);
+    if (jb >= 32) return 0;  // one target of more than 2^31 windows: 64-bit locations
     if (jb + tb < 32) return jb;
     // 32 bits: usable unless the all-ones key (the empty-slot marker) is a
     // location; a sliding-window lookup of that key only ever meets empty
@@ -1104,7 +1483,8 @@ bool tuning_valid(const Tuning& t) {
         return false;
     };
     return in(t.hist_slots, {256, 512, 1024}) && in(t.probe_batch, {2, 4, 8}) && in(t.gather_batch, {4, 8, 16}) &&
-           in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4}) && t.wide_keys <= 1;
+           in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4}) && t.wide_keys <= 1 &&
+           in(t.score_mode, {SCORE_SORT, SCORE_HASH}) && in(t.sort_max, {256, 512, 1024});
 }
 
 uint32_t classify_default_large_warps() {
@@ -1150,7 +1530,7 @@ cudaError_t classify_enqueue(const ClassifyDb& db, const ClassifyQuery& Q, const
     for (uint32_t q0 = 0; q0 < Q.n_q; q0 += sc.chunk) {
         if ((e = launch_lookup(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
         if ((e = launch_score(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
-        n += 3;
+        n += 2 + (g.sort ? g.n_sort : 1);
         if (sc.chunk == 0) break;
     }
     if ((e = launch_large(g, db, Q, sc, s)) != cudaSuccess) return e;
@@ -1261,6 +1641,7 @@ cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, cons
             for (uint32_t gb : {4u, 8u, 16u}) {
                 for (uint32_t sw : {2u, 4u}) {
                     Tuning t = cur;
+                    t.score_mode = SCORE_HASH;
                     t.hist_slots = ka;
                     t.gather_batch = gb;
                     t.score_warps = sw;
@@ -1285,6 +1666,35 @@ cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, cons
                         bs = t;
                         first = false;
                     }
+                }
+            }
+        }
+        // the sort path, for each largest size class
+        if (db.jbits) {
+            for (uint32_t smax : {256u, 512u, 1024u}) {
+                Tuning t = cur;
+                t.score_mode = SCORE_SORT;
+                t.sort_max = smax;
+                t.wide_keys = 0;
+                Geometry g;
+                if ((e = geometry(db, t, sc, &g)) != cudaSuccess) goto done;
+                float ms = 0;
+                e = timed(
+                    [&]() -> cudaError_t {
+                        cudaError_t err;
+                        if ((err = cudaMemcpyAsync(qc, qc + 4, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) !=
+                            cudaSuccess)
+                            return err;
+                        if ((err = cudaMemsetAsync(qc + 1, 0, sizeof(uint32_t), s)) != cudaSuccess) return err;
+                        if ((err = launch_score(g, db, Q, sc, 0, s)) != cudaSuccess) return err;
+                        return launch_large(g, db, Q, sc, s);
+                    },
+                    &ms);
+                if (e != cudaSuccess) goto done;
+                if (records) records->push_back(TuneRecord{t, 1, ms});
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    bs = t;
                 }
             }
         }

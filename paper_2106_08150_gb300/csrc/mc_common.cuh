@@ -76,6 +76,52 @@ __host__ __device__ __forceinline__ uint32_t hash_h2_inverse(uint32_t y) {
     return y;
 }
 
+// ------------------------------------------------------- feature table
+// The condensed layout's feature table (Section 4.2 / 5.1: a single-value
+// hash table from a feature to its bucket) holds one 8-byte word per slot.
+// Features are placed by ordered linear probing in the order of h = h2(f):
+// the home slot of h is its top log_t bits, and the word in slot s holds
+//   count  (cbits bits, >= 1; 0 marks an empty slot),
+//   disp   (TAB_DBITS bits: s - home),
+//   low    (32 - log_t bits: the low bits of h),
+//   offset (the remaining bits: the bucket's first location).
+// The high bits of h are home = s - disp, so h is recovered exactly.
+constexpr uint32_t TAB_DBITS = 6;
+constexpr uint32_t TAB_MAX_DISP = (1u << TAB_DBITS) - 1;
+
+struct TableFmt {
+    uint32_t log_t;  // 1..32: slots = 2^log_t (plus padding)
+    uint32_t cbits;  // bits of the count field
+    __host__ __device__ __forceinline__ uint32_t lbits() const { return 32 - log_t; }
+    __host__ __device__ __forceinline__ uint32_t obits() const { return 64 - cbits - TAB_DBITS - lbits(); }
+    __host__ __device__ __forceinline__ uint64_t home(uint32_t h) const { return (uint64_t)(h >> lbits()); }
+    __host__ __device__ __forceinline__ uint64_t pack(uint64_t off, uint32_t h, uint32_t disp, uint32_t cnt) const {
+        const uint64_t low = (uint64_t)h & ((1ull << lbits()) - 1);
+        return (((off << lbits() | low) << TAB_DBITS | disp) << cbits) | cnt;
+    }
+    __host__ __device__ __forceinline__ uint32_t count(uint64_t e) const {
+        return (uint32_t)(e & ((1ull << cbits) - 1));
+    }
+    __host__ __device__ __forceinline__ uint32_t disp(uint64_t e) const {
+        return (uint32_t)(e >> cbits) & TAB_MAX_DISP;
+    }
+    __host__ __device__ __forceinline__ uint64_t offset(uint64_t e) const {
+        return e >> (cbits + TAB_DBITS + lbits());
+    }
+    // h2 value of the (non-empty) word e found in slot s
+    __host__ __device__ __forceinline__ uint32_t key(uint64_t e, uint64_t s) const {
+        const uint64_t low = (e >> (cbits + TAB_DBITS)) & ((1ull << lbits()) - 1);
+        return (uint32_t)(((s - disp(e)) << lbits()) | low);
+    }
+};
+
+// Bits of the count field for a bucket cap.
+__host__ __device__ inline uint32_t count_bits(uint32_t cap) {
+    uint32_t b = 1;
+    while ((1ull << b) <= cap) ++b;
+    return b;
+}
+
 // ------------------------------------------------------ windows, lanes
 // Windows of a sequence of length L (k-mer starts 0, stride, 2 stride, ...).
 __host__ __device__ __forceinline__ uint64_t num_windows(uint64_t L, uint32_t k, uint32_t stride) {

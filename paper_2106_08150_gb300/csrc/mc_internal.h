@@ -98,24 +98,31 @@ struct FinalizeOut {
     uint64_t n_keys = 0;
     uint64_t n_kept = 0;
     uint64_t overflow_keys = 0;
-    uint64_t* locs = nullptr;  // n_kept, (target << 32) | window
-    uint4* table = nullptr;         // table_len entries {h2, count, offset lo, offset hi}
+    void* locs = nullptr;        // n_kept locations (encoding: loc_bytes)
+    uint64_t* table = nullptr;   // table_len packed words (TableFmt)
     uint64_t table_len = 0;
     uint64_t table_bytes = 0;
-    uint32_t log_t = 0;
+    TableFmt fmt{1, 1};
     uint32_t max_probe = 0;
+    bool table_full = false;     // no table format can hold the layout
 };
 
+// Location encoding of a database: jbits > 0 = 32-bit words target << jbits
+// | window (every target and window id fits; the all-ones word is never a
+// location), 0 = 64-bit words target << 32 | window.
+__host__ __device__ inline uint32_t loc_bytes(uint32_t jbits) { return jbits ? 4u : 8u; }
+
 // Condensed layout from sorted pairs: keep the first `cap` pairs of each
-// feature, convert global windows to (target, window), build the ordered
-// linear-probing feature table.  wbase: n_targets+1 global window bases.
+// feature, convert global windows to (target, window) locations in the
+// jbits encoding, build the ordered linear-probing feature table.  wbase:
+// n_targets+1 global window bases.
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
-                           uint32_t n_targets, FinalizeOut* out, cudaStream_t s);
+                           uint32_t n_targets, uint32_t jbits, FinalizeOut* out, cudaStream_t s);
 
 // The (h2 << 32 | global window) pairs of a finalized layout, in layout
 // order (out has n_kept entries).
-cudaError_t reconstruct_pairs(const uint4* table, uint64_t table_len, const uint64_t* locs, const uint32_t* wbase,
-                              uint64_t* out, cudaStream_t s);
+cudaError_t reconstruct_pairs(const uint64_t* table, uint64_t table_len, TableFmt fmt, const void* locs, uint32_t jbits,
+                              const uint32_t* wbase, uint64_t* out, cudaStream_t s);
 
 // Taxonomy: depth per node and lineage rows lin[x * stride + d].
 cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* depth, uint32_t* max_depth,
@@ -123,18 +130,20 @@ cudaError_t taxonomy_depths(const uint32_t* parent, uint32_t n_taxa, uint32_t* d
 cudaError_t taxonomy_lineage(const uint32_t* parent, uint32_t n_taxa, const uint32_t* depth, uint32_t* lin,
                              uint32_t stride, cudaStream_t s);
 
-// Dump support: entries of the table whose feature is in [lo, hi).
-cudaError_t dump_select(const uint4* table, uint64_t table_len, uint64_t lo, uint64_t hi, uint32_t* keys,
-                        uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel, cudaStream_t s);
-cudaError_t dump_gather(const uint64_t* locs, const uint64_t* src_off, const uint32_t* counts, const uint64_t* dst_off,
-                        uint64_t n, uint64_t* out, cudaStream_t s);
+// Dump support: entries of the table whose feature is in [lo, hi), and
+// their buckets as 64-bit locations (target << 32 | window).
+cudaError_t dump_select(const uint64_t* table, uint64_t table_len, TableFmt fmt, uint64_t lo, uint64_t hi,
+                        uint32_t* keys, uint64_t* offs, uint32_t* counts, uint64_t cap, unsigned long long* n_sel,
+                        cudaStream_t s);
+cudaError_t dump_gather(const void* locs, uint32_t jbits, const uint64_t* src_off, const uint32_t* counts,
+                        const uint64_t* dst_off, uint64_t n, uint64_t* out, cudaStream_t s);
 
 // --------------------------------------------------------- mc_classify.cu
 struct ClassifyDb {
-    const uint4* table;
-    uint32_t log_t;
+    const uint64_t* table;  // packed feature-table words
+    TableFmt fmt;
     uint32_t max_probe;
-    const uint64_t* locs;
+    const void* locs;       // locations, 32-bit words when jbits > 0, else 64-bit
     const uint32_t* taxon_of_target;
     uint32_t n_targets;
     const uint32_t* lineage;
@@ -143,8 +152,8 @@ struct ClassifyDb {
     uint32_t n_taxa;
     SketchParams sp;
     // > 0: every (target, window) of the database fits 32 bits as
-    // target << jbits | window without being all ones (compact histogram
-    // keys); 0: 64-bit keys
+    // target << jbits | window without being all ones: the locations are
+    // stored in that form and the histograms can key by it; 0: 64-bit
     uint32_t jbits;
 };
 
@@ -183,10 +192,11 @@ struct ClassifyQuery {
 };
 
 // Launch shape of the classification kernels (mc_tuning).
+constexpr uint32_t SCORE_SORT = 1, SCORE_HASH = 2;
 struct Tuning {
-    uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps, wide_keys;
+    uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps, wide_keys, score_mode, sort_max;
 };
-constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4, 0};
+constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4, 0, SCORE_SORT, 1024};
 bool tuning_valid(const Tuning& t);
 
 // Device scratch of one classify launch set for up to n_q_cap queries.

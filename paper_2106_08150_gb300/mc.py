@@ -50,7 +50,8 @@ class mc_db_stats_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ["n_targets", "n_windows", "n_pairs", "n_keys", "n_locations", "overflow_keys", "dropped_locations",
                  "table_slots", "max_probe", "device_bytes"]] + \
-               [("load_factor", ctypes.c_double), ("finalized", ctypes.c_uint32), ("max_depth", ctypes.c_uint32)]
+               [("load_factor", ctypes.c_double), ("finalized", ctypes.c_uint32), ("max_depth", ctypes.c_uint32),
+                ("loc_bytes", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class mc_batch(ctypes.Structure):
@@ -61,7 +62,8 @@ class mc_batch(ctypes.Structure):
 
 class mc_tuning(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint32) for n in
-                ["hist_slots", "probe_batch", "gather_batch", "lookup_warps", "score_warps", "wide_keys"]]
+                ["hist_slots", "probe_batch", "gather_batch", "lookup_warps", "score_warps", "wide_keys", "score_mode",
+                 "sort_max"]]
 
     def as_dict(self) -> dict:
         return {n: getattr(self, n) for n, _ in self._fields_}

@@ -31,7 +31,7 @@ def test_header_is_plain_c(mc):
 
 
 def test_version_and_status_strings(mc):
-    assert mc.mc_version() == 1
+    assert mc.mc_version() == 2
     lib = ctypes.CDLL(mc.LIB_PATH)
     lib.mc_status_string.restype = ctypes.c_char_p
     assert lib.mc_status_string(0) == b"MC_OK"

@@ -90,13 +90,20 @@ def test_batches_match_per_batch_calls_and_oracle(mc, setup):
     _assert_same(got, [ol, oh, ot])
 
 
+# score_mode 1 = sort path (the default for 32-bit locations), 2 = hash path;
+# the expected results come from the default shape, so every hash-path shape
+# is also checked against the sort path
 TUNINGS = [
     dict(),
-    dict(hist_slots=256, probe_batch=2, gather_batch=4, lookup_warps=4, score_warps=2),
-    dict(hist_slots=1024, probe_batch=8, gather_batch=16, lookup_warps=8, score_warps=4),
-    dict(hist_slots=256, gather_batch=16, score_warps=4),
+    dict(sort_max=256),
+    dict(sort_max=512, probe_batch=8, lookup_warps=4),
+    dict(score_mode=1, sort_max=1024, probe_batch=2),
+    dict(score_mode=2),
+    dict(score_mode=2, hist_slots=256, probe_batch=2, gather_batch=4, lookup_warps=4, score_warps=2),
+    dict(score_mode=2, hist_slots=1024, probe_batch=8, gather_batch=16, lookup_warps=8, score_warps=4),
+    dict(score_mode=2, hist_slots=256, gather_batch=16, score_warps=4),
     dict(wide_keys=1),
-    dict(hist_slots=256, probe_batch=2, gather_batch=4, score_warps=2, wide_keys=1),
+    dict(score_mode=2, hist_slots=256, probe_batch=2, gather_batch=4, score_warps=2, wide_keys=1),
 ]
 
 
@@ -124,7 +131,7 @@ def test_every_tuning_gives_the_same_results(mc, setup, t):
 def test_invalid_tuning_is_rejected(mc, setup):
     w, db, batches = setup
     for bad in [dict(hist_slots=300), dict(probe_batch=3), dict(gather_batch=32), dict(lookup_warps=16),
-                dict(score_warps=8)]:
+                dict(score_warps=8), dict(score_mode=3), dict(sort_max=300)]:
         with pytest.raises(mc.McError) as e:
             mc.mc_db_set_tuning(db.handle, mc.tuning(**bad))
         assert e.value.code == mc.MC_ERR_ARG
@@ -138,7 +145,7 @@ def test_plan_replays_new_batch_sets(mc, setup):
     total = sum(b.nq for b in dbs)
     plan = mc.Plan(db.handle, cp, max_batches=len(dbs), max_queries=total)
     try:
-        assert plan.kernels == 4  # lookup, score, medium path, large path
+        assert plan.kernels == 6  # lookup, three sort-path size classes, medium path, large path
         for subset in [list(range(len(dbs))), [3, 0, 5], [7], list(range(len(dbs)))[::-1], []]:
             for b in dbs:
                 b.reset()
@@ -206,7 +213,7 @@ def test_autotune_picks_a_valid_setting_with_equal_results(mc, setup):
     dbs = [DevBatch(mc, *b[:3]) for b in batches]
     want = [_per_batch(mc, db, cp, b) for b in dbs]
     best, rec = mc.mc_autotune(db.handle, cp, [b.desc for b in dbs], reps=2)
-    assert len(rec) == 6 + 18
+    assert len(rec) == 6 + 18 + 3  # lookup shapes, hash-path shapes, sort-path size limits
     assert {r[0] for r in rec} == {0, 1} and all(r[2] > 0 for r in rec)
     bt = best.as_dict()
     assert bt["hist_slots"] in (256, 512, 1024) and bt["probe_batch"] in (2, 4, 8)

@@ -312,6 +312,35 @@ def test_medium_and_large_histogram_paths(mc):
     db.free()
 
 
+def test_wide_location_database_matches_oracle(mc):
+    """Target and window ids that do not fit 32 bits together (2^17 + 1
+    short targets and one target of 66,372 windows): the database stores
+    64-bit locations instead of 32-bit ones, and the dump, the counters and
+    the classification must still equal the oracle's."""
+    big, big_o = synth.iid_genomes(17, [7_500_000])
+    n_small = (1 << 17) + 1
+    small, small_o = synth.iid_genomes(18, [24] * n_small, stream_base=0xD000000000)
+    genomes = np.concatenate([small, big])
+    goffs = np.concatenate([small_o, small_o[-1] + big_o[1:]]).astype(np.uint64)
+    n_t = n_small + 1
+    # taxonomy: root -> 64 genera -> targets
+    parent = np.concatenate([[0], np.zeros(64, np.uint32), 1 + np.arange(n_t) % 64]).astype(np.uint32)
+    taxon = np.arange(65, 65 + n_t, dtype=np.uint32)
+    p = dict(k=16, sketch_size=16, window_len=128, window_stride=113, bucket_cap=254)
+    db = gpu_build(mc, genomes, goffs, parent, taxon, **p)
+    odb = _oracle_db(genomes, goffs, p)
+    try:
+        assert db.stats()["loc_bytes"] == 8
+        _assert_dump_equal(mc, db, odb)
+        _assert_stats_equal(db, odb)
+        reads, roffs, qoffs, _ = synth.simulate_reads(19, 3000, big, big_o, paired=True, len_lo=150, len_hi=150,
+                                                      sub=0.01, frag_b=300.0, frag_sd_abs=30.0)
+        _check_classify(mc, db, odb, parent, taxon, reads, roffs, qoffs, m=4, hits_min=4, lca_band_pct=10,
+                        max_insert=390)
+    finally:
+        db.free()
+
+
 def test_query_beyond_window_limit_reports_capacity(mc, tiny):
     w = tiny
     db = gpu_build(mc, w.genomes, w.goffs, w.parent, w.taxon_of_target, **w.db_params)
