@@ -205,6 +205,11 @@ def kernel_source_hash(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
+# scoring kernels and their block of mc_classify_debug's per-kernel counters
+SCORE_KERNELS = {"classify_score": 0, "classify_sort256": 1, "classify_sort512": 2, "classify_sort1024": 3,
+                 "classify_medium": 4, "classify_large": 5}
+
+
 def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
     """Algorithmic HBM bytes of ALL launches of `kernel` in one step: every
     input the kernel needs read once and every output written once, random
@@ -231,9 +236,12 @@ def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:
     if kernel == "classify_lookup":
         # bases + offsets, one 32 B table sector per feature, bucket list + metadata out
         return reads_in + 32.0 * float(ctr[0]) + 8.0 * float(ctr[4]) + 16.0 * w.n_queries
-    if kernel == "classify_score":
-        # metadata + bucket list in, the 32 B sectors of every gathered bucket, 12 B of outputs
-        return 16.0 * w.n_queries + 8.0 * float(ctr[4]) + 32.0 * float(ctr[5]) + 12.0 * w.n_queries
+    if kernel in SCORE_KERNELS:
+        # the queries this kernel finished: metadata + bucket list in, the 32 B
+        # sectors of every gathered bucket, 12 B of outputs
+        k = SCORE_KERNELS[kernel]
+        q, found, sect = (float(ctr[7 + 3 * k + i]) for i in range(3))
+        return (16.0 + 12.0) * q + 8.0 * found + 32.0 * sect
     return None
 
 
@@ -325,21 +333,22 @@ def run_gpu(args, rank, world, local_rank):
         db.free()  # synchronises the database stream
         return db
 
-    # untimed: database statistics and classify counters for the roofline
+    # untimed: database statistics, the launch shape of the classify kernels
+    # (the autotuner on the first 2^20 pairs; any shape gives the same
+    # labels) and the classify counters of that shape, for the roofline
     db = mc.Database.create(w.parent, stream=stream, **w.db_params)
     db.add_targets(g, go, w.taxon_of_target)
     db.finalize()
     st = db.stats()
-    ctr = torch.zeros(7, dtype=torch.int64, device=dev)
-    mc.mc_classify_debug(db.handle, cp, w.n_seq, r, ro, nq, qo, label, hits, top, None, ctr, stream=stream)
-    mc.mc_classify_status(db.handle, stream)
-    ctr = ctr.cpu().numpy()
-    # launch shape of the classify kernels: the autotuner on the first 2^20
-    # pairs (any shape gives the same labels)
     n_s = min(nq, 1 << 20)
     sample = [mc.batch(int(w.qoffs[n_s]), r, ro, qo[: n_s + 1], label, hits, top)]
     if not args.no_autotune:
         tuned, tune_rec = mc.mc_autotune(db.handle, cp, sample, reps=2)
+        mc.mc_db_set_tuning(db.handle, tuned)
+    ctr = torch.zeros(mc.MC_DEBUG_COUNTERS, dtype=torch.int64, device=dev)
+    mc.mc_classify_debug(db.handle, cp, w.n_seq, r, ro, nq, qo, label, hits, top, None, ctr, stream=stream)
+    mc.mc_classify_status(db.handle, stream)
+    ctr = ctr.cpu().numpy()
     db.free()
     torch.cuda.synchronize()
 
@@ -499,7 +508,7 @@ def run_gpu(args, rank, world, local_rank):
     rand_roof = {"read16_gbs": rand[16], "read32_gbs": rand[32], "unit": "GB/s",
                  "note": "best of 6 shapes of random aligned reads of 16 / 32 bytes, 8 GiB buffer; the classify "
                          "kernels' algorithmic bytes count 32-byte sectors, so they are compared with read32_gbs"}
-    for kname in ("classify_lookup", "classify_score"):
+    for kname in ["classify_lookup", *SCORE_KERNELS]:
         if kname in kernels:
             b = algorithmic_bytes(kname, w, st, ctr)
             per = kernels[kname]["launches"] / args.steps
@@ -525,7 +534,10 @@ def run_gpu(args, rank, world, local_rank):
         "classify_counters": {"features": int(ctr[0]), "locations": int(ctr[1]), "distinct_locations": int(ctr[2]),
                               "large_path_queries": int(ctr[3]), "medium_path_queries": int(ctr[6]),
                               "features_found": int(ctr[4]),
-                              "bucket_sectors": int(ctr[5])},
+                              "bucket_sectors": int(ctr[5]),
+                              "per_kernel": {k: {"queries": int(ctr[7 + 3 * i]), "found": int(ctr[8 + 3 * i]),
+                                                 "sectors": int(ctr[9 + 3 * i])}
+                                             for k, i in SCORE_KERNELS.items() if int(ctr[7 + 3 * i])}},
         "roofline": roof,
         "random_access_roofline": rand_roof,
         "e2e": e2e,
@@ -612,7 +624,7 @@ def run_batched(args, w, dev, stream):
                    for x, y in zip(rx, ox))
 
     # untimed: counters of all batches and a per-kernel trace of one launch set
-    ctr = torch.zeros(7, dtype=torch.int64, device=dev)
+    ctr = torch.zeros(mc.MC_DEBUG_COUNTERS, dtype=torch.int64, device=dev)
     for (n_seq, nq, seq, offs, qo), o in zip(ins, out):
         if nq:
             mc.mc_classify_debug(db.handle, cp, n_seq, seq, offs, nq, qo, *o, None, ctr, stream=stream)

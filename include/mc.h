@@ -154,6 +154,65 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
  * mc_db_finalize calls return MC_ERR_STATE. */
 int mc_db_finalize(mc_db* db);
 
+/* ---------------------------------------------------------------------
+ * Databases partitioned by target (Section 4.3: the reference targets are
+ * split over several GPUs, each builds and queries a database of its own
+ * targets, Section 4.2: and the top candidates of the partitions are
+ * merged).  A shard holds a contiguous range of global target ids, given
+ * in ascending order: shard 0 the first targets, shard 1 the next, and so
+ * on.  The cap smallest locations of a feature over all targets are then
+ * those of the earlier shards first, so shard s keeps at most
+ * bucket_cap - prior(f) of its own locations of feature f, prior(f) being
+ * f's locations in shards 0..s-1.  Built that way the shards together hold
+ * exactly the database of all targets, and merged classification equals
+ * the single-database result.  (The paper caps each partition on its own,
+ * which keeps more locations than one database would; this library
+ * enforces the single-database cap.)  Protocol: every shard adds its
+ * targets, calls mc_db_feature_counts, the lists of the earlier shards are
+ * exchanged (e.g. an all-gather), and each shard calls
+ * mc_db_finalize_after with them; queries go to every shard
+ * (mc_classify_debug with a cands buffer) and mc_merge_candidates merges
+ * the lists. */
+
+/* Features of the targets added so far (before the first finalize) and
+ * how often each occurs, for the shards after this one: keys (device out,
+ * max_keys entries) receives the features' keys in the library's internal
+ * order (ascending; opaque values to pass to mc_db_finalize_after), counts
+ * (device out) their location counts clamped to bucket_cap.  *n_keys
+ * (host) = the number of features; MC_ERR_CAPACITY (nothing written) if it
+ * exceeds max_keys.  Sorts the pending pairs in place (mc_db_finalize then
+ * skips that sort).  MC_ERR_STATE after a finalize.  Synchronises the
+ * database stream. */
+int mc_db_feature_counts(mc_db* db, uint64_t max_keys, uint32_t* keys, uint32_t* counts, uint64_t* n_keys);
+
+/* mc_db_finalize for a shard: the n_lists lists (host arrays of device
+ * pointers keys[l], counts[l] and host sizes n_keys[l]; each from
+ * mc_db_feature_counts of an earlier shard) give prior(f) = the sum of f's
+ * counts, and feature f keeps at most max(0, bucket_cap - prior(f)) of this
+ * database's locations.  With n_lists = 0 it is mc_db_finalize.
+ * overflow_keys (mc_db_stats) counts the features whose locations here and
+ * in the prior lists exceed bucket_cap.  Errors as mc_db_finalize. */
+int mc_db_finalize_after(mc_db* db, uint32_t n_lists, const uint32_t* const* keys, const uint32_t* const* counts,
+                         const uint64_t* n_keys);
+
+/* Merges the top-m candidate lists of n_lists shards per query into the
+ * global top m and labels each query exactly as mc_classify does.
+ *  db         : any database with the taxonomy (its lineage table is used).
+ *  params     : max_candidates = m of the lists; hits_min, lca_band_pct as
+ *               for mc_classify (max_insert unused).
+ *  cands      : host array of n_lists device pointers, each n_queries x m x
+ *               {score, target, first window, last window} as written by
+ *               mc_classify_debug (targets are the shard's local ids).
+ *  target_base: host, n_lists global ids of each shard's target 0.
+ *  taxon_of_target : device, n_targets taxa of the global targets.
+ *  label, hits, top_target (nullable), cands_out (nullable, n_queries x m
+ *  x 4, global targets): device outputs.
+ * Synchronises `stream`. */
+int mc_merge_candidates(const mc_db* db, const mc_classify_params* params, uint32_t n_queries, uint32_t n_lists,
+                        const uint32_t* const* cands, const uint32_t* target_base, const uint32_t* taxon_of_target,
+                        uint32_t n_targets, uint32_t* label, uint32_t* hits, uint32_t* top_target,
+                        uint32_t* cands_out, void* stream);
+
 /* Classifies queries (Section 4.2 query phase, Section 5.2 query steps 1-8).
  *  params    : host.
  *  n_seq     : number of sequences (mates) in seq.
@@ -492,10 +551,15 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
 /* mc_classify with test outputs.  cands (device out, nullable):
  * n_queries x max_candidates x {score, target, first window, last window}
  * of the top candidates (unused slots: score 0, target MC_NO_TARGET).
- * counters (device out, nullable, 7 x uint64, accumulated): features looked
- * up, locations gathered, distinct locations, queries sent to the
- * large-histogram path, features found, 32-byte sectors of the gathered
- * buckets, queries finished on the medium-histogram path. */
+ * counters (device out, nullable, MC_DEBUG_COUNTERS x uint64, accumulated):
+ * [0] features looked up, [1] locations gathered, [2] distinct locations,
+ * [3] queries sent to the large-histogram path, [4] features found, [5]
+ * 32-byte sectors of the gathered buckets, [6] queries finished on the
+ * medium-histogram path; then per scoring kernel k (0 hash-path score
+ * kernel, 1-3 sort path for up to 256/512/1024 locations, 4 medium path,
+ * 5 large path): [7 + 3k] queries it finished, [8 + 3k] their found
+ * features, [9 + 3k] their 32-byte sectors. */
+#define MC_DEBUG_COUNTERS 25
 int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                       const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,

@@ -48,6 +48,10 @@ def _load():
         lib.oracle_sketch.restype = u64
         lib.oracle_db_build.argtypes = [u32, u32, u32, u32, u32, u32, vp, vp, vp, u64, i32]
         lib.oracle_db_build.restype = vp
+        lib.oracle_db_build_shard.argtypes = [u32, u32, u32, u32, u32, u32, vp, vp, vp, u64, i32, u32, vp, vp, u64]
+        lib.oracle_db_build_shard.restype = vp
+        lib.oracle_db_feature_counts.argtypes, lib.oracle_db_feature_counts.restype = [vp, vp, vp], u64
+        lib.oracle_merge.argtypes = [u32, vp, u32, u32, u32, vp, vp, u32, u32, vp, vp, vp, vp]
         lib.oracle_db_free.argtypes = [vp]
         lib.oracle_db_stats.argtypes = [vp, vp]
         lib.oracle_db_lookup.argtypes, lib.oracle_db_lookup.restype = [vp, u32, vp, u64], u64
@@ -114,17 +118,34 @@ class DB:
     """Oracle database: feature -> sorted locations (target<<32 | window), capped."""
 
     def __init__(self, seq, offs, *, k, sketch_size, window_len, window_stride, bucket_cap,
-                 key_filter=None, n_threads: int = 1, **_):
+                 key_filter=None, n_threads: int = 1, target_base: int = 0, prior=None, **_):
+        """A database of the targets seq/offs.  For one partition (shard) of
+        a partitioned database: target_base = the global id of its first
+        target, prior = (features ascending, counts) of the earlier shards'
+        locations (see oracle_db_build_shard)."""
         lib = _load()
         self._seq = _u8(seq)
         self._offs = np.ascontiguousarray(offs, dtype=np.uint64)
         self.params = dict(k=k, sketch_size=sketch_size, window_len=window_len, window_stride=window_stride,
                            bucket_cap=bucket_cap)
         kf = None if key_filter is None else np.unique(np.ascontiguousarray(key_filter, dtype=np.uint32))
-        self._h = lib.oracle_db_build(k, sketch_size, window_len, window_stride, bucket_cap,
-                                      len(self._offs) - 1, _p(self._seq), _p(self._offs), _p(kf),
-                                      0 if kf is None else len(kf), n_threads)
+        pk = pc = None
+        if prior is not None:
+            pk = np.ascontiguousarray(prior[0], dtype=np.uint32)
+            pc = np.ascontiguousarray(prior[1], dtype=np.uint32)
+        self._h = lib.oracle_db_build_shard(k, sketch_size, window_len, window_stride, bucket_cap,
+                                            len(self._offs) - 1, _p(self._seq), _p(self._offs), _p(kf),
+                                            0 if kf is None else len(kf), n_threads, target_base, _p(pk), _p(pc),
+                                            0 if pk is None else len(pk))
         self._lib = lib
+
+    def feature_counts(self):
+        """(features ascending, location counts before the cap clamped to the cap)."""
+        n = self._lib.oracle_db_feature_counts(self._h, None, None)
+        keys = np.zeros(max(1, n), dtype=np.uint32)
+        counts = np.zeros(max(1, n), dtype=np.uint32)
+        self._lib.oracle_db_feature_counts(self._h, _p(keys), _p(counts))
+        return keys[:n], counts[:n]
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -186,3 +207,23 @@ def sws(n_mates: int, span_sum: int, max_insert: int, k: int, stride: int) -> in
 def lca(parent, a: int, b: int) -> int:
     parent = np.ascontiguousarray(parent, dtype=np.uint32)
     return int(_load().oracle_lca(len(parent), _p(parent), a, b))
+
+
+def merge(lists, parent, taxon_of_target, *, max_candidates, hits_min, lca_band_pct, **_):
+    """Merged classification of a partitioned database: lists = per-shard
+    candidate arrays [n_q, m, 4] with global target ids.  Returns (label,
+    hits, top_target, cands[n_q, m, 4])."""
+    lib = _load()
+    arrs = [np.ascontiguousarray(x, dtype=np.uint32) for x in lists]
+    nq = arrs[0].shape[0] if arrs else 0
+    m = max_candidates
+    ptrs = (ctypes.c_void_p * max(1, len(arrs)))(*[a.ctypes.data for a in arrs])
+    parent = np.ascontiguousarray(parent, dtype=np.uint32)
+    tax = np.ascontiguousarray(taxon_of_target, dtype=np.uint32)
+    label = np.zeros(max(1, nq), dtype=np.uint32)
+    hits = np.zeros(max(1, nq), dtype=np.uint32)
+    top = np.zeros(max(1, nq), dtype=np.uint32)
+    cands = np.zeros((max(1, nq), m, 4), dtype=np.uint32)
+    lib.oracle_merge(len(arrs), ptrs, m, nq, len(parent), _p(parent), _p(tax), hits_min, lca_band_pct, _p(label),
+                     _p(hits), _p(top), _p(cands))
+    return label[:nq], hits[:nq], top[:nq], cands[:nq]

@@ -129,6 +129,8 @@ struct DB {
     uint64_t overflow_keys = 0; // features that had more than cap locations
     // Section 4.1: each feature maps to a bucket of locations, limited to cap.
     std::unordered_map<uint32_t, std::vector<uint64_t>> buckets;
+    // locations of each feature before the cap (for the shards after this one)
+    std::unordered_map<uint32_t, uint64_t> uncapped;
 };
 
 struct TargetSketches {
@@ -208,9 +210,22 @@ uint64_t oracle_sketch(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint
 // which lets tests check sampled keys of a large database.
 // Sketching may use n_threads threads (per-target work); the insertion is
 // one thread in target order.
-void* oracle_db_build(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint32_t cap, uint32_t n_targets,
-                      const char* seq, const uint64_t* offs, const uint32_t* key_filter, uint64_t n_filter,
-                      int n_threads) {
+//
+// Partitioned databases (Section 4.3: the targets are split over GPUs, each
+// building a database of its own targets): target_base is the global id of
+// this shard's first target, so its locations carry global ids.  The
+// shards hold contiguous id ranges in order, so the cap smallest locations
+// of a feature over all targets are the earlier shards' first; with the
+// earlier shards' location counts prior(f) (prior_keys ascending), this
+// shard keeps at most max(0, cap - prior(f)) of its own, and the shards
+// together hold exactly the database of all targets.  (Reading: the paper
+// caps each partition on its own; the single-database cap is kept here so
+// that sharded results equal the unsharded ones.)  overflow_keys counts
+// the features whose locations here and in the prior exceed cap.
+void* oracle_db_build_shard(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint32_t cap, uint32_t n_targets,
+                            const char* seq, const uint64_t* offs, const uint32_t* key_filter, uint64_t n_filter,
+                            int n_threads, uint32_t target_base, const uint32_t* prior_keys,
+                            const uint32_t* prior_counts, uint64_t n_prior) {
     DB* db = new DB;
     db->p = Params{k, s, w, stride, cap};
     db->n_targets = n_targets;
@@ -243,20 +258,50 @@ void* oracle_db_build(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint3
             for (uint32_t f : sk[t].win[j]) {
                 db->n_pairs++;
                 if (key_filter && !std::binary_search(key_filter, key_filter + n_filter, f)) continue;
-                db->buckets[f].push_back(make_loc(t, (uint32_t)j));
+                db->buckets[f].push_back(make_loc(target_base + t, (uint32_t)j));
             }
         }
         sk[t].win.clear();
         sk[t].win.shrink_to_fit();
     }
-    for (auto& kv : db->buckets) {
-        std::sort(kv.second.begin(), kv.second.end());
-        if (kv.second.size() > cap) {
-            db->overflow_keys++;
-            kv.second.resize(cap);
+    for (auto it = db->buckets.begin(); it != db->buckets.end();) {
+        std::vector<uint64_t>& b = it->second;
+        std::sort(b.begin(), b.end());
+        db->uncapped[it->first] = b.size();
+        uint64_t prior = 0;
+        if (n_prior) {
+            const uint32_t* p = std::lower_bound(prior_keys, prior_keys + n_prior, it->first);
+            if (p != prior_keys + n_prior && *p == it->first) prior = prior_counts[p - prior_keys];
         }
+        const uint64_t limit = prior >= cap ? 0 : cap - prior;
+        if (prior + b.size() > cap) db->overflow_keys++;
+        if (b.size() > limit) b.resize(limit);
+        if (b.empty()) it = db->buckets.erase(it);
+        else ++it;
     }
     return db;
+}
+
+void* oracle_db_build(uint32_t k, uint32_t s, uint32_t w, uint32_t stride, uint32_t cap, uint32_t n_targets,
+                      const char* seq, const uint64_t* offs, const uint32_t* key_filter, uint64_t n_filter,
+                      int n_threads) {
+    return oracle_db_build_shard(k, s, w, stride, cap, n_targets, seq, offs, key_filter, n_filter, n_threads, 0,
+                                 nullptr, nullptr, 0);
+}
+
+// Features of a database and their location counts before the cap, clamped
+// to cap (what a later shard needs), ascending.  Returns the number of
+// features; with null outputs it only counts.
+uint64_t oracle_db_feature_counts(void* h, uint32_t* keys, uint32_t* counts) {
+    DB* db = (DB*)h;
+    std::vector<uint32_t> ks;
+    for (auto& kv : db->uncapped) ks.push_back(kv.first);
+    std::sort(ks.begin(), ks.end());
+    for (size_t i = 0; i < ks.size() && keys; ++i) {
+        keys[i] = ks[i];
+        counts[i] = (uint32_t)std::min<uint64_t>(db->uncapped[ks[i]], db->p.cap);
+    }
+    return ks.size();
 }
 
 void oracle_db_free(void* h) { delete (DB*)h; }
@@ -337,6 +382,68 @@ struct Cand { uint32_t score, t, j0, j1; };
 uint64_t oracle_sws(uint32_t n_mates, uint64_t span_sum, uint32_t max_insert, uint32_t k, uint32_t stride) {
     uint64_t span = n_mates <= 1 ? span_sum : std::max<uint64_t>(span_sum, max_insert);
     return span >= k ? (span - k + stride - 1) / stride + 1 : 0;
+}
+
+// Step 6 of classification (Section 4.2 and Section 6.5 hit threshold), on
+// the top-m candidates in order (score descending, target ascending): no
+// candidate or top score < hits_min -> unclassified; else the candidates
+// within lca_band_pct percent of the top score are "close": one -> its
+// target's taxon, several -> the LCA of their taxa.  hits = top score (0
+// without candidates), top_target = top target (NO_TAXON without).
+void assign_label(const std::vector<Cand>& cands, uint32_t n_taxa, const uint32_t* parent,
+                  const uint32_t* taxon_of_target, uint32_t hits_min, uint32_t lca_band_pct, uint32_t* label,
+                  uint32_t* hits, uint32_t* top_target) {
+    if (cands.empty()) {
+        *label = NO_TAXON;
+        *hits = 0;
+        if (top_target) *top_target = NO_TAXON;
+        return;
+    }
+    const Cand& top = cands[0];
+    *hits = top.score;
+    if (top_target) *top_target = top.t;
+    if (top.score < hits_min) {
+        *label = NO_TAXON;
+        return;
+    }
+    std::vector<uint32_t> close;
+    for (const Cand& c : cands)
+        if (100ull * c.score >= (uint64_t)(100 - lca_band_pct) * top.score) close.push_back(c.t);
+    uint32_t lab = taxon_of_target[close[0]];
+    for (size_t i = 1; i < close.size(); ++i) lab = oracle_lca(n_taxa, parent, lab, taxon_of_target[close[i]]);
+    *label = lab;
+}
+
+// Merge of partitioned results (Section 4.2: with a partitioned database
+// the top candidates of every partition are merged).  lists[l] holds, per
+// query, m candidates {score, global target, j0, j1} (score 0 = unused) of
+// partition l.  A target lives in one partition, so the global top m are
+// the m best of the union (score descending, target ascending), labelled
+// by the same rule as oracle_classify.  cands_out (optional) as there.
+void oracle_merge(uint32_t n_lists, const uint32_t* const* lists, uint32_t m, uint32_t n_q, uint32_t n_taxa,
+                  const uint32_t* parent, const uint32_t* taxon_of_target, uint32_t hits_min, uint32_t lca_band_pct,
+                  uint32_t* label, uint32_t* hits, uint32_t* top_target, uint32_t* cands_out) {
+    for (uint32_t q = 0; q < n_q; ++q) {
+        std::vector<Cand> all;
+        for (uint32_t l = 0; l < n_lists; ++l)
+            for (uint32_t i = 0; i < m; ++i) {
+                const uint32_t* c = lists[l] + ((uint64_t)q * m + i) * 4;
+                if (c[0]) all.push_back(Cand{c[0], c[1], c[2], c[3]});
+            }
+        std::sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) {
+            if (a.score != b.score) return a.score > b.score;
+            return a.t < b.t;
+        });
+        if (all.size() > m) all.resize(m);
+        if (cands_out)
+            for (uint32_t i = 0; i < m; ++i) {
+                uint32_t* o = cands_out + ((uint64_t)q * m + i) * 4;
+                if (i < all.size()) { o[0] = all[i].score; o[1] = all[i].t; o[2] = all[i].j0; o[3] = all[i].j1; }
+                else { o[0] = 0; o[1] = NO_TAXON; o[2] = 0; o[3] = 0; }
+            }
+        assign_label(all, n_taxa, parent, taxon_of_target, hits_min, lca_band_pct, &label[q], &hits[q],
+                     top_target ? &top_target[q] : nullptr);
+    }
 }
 
 // Read classification (Section 4.2 query phase; Section 5.2 query steps 1-8).
@@ -436,25 +543,8 @@ void oracle_classify(void* h, uint32_t n_taxa, const uint32_t* parent, const uin
             stats[3 * (uint64_t)q + 1] = found.size();
             stats[3 * (uint64_t)q + 2] = stat.size();
         }
-        if (cands.empty()) {
-            label[q] = NO_TAXON;
-            hits[q] = 0;
-            if (top_target) top_target[q] = NO_TAXON;
-            return;
-        }
-        const Cand& top = cands[0];
-        hits[q] = top.score;
-        if (top_target) top_target[q] = top.t;
-        if (top.score < hits_min) {
-            label[q] = NO_TAXON;
-            return;
-        }
-        std::vector<uint32_t> close;
-        for (const Cand& c : cands)
-            if (100ull * c.score >= (uint64_t)(100 - lca_band_pct) * top.score) close.push_back(c.t);
-        uint32_t lab = taxon_of_target[close[0]];
-        for (size_t i = 1; i < close.size(); ++i) lab = oracle_lca(n_taxa, parent, lab, taxon_of_target[close[i]]);
-        label[q] = lab;
+        assign_label(cands, n_taxa, parent, taxon_of_target, hits_min, lca_band_pct, &label[q], &hits[q],
+                     top_target ? &top_target[q] : nullptr);
     };
     if (n_threads <= 1) {
         for (uint32_t q = 0; q < n_q; ++q) one(q);

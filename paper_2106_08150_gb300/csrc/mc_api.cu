@@ -164,6 +164,7 @@ struct mc_db {
     // additions not yet finalized
     DevBuf pending;  // u64 pairs
     uint64_t pending_n = 0, pending_real = 0;
+    bool pending_sorted = false;  // pending holds pending_real sorted pairs (mc_db_feature_counts)
     // published condensed layout: locations in the loc_jbits encoding
     // (mc::loc_bytes), packed feature-table words in format fmt
     DevBuf locs, table;
@@ -485,6 +486,7 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
         MC_CU(cudaStreamSynchronize(s));
         db->pending_n += npairs;
         db->pending_real += real;
+        db->pending_sorted = false;
     }
     db->n_windows += nw;
     db->n_targets += n_targets;
@@ -492,7 +494,13 @@ int mc_db_add_targets(mc_db* db, uint32_t n_targets, const char* seq, const uint
     return MC_OK;
 }
 
-int mc_db_finalize(mc_db* db) {
+}  // extern "C"
+
+namespace {
+// mc_db_finalize with an optional prior (sharded builds): n_lists lists of
+// earlier shards' feature counts.
+int finalize_impl(mc_db* db, uint32_t n_lists, const uint32_t* const* keys, const uint32_t* const* counts,
+                  const uint64_t* list_n) {
     g_err[0] = 0;
     if (!db) return fail(MC_ERR_ARG, "db is NULL");
     if (db->failed) return fail(MC_ERR_STATE, "an earlier mc_db_finalize failed after consuming the added targets");
@@ -502,8 +510,9 @@ int mc_db_finalize(mc_db* db) {
     const uint64_t n_total = n_old + db->pending_n;
     const uint64_t n_real = n_old + db->pending_real;
     // sort input: previously kept pairs (sorted) followed by the new pairs;
-    // without previous pairs the pending buffer itself is sorted in place.
-    // Until the sort starts a failure leaves the pending pairs as they were.
+    // without previous pairs the pending buffer itself is sorted in place
+    // (or already is, after mc_db_feature_counts).  Until the sort starts a
+    // failure leaves the pending pairs as they were.
     DevBuf a, b;
     const bool a_is_pending = n_old == 0;
     if (a_is_pending) {
@@ -524,22 +533,34 @@ int mc_db_finalize(mc_db* db) {
         if (!a_is_pending) release(db, a);
         release(db, b);
     };
-    if (!grab(db, b, n_total * 8)) {
-        release_tmp();
-        return fail(MC_ERR_OOM, "finalize: allocation failed");
+    if (!(a_is_pending && db->pending_sorted)) {
+        if (!grab(db, b, n_total * 8)) {
+            release_tmp();
+            return fail(MC_ERR_OOM, "finalize: allocation failed");
+        }
+        cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)a.p, (uint64_t*)b.p, n_total, n_real, s);
+        if (e != cudaSuccess) {
+            release_tmp();
+            // the sort allocates its scratch before it touches the pairs
+            if (e != cudaErrorMemoryAllocation) db->failed = true;
+            return cuda_fail(e, "finalize: sort");
+        }
+        release(db, b);
     }
-    cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)a.p, (uint64_t*)b.p, n_total, n_real, s);
-    if (e != cudaSuccess) {
-        release_tmp();
-        // the sort allocates its scratch before it touches the pairs
-        if (e != cudaErrorMemoryAllocation) db->failed = true;
-        return cuda_fail(e, "finalize: sort");
+    uint64_t prior_over = 0;
+    if (n_lists) {
+        cudaError_t e = mc::apply_prior(db->mem, (uint64_t*)a.p, n_real, db->cap, n_lists, keys, counts, list_n,
+                                        &prior_over, s);
+        if (e != cudaSuccess) {
+            release_tmp();
+            db->failed = true;
+            return cuda_fail(e, "finalize: prior counts");
+        }
     }
-    release(db, b);
     mc::FinalizeOut fo;
     const uint32_t jbits = mc::compact_key_bits(db->n_targets, db->max_target_windows);
-    e = mc::finalize_pairs(db->mem, (const uint64_t*)a.p, n_real, db->cap, (const uint32_t*)db->wbase.p,
-                           db->n_targets, jbits, &fo, s);
+    cudaError_t e = mc::finalize_pairs(db->mem, (const uint64_t*)a.p, n_real, db->cap, (const uint32_t*)db->wbase.p,
+                                       db->n_targets, jbits, &fo, s);
     release_tmp();
     if (e != cudaSuccess) {
         db->failed = true;
@@ -558,18 +579,62 @@ int mc_db_finalize(mc_db* db) {
     db->loc_jbits = jbits;
     db->n_pairs += db->pending_real;
     db->pending_n = db->pending_real = 0;
+    db->pending_sorted = false;
     db->n_kept = fo.n_kept;
     db->n_keys = fo.n_keys;
     db->table_len = fo.table_len;
     db->fmt = fo.fmt;
     db->max_probe = fo.max_probe;
-    db->overflow_keys = fo.overflow_keys;
+    db->overflow_keys = fo.overflow_keys + prior_over;
     db->dirty = false;
     db->has_table = true;
     ++db->epoch;
     MC_CU(cudaEventRecord(db->ready, s));
     MC_CU(cudaStreamSynchronize(s));
     return MC_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int mc_db_finalize(mc_db* db) { return finalize_impl(db, 0, nullptr, nullptr, nullptr); }
+
+int mc_db_feature_counts(mc_db* db, uint64_t max_keys, uint32_t* keys, uint32_t* counts, uint64_t* n_keys) {
+    g_err[0] = 0;
+    if (!db || !n_keys) return fail(MC_ERR_ARG, "NULL argument");
+    *n_keys = 0;
+    if (db->failed) return fail(MC_ERR_STATE, "an earlier mc_db_finalize failed");
+    if (db->has_table) return fail(MC_ERR_STATE, "mc_db_feature_counts: the database was finalized already");
+    cudaStream_t s = db->stream;
+    if (!db->pending_sorted && db->pending_n) {
+        DevBuf b;
+        if (!grab(db, b, db->pending_n * 8)) return fail(MC_ERR_OOM, "mc_db_feature_counts: allocation failed");
+        cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)db->pending.p, (uint64_t*)b.p, db->pending_n,
+                                       db->pending_real, s);
+        release(db, b);
+        if (e != cudaSuccess) {
+            if (e != cudaErrorMemoryAllocation) db->failed = true;
+            return cuda_fail(e, "mc_db_feature_counts: sort");
+        }
+        // the first pending_real pairs are sorted, the rest is stale
+        db->pending_n = db->pending_real;
+        db->pending_sorted = true;
+    }
+    uint64_t n = 0;
+    MC_CU(mc::feature_counts(db->mem, (const uint64_t*)db->pending.p, db->pending_real, db->cap, max_keys, keys,
+                             counts, &n, s));
+    *n_keys = n;
+    if (n > max_keys) return fail(MC_ERR_CAPACITY, "mc_db_feature_counts: %llu features", (unsigned long long)n);
+    return MC_OK;
+}
+
+int mc_db_finalize_after(mc_db* db, uint32_t n_lists, const uint32_t* const* keys, const uint32_t* const* counts,
+                         const uint64_t* n_keys) {
+    g_err[0] = 0;
+    if (n_lists && (!keys || !counts || !n_keys)) return fail(MC_ERR_ARG, "NULL prior list arrays");
+    for (uint32_t l = 0; l < n_lists; ++l)
+        if (n_keys[l] && (!keys[l] || !counts[l])) return fail(MC_ERR_ARG, "prior list %u has NULL arrays", l);
+    return finalize_impl(db, n_lists, keys, counts, n_keys);
 }
 
 static int classify_impl(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
@@ -683,6 +748,28 @@ int mc_debug_stall_next_sort(uint64_t limit_ns) {
     if (limit_ns < 1000000ull || limit_ns > 2000000000ull)
         return fail(MC_ERR_ARG, "mc_debug_stall_next_sort: limit must be in 1e6..2e9 ns");
     mc::arm_sort_stall(limit_ns);
+    return MC_OK;
+}
+
+int mc_merge_candidates(const mc_db* db, const mc_classify_params* params, uint32_t n_queries, uint32_t n_lists,
+                        const uint32_t* const* cands, const uint32_t* target_base, const uint32_t* taxon_of_target,
+                        uint32_t n_targets, uint32_t* label, uint32_t* hits, uint32_t* top_target,
+                        uint32_t* cands_out, void* stream) {
+    g_err[0] = 0;
+    if (!db) return fail(MC_ERR_ARG, "db is NULL");
+    int rc = check_cls(params);
+    if (rc) return rc;
+    if (n_queries == 0) return MC_OK;
+    if (!label || !hits || (n_lists && (!cands || !target_base)) || (n_targets && !taxon_of_target))
+        return fail(MC_ERR_ARG, "NULL argument");
+    std::vector<mc::MergeList> lists(n_lists);
+    for (uint32_t l = 0; l < n_lists; ++l) {
+        if (!cands[l]) return fail(MC_ERR_ARG, "candidate list %u is NULL", l);
+        lists[l] = mc::MergeList{cands[l], target_base[l]};
+    }
+    MC_CU(mc::merge_candidates(db->mem, db_view(db), taxon_of_target, n_targets, lists.data(), n_lists, n_queries,
+                               params->max_candidates, params->hits_min, params->lca_band_pct, label, hits, top_target,
+                               cands_out, (cudaStream_t)stream));
     return MC_OK;
 }
 

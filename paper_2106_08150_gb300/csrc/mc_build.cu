@@ -22,6 +22,7 @@
 // accesses of the whole database life are the lookups of the query path.
 #include <atomic>
 #include <cstdio>
+#include <vector>
 
 #include "mc_internal.h"
 #include "mc_sketch.cuh"
@@ -590,18 +591,26 @@ __device__ __forceinline__ uint32_t hk_of(uint64_t v) { return (uint32_t)(v >> 3
 
 // In the sorted pair array, e starts a feature's run if its predecessor has
 // another feature; e is kept (rank in its run < cap) unless the pair cap
-// places earlier has the same feature (runs are contiguous).
+// places earlier has the same feature (runs are contiguous).  Sentinel
+// pairs may end a run (the part a sharded build gives up to earlier
+// shards, finalize_after): they are neither kept nor starts, and a pair
+// after one starts a new run.
+__device__ __forceinline__ bool same_feature(uint64_t x, uint32_t hk) {
+    return x != SENTINEL_PAIR && hk_of(x) == hk;
+}
+
 __device__ __forceinline__ void fin_flags(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap, uint64_t e,
                                           uint64_t& v, bool& st, bool& kept, bool& over) {
     st = kept = over = false;
     if (e >= n) return;
     v = a[e];
+    if (v == SENTINEL_PAIR) return;
     const uint32_t hk = hk_of(v);
-    st = e == 0 || hk_of(a[e - 1]) != hk;
-    const bool dropped = e >= cap && hk_of(a[e - cap]) == hk;
+    st = e == 0 || !same_feature(a[e - 1], hk);
+    const bool dropped = e >= cap && same_feature(a[e - cap], hk);
     kept = !dropped;
     // the first dropped pair of an overflowing run: the pair cap earlier starts the run
-    over = dropped && (e == cap || hk_of(a[e - cap - 1]) != hk);
+    over = dropped && (e == cap || !same_feature(a[e - cap - 1], hk));
 }
 
 // Tile sums of kept pairs and run starts.
@@ -791,11 +800,10 @@ __global__ void __launch_bounds__(BT) k_tab_dispmax(const uint32_t* __restrict__
 }
 
 // slot(k) = k + max(prefix, inclusive max of home - k); writes the packed
-// word.  A displacement beyond the word's field sets *too_far (the host then
+// word (count = kept locations, koff[k + 1] - koff[k]).  A displacement beyond the word's field sets *too_far (the host then
 // retries with a larger table).
 __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ khk, const uint64_t* __restrict__ koff,
-                                                 const uint64_t* __restrict__ kstart, uint64_t n, uint32_t cap,
-                                                 TableFmt fmt, const int64_t* __restrict__ tpre, uint64_t n_tiles,
+                                                 uint64_t n, TableFmt fmt, const int64_t* __restrict__ tpre, uint64_t n_tiles,
                                                  uint64_t* __restrict__ table, unsigned int* max_disp,
                                                  unsigned int* too_far) {
     __shared__ int64_t sm[NWARP];
@@ -816,8 +824,7 @@ __global__ void __launch_bounds__(BT) k_tab_emit(const uint32_t* __restrict__ kh
             carry = max(carry, tot);
             if (in_range) {
                 uint64_t slot = (uint64_t)((int64_t)e + inc);
-                uint64_t len = kstart[e + 1] - kstart[e];
-                uint32_t cnt = (uint32_t)(len < cap ? len : cap);
+                const uint32_t cnt = (uint32_t)(koff[e + 1] - koff[e]);  // kept locations (<= cap)
                 const uint64_t disp = slot - home;
                 if (disp > TAB_MAX_DISP) atomicMax(too_far, 1u);
                 table[slot] = fmt.pack(koff[e], hk, (uint32_t)(disp & TAB_MAX_DISP), cnt);
@@ -874,7 +881,7 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
         return cudaSuccess;
     }
     Tmp<unsigned char> locs(mem, n_kept * loc_bytes(jbits), s);
-    Tmp<uint64_t> koff(mem, n_keys, s), kstart(mem, n_keys + 1, s);
+    Tmp<uint64_t> koff(mem, n_keys + 1, s), kstart(mem, n_keys + 1, s);
     Tmp<uint32_t> khk(mem, n_keys, s);
     if (!locs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
@@ -883,6 +890,7 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
                                               locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+        if ((e = cudaMemcpyAsync(koff.ptr + n_keys, &n_kept, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
     }
     const uint64_t ktiles = (n_keys + FIN_TILE - 1) / FIN_TILE;
     Tmp<int64_t> kt_max(mem, ktiles + 1, s), kt_pre(mem, ktiles + 1, s);
@@ -910,8 +918,8 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
         if ((e = cudaMemsetAsync(ctr.ptr + 1, 0, 2 * sizeof(unsigned long long), s)) != cudaSuccess) return e;
         if (n_keys > 0) {
             MC_LAUNCH("tab_emit", s,
-                      k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, kstart.ptr, n_keys, cap, fmt,
-                                                                 kt_pre.ptr, ktiles, table.ptr,
+                      k_tab_emit<<<grid_for(ktiles), BT, 0, s>>>(khk.ptr, koff.ptr, n_keys, fmt, kt_pre.ptr, ktiles,
+                                                                 table.ptr,
                                                                  (unsigned int*)(ctr.ptr + 1),
                                                                  (unsigned int*)(ctr.ptr + 2)));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -936,6 +944,178 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     out->max_probe = (uint32_t)(host_ctr[1] & 0xFFFFFFFFull);
     out->fmt = fmt;
     out->locs = locs.release();
+    return cudaSuccess;
+}
+
+// ------------------------------------------------------- sharded builds
+// Section 4.3 partitions the reference targets over GPUs.  A shard holds a
+// contiguous range of target ids, so every location of an earlier shard is
+// smaller than every location of a later one, and the cap smallest
+// locations of a feature over all shards are: those of the earlier shards
+// first.  A shard therefore keeps at most cap - prior(f) of its own
+// locations of feature f, prior(f) = f's locations in the earlier shards
+// (clamped to cap), and the union of the shards equals the database of all
+// targets.
+namespace {
+
+// Run starts of sorted pairs: keys and start indices at the scanned
+// positions tkeys (exclusive prefix of each tile's run starts).
+__global__ void __launch_bounds__(BT) k_run_emit(const uint64_t* __restrict__ a, uint64_t n,
+                                                 const uint64_t* __restrict__ tkeys, uint64_t n_tiles,
+                                                 uint32_t* __restrict__ khk, uint64_t* __restrict__ kstart) {
+    __shared__ uint32_t wsx[NWARP];
+    const int w = threadIdx.x >> 5;
+    const uint32_t lane = lane_id();
+    const uint32_t lt = lanemask_lt();
+    for (uint64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const uint64_t base = tile * FIN_TILE + (uint64_t)w * 32 * FIN_ITEMS + lane;
+        uint32_t smask = 0, ns = 0;
+        uint64_t v[FIN_ITEMS];
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            bool st, kept, over;
+            fin_flags(a, n, 0xFFFFFFFFu, base + (uint64_t)i * 32, v[i], st, kept, over);
+            smask |= (st ? 1u : 0u) << i;
+            ns += __popc(__ballot_sync(FULL_MASK, st));
+        }
+        if (lane == 0) wsx[w] = ns;
+        __syncthreads();
+        uint64_t kidx = tkeys[tile];
+        for (int i = 0; i < w; ++i) kidx += wsx[i];
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < FIN_ITEMS; ++i) {
+            const bool st = (smask >> i) & 1u;
+            const uint32_t bs = __ballot_sync(FULL_MASK, st);
+            if (st) {
+                const uint64_t my_s = kidx + __popc(bs & lt);
+                khk[my_s] = hk_of(v[i]);
+                kstart[my_s] = base + (uint64_t)i * 32;
+            }
+            kidx += __popc(bs);
+        }
+    }
+}
+
+// counts[i] = min(cap, length of run i); kstart has n_runs + 1 entries.
+__global__ void k_run_counts(const uint64_t* __restrict__ kstart, uint64_t n_runs, uint32_t cap,
+                             uint32_t* __restrict__ counts) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_runs;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t len = kstart[i + 1] - kstart[i];
+        counts[i] = (uint32_t)(len < cap ? len : cap);
+    }
+}
+
+// One list of earlier shards' feature counts (keys ascending).
+struct PriorList {
+    const uint32_t* keys;
+    const uint32_t* counts;
+    uint64_t n;
+};
+
+// Per run (thread per run): prior = the run's feature counts in the prior
+// lists (binary search in each), limit = max(0, cap - prior); pairs of the
+// run beyond the limit become sentinels.  Counts features whose locations
+// together with the prior ones exceed cap.
+__global__ void k_prior_limits(uint64_t* __restrict__ a, const uint32_t* __restrict__ khk,
+                               const uint64_t* __restrict__ kstart, uint64_t n_runs, uint32_t cap,
+                               const PriorList* __restrict__ lists, uint32_t n_lists,
+                               unsigned long long* overflow) {
+    unsigned long long n_over = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n_runs;
+         i += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t key = khk[i];
+        uint64_t prior = 0;
+        for (uint32_t l = 0; l < n_lists; ++l) {
+            const PriorList L = lists[l];
+            uint64_t lo = 0, hi = L.n;  // first index with keys >= key
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) >> 1;
+                if (L.keys[mid] < key) lo = mid + 1; else hi = mid;
+            }
+            if (lo < L.n && L.keys[lo] == key) prior += L.counts[lo];
+        }
+        if (prior == 0) continue;  // the plain cap applies
+        const uint64_t len = kstart[i + 1] - kstart[i];
+        const uint64_t limit = prior >= cap ? 0 : cap - prior;
+        if (prior + len > cap) ++n_over;
+        for (uint64_t e = kstart[i] + limit; e < kstart[i] + len; ++e) a[e] = SENTINEL_PAIR;
+    }
+    for (int o = 16; o >= 1; o >>= 1) n_over += __shfl_xor_sync(FULL_MASK, n_over, o);
+    if (lane_id() == 0 && n_over) atomicAdd(overflow, n_over);
+}
+
+// Run starts of sorted pairs a[0..n): *n_runs, and (when keys != null and
+// the runs fit max) keys[i], kstart[i] (n_runs + 1 entries, kstart[n_runs]
+// = n) allocated by the caller.
+cudaError_t sorted_runs(const Mem& mem, const uint64_t* a, uint64_t n, uint64_t max, uint32_t* keys,
+                        uint64_t* kstart, uint64_t* n_runs, cudaStream_t s) {
+    cudaError_t e;
+    *n_runs = 0;
+    if (n == 0) return cudaSuccess;
+    const uint64_t tiles = (n + FIN_TILE - 1) / FIN_TILE;
+    Tmp<uint64_t> tkept(mem, tiles + 1, s), tkeys(mem, tiles + 1, s);
+    if (!tkept.ok() || !tkeys.ok()) return cudaErrorMemoryAllocation;
+    MC_LAUNCH("fin_count", s, k_fin_count<<<grid_for(tiles), BT, 0, s>>>(a, n, 0xFFFFFFFFu, tkept.ptr, tkeys.ptr, tiles));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = scan_exclusive_sum(mem, tkeys.ptr, tkeys.ptr, tiles, s)) != cudaSuccess) return e;
+    uint64_t total = 0;
+    if ((e = cudaMemcpyAsync(&total, tkeys.ptr + tiles, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *n_runs = total;
+    if (!keys || total > max) return cudaSuccess;
+    MC_LAUNCH("run_emit", s, k_run_emit<<<grid_for(tiles), BT, 0, s>>>(a, n, tkeys.ptr, tiles, keys, kstart));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaMemcpyAsync(kstart + total, &n, 8, cudaMemcpyHostToDevice, s);
+}
+}  // namespace
+
+cudaError_t feature_counts(const Mem& mem, const uint64_t* a, uint64_t n, uint32_t cap, uint64_t max, uint32_t* keys,
+                           uint32_t* counts, uint64_t* n_keys, cudaStream_t s) {
+    uint64_t runs = 0;
+    cudaError_t e = sorted_runs(mem, a, n, 0, nullptr, nullptr, &runs, s);
+    *n_keys = runs;
+    if (e != cudaSuccess || runs == 0 || runs > max || !keys || !counts) return e;
+    Tmp<uint64_t> kstart(mem, runs + 1, s);
+    if (!kstart.ok()) return cudaErrorMemoryAllocation;
+    uint64_t again = 0;
+    if ((e = sorted_runs(mem, a, n, runs, keys, kstart.ptr, &again, s)) != cudaSuccess) return e;
+    MC_LAUNCH("run_counts", s,
+              k_run_counts<<<grid_for((runs + BT - 1) / BT), BT, 0, s>>>(kstart.ptr, runs, cap, counts));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t apply_prior(const Mem& mem, uint64_t* a, uint64_t n, uint32_t cap, uint32_t n_lists,
+                        const uint32_t* const* keys, const uint32_t* const* counts, const uint64_t* list_n,
+                        uint64_t* overflow, cudaStream_t s) {
+    cudaError_t e;
+    *overflow = 0;
+    if (n == 0 || n_lists == 0) return cudaSuccess;
+    uint64_t runs = 0;
+    if ((e = sorted_runs(mem, a, n, 0, nullptr, nullptr, &runs, s)) != cudaSuccess) return e;
+    Tmp<uint32_t> khk(mem, runs, s);
+    Tmp<uint64_t> kstart(mem, runs + 1, s);
+    Tmp<PriorList> dl(mem, n_lists, s);
+    Tmp<unsigned long long> ctr(mem, 1, s);
+    if (!khk.ok() || !kstart.ok() || !dl.ok() || !ctr.ok()) return cudaErrorMemoryAllocation;
+    std::vector<PriorList> hl(n_lists);
+    for (uint32_t l = 0; l < n_lists; ++l) hl[l] = PriorList{keys[l], counts[l], list_n[l]};
+    uint64_t again = 0;
+    if ((e = sorted_runs(mem, a, n, runs, khk.ptr, kstart.ptr, &again, s)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(dl.ptr, hl.data(), n_lists * sizeof(PriorList), cudaMemcpyHostToDevice, s)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaMemsetAsync(ctr.ptr, 0, 8, s)) != cudaSuccess) return e;
+    MC_LAUNCH("prior_limits", s,
+              k_prior_limits<<<grid_for((runs + BT - 1) / BT), BT, 0, s>>>(a, khk.ptr, kstart.ptr, runs, cap, dl.ptr,
+                                                                           n_lists, ctr.ptr));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    unsigned long long h = 0;
+    if ((e = cudaMemcpyAsync(&h, ctr.ptr, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    *overflow = h;
     return cudaSuccess;
 }
 

@@ -220,8 +220,14 @@ __device__ __forceinline__ Scratch<CntT, KeyT> carve(unsigned char* base, uint32
 }
 
 struct Counters {
-    unsigned long long features = 0, locations = 0, distinct = 0, found = 0, sectors = 0;
+    unsigned long long features = 0, locations = 0, distinct = 0, found = 0, sectors = 0, queries = 0;
 };
+
+// Per-kernel counter block of mc_classify_debug: kernel k (0 hash score,
+// 1-3 sort path 256/512/1024, 4 medium path, 5 large path) adds the
+// queries it finished, their found buckets and their 32-byte sectors at
+// counters[7 + 3k ...].
+constexpr int KC_SCORE = 0, KC_MEDIUM = 4, KC_LARGE = 5;
 
 // Batch holding query q of a multi-batch launch: the last batch whose
 // first query is <= q (empty batches share their first query number with
@@ -692,6 +698,7 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
         ctr.features += n_feat;
         ctr.found += n_list;
         ctr.sectors += n_sect;
+        ++ctr.queries;
     }
     return r;
 }
@@ -699,7 +706,7 @@ __device__ __forceinline__ int process_query(const ClassifyDb& db, const Classif
 // counters: [0] features looked up, [1] locations gathered, [2] distinct
 // locations, [3] queries on the large path, [4] features found, [5] 32-byte
 // sectors of the gathered buckets, [6] queries finished on the medium path.
-__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, const Counters& c) {
+__device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, const Counters& c, int kidx) {
     const unsigned long long sect = c.sectors;
     if (Q.counters && lane_id() == 0) {
         atomicAdd(Q.counters + 0, c.features);
@@ -707,6 +714,9 @@ __device__ __forceinline__ void flush_counters(const ClassifyQuery& Q, const Cou
         atomicAdd(Q.counters + 2, c.distinct);
         atomicAdd(Q.counters + 4, c.found);
         atomicAdd(Q.counters + 5, sect);
+        atomicAdd(Q.counters + 7 + 3 * kidx, c.queries);
+        atomicAdd(Q.counters + 8 + 3 * kidx, c.found);
+        atomicAdd(Q.counters + 9 + 3 * kidx, sect);
     }
 }
 
@@ -865,10 +875,11 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
             ctr.features += meta_feat(mt);
             ctr.found += mt.x;
             ctr.sectors += mt.w;
+            ++ctr.queries;
         }
         __syncwarp();
     }
-    flush_counters(Q, ctr);
+    flush_counters(Q, ctr, KC_SCORE);
 }
 
 // Medium path: the chunk's queries whose histogram did not fit the main
@@ -910,11 +921,12 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
             ctr.features += meta_feat(mt);
             ctr.found += mt.x;
             ctr.sectors += mt.w;
+            ++ctr.queries;
             ++n_medium;
         }
         __syncwarp();
     }
-    flush_counters(Q, ctr);
+    flush_counters(Q, ctr, KC_MEDIUM);
     if (Q.counters && lane == 0 && n_medium) atomicAdd(Q.counters + 6, n_medium);
 }
 
@@ -1186,9 +1198,10 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db
         ctr.features += meta_feat(mt);
         ctr.found += mt.x;
         ctr.sectors += mt.w;
+        ++ctr.queries;
         __syncwarp();
     }
-    flush_counters(Q, ctr);
+    flush_counters(Q, ctr, E == 8 ? 1 : (E == 16 ? 2 : 3));
 }
 
 // Large path: queries queued by the shared-memory path, one warp each, with
@@ -1220,7 +1233,7 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 4) k_classify_large(ClassifyDb
         }
         __syncwarp();
     }
-    flush_counters(Q, ctr);
+    flush_counters(Q, ctr, KC_LARGE);
     if (Q.counters && lane_id() == 0 && n_large) atomicAdd(Q.counters + 3, n_large);
 }
 
@@ -1461,6 +1474,94 @@ cudaError_t launch_large(const Geometry& g, const ClassifyDb& db, const Classify
 }
 
 }  // namespace
+
+// ------------------------------------------------------------ shard merge
+// Sharded classification (Section 4.2: with the database partitioned over
+// GPUs, the top candidates of every partition are merged).  One thread per
+// query merges the per-shard top-m lists into the global top m (score
+// descending, global target ascending; a target lives in one shard, so no
+// candidate spans lists) and labels it as query_score does.
+namespace {
+__global__ void k_merge_candidates(ClassifyDb db, const uint32_t* __restrict__ taxon, uint32_t n_targets,
+                                   const MergeList* __restrict__ lists, uint32_t n_lists, uint32_t n_q, uint32_t m,
+                                   uint32_t hits_min, uint32_t band, uint32_t* __restrict__ label,
+                                   uint32_t* __restrict__ hits, uint32_t* __restrict__ top_target,
+                                   uint32_t* __restrict__ cands_out) {
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < n_q; q += gridDim.x * blockDim.x) {
+        uint32_t ts[MAX_M], tt[MAX_M], tj0[MAX_M], tj1[MAX_M];
+#pragma unroll
+        for (int a = 0; a < MAX_M; ++a) {
+            ts[a] = 0;
+            tt[a] = 0xFFFFFFFFu;
+            tj0[a] = tj1[a] = 0;
+        }
+        for (uint32_t l = 0; l < n_lists; ++l) {
+            const MergeList L = lists[l];
+            for (uint32_t i = 0; i < m; ++i) {
+                const uint4 c = *reinterpret_cast<const uint4*>(L.cands + ((uint64_t)q * m + i) * 4);
+                if (c.x == 0) break;  // the rest of this list is empty
+                uint32_t cs = c.x, ct = L.base + c.y, c0 = c.z, c1 = c.w;
+                // one bubbling insertion pass (score descending, target ascending)
+#pragma unroll
+                for (int a = 0; a < MAX_M; ++a) {
+                    if ((uint32_t)a < m && (cs > ts[a] || (cs == ts[a] && ct < tt[a]))) {
+                        const uint32_t xs = ts[a], xt = tt[a], x0 = tj0[a], x1 = tj1[a];
+                        ts[a] = cs;
+                        tt[a] = ct;
+                        tj0[a] = c0;
+                        tj1[a] = c1;
+                        cs = xs;
+                        ct = xt;
+                        c0 = x0;
+                        c1 = x1;
+                    }
+                }
+            }
+        }
+        uint32_t lab = NO_TAXON;
+        const uint32_t h = ts[0];
+        if (h > 0 && h >= hits_min) {
+            lab = tt[0] < n_targets ? taxon[tt[0]] : NO_TAXON;
+            const uint64_t bar = (uint64_t)(100 - band) * h;
+#pragma unroll
+            for (int a = 1; a < MAX_M; ++a) {
+                if ((uint32_t)a >= m || ts[a] == 0 || 100ull * ts[a] < bar) break;
+                lab = lca2(db, lab, tt[a] < n_targets ? taxon[tt[a]] : NO_TAXON);
+            }
+        }
+        label[q] = lab;
+        hits[q] = h;
+        if (top_target) top_target[q] = h ? tt[0] : 0xFFFFFFFFu;
+        if (cands_out) {
+#pragma unroll
+            for (int a = 0; a < MAX_M; ++a)
+                if ((uint32_t)a < m)
+                    *reinterpret_cast<uint4*>(cands_out + ((uint64_t)q * m + a) * 4) =
+                        make_uint4(ts[a], ts[a] ? tt[a] : 0xFFFFFFFFu, ts[a] ? tj0[a] : 0, ts[a] ? tj1[a] : 0);
+        }
+    }
+}
+}  // namespace
+
+cudaError_t merge_candidates(const Mem& mem, const ClassifyDb& db, const uint32_t* taxon, uint32_t n_targets,
+                             const MergeList* lists, uint32_t n_lists, uint32_t n_q, uint32_t m, uint32_t hits_min,
+                             uint32_t band, uint32_t* label, uint32_t* hits, uint32_t* top_target, uint32_t* cands_out,
+                             cudaStream_t s) {
+    if (n_q == 0) return cudaSuccess;
+    Tmp<MergeList> dl(mem, std::max<uint32_t>(n_lists, 1), s);
+    if (!dl.ok()) return cudaErrorMemoryAllocation;
+    cudaError_t e;
+    if (n_lists &&
+        (e = cudaMemcpyAsync(dl.ptr, lists, n_lists * sizeof(MergeList), cudaMemcpyHostToDevice, s)) != cudaSuccess)
+        return e;
+    const uint32_t grid = (uint32_t)std::min<uint64_t>((n_q + 255) / 256, (uint64_t)NUM_SMS_HINT * 8);
+    MC_LAUNCH("merge_candidates", s,
+              k_merge_candidates<<<grid, 256, 0, s>>>(db, taxon, n_targets, dl.ptr, n_lists, n_q, m, hits_min, band,
+                                                      label, hits, top_target, cands_out));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // the host list array is read by the copy above: wait for it before returning
+    return cudaStreamSynchronize(s);
+}
 
 uint32_t compact_key_bits(uint64_t n_targets, uint64_t max_windows) {
     auto bits = [](uint64_t x) { return x ? 64u - (uint32_t)__builtin_clzll(x) : 0u; };

@@ -119,6 +119,21 @@ __host__ __device__ inline uint32_t loc_bytes(uint32_t jbits) { return jbits ? 4
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
                            uint32_t n_targets, uint32_t jbits, FinalizeOut* out, cudaStream_t s);
 
+// Sharded builds (Section 4.3): distinct features of sorted pairs a[0..n)
+// (h2 keys ascending) with their counts clamped to cap; *n_keys = the
+// number of features, written only when they fit max.
+cudaError_t feature_counts(const Mem& mem, const uint64_t* a, uint64_t n, uint32_t cap, uint64_t max, uint32_t* keys,
+                           uint32_t* counts, uint64_t* n_keys, cudaStream_t s);
+// Turns into sentinels, in sorted pairs a[0..n), the pairs each feature
+// gives up to earlier shards: feature f keeps at most cap - prior(f) pairs,
+// prior(f) = the sum of f's counts in the n_lists device lists (keys
+// ascending, host arrays of device pointers).  *overflow = features whose
+// pairs together with the prior ones exceed cap (features without prior
+// pairs are left to the plain cap of finalize_pairs).
+cudaError_t apply_prior(const Mem& mem, uint64_t* a, uint64_t n, uint32_t cap, uint32_t n_lists,
+                        const uint32_t* const* keys, const uint32_t* const* counts, const uint64_t* list_n,
+                        uint64_t* overflow, cudaStream_t s);
+
 // The (h2 << 32 | global window) pairs of a finalized layout, in layout
 // order (out has n_kept entries).
 cudaError_t reconstruct_pairs(const uint64_t* table, uint64_t table_len, TableFmt fmt, const void* locs, uint32_t jbits,
@@ -241,6 +256,19 @@ constexpr uint32_t CLASSIFY_CHUNK = 1u << 20;  // queries per lookup/score round
 size_t classify_noalloc_bytes(uint32_t n_q, uint32_t sketch_size);
 cudaError_t classify_launch_noalloc(const ClassifyDb& db, const ClassifyQuery& q, const Tuning& t,
                                    unsigned char* scratch, size_t scratch_len, cudaStream_t s);
+
+// One shard's top-m lists (device, n_q x m x {score, target, j0, j1}) and
+// the global id of its target 0.
+struct MergeList {
+    const uint32_t* cands;
+    uint32_t base;
+};
+// Merges n_lists shards' top-m lists per query and labels the result
+// (taxon: device, n_targets global targets).  Synchronises `s`.
+cudaError_t merge_candidates(const Mem& mem, const ClassifyDb& db, const uint32_t* taxon, uint32_t n_targets,
+                             const MergeList* lists, uint32_t n_lists, uint32_t n_q, uint32_t m, uint32_t hits_min,
+                             uint32_t band, uint32_t* label, uint32_t* hits, uint32_t* top_target, uint32_t* cands_out,
+                             cudaStream_t s);
 
 // ------------------------------------------------------------- mc_api.cu
 // Records an error message for mc_last_error_string and returns `code`.

@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 MC_OK, MC_ERR_ARG, MC_ERR_STATE, MC_ERR_OOM, MC_ERR_TABLE_FULL, MC_ERR_TIMEOUT, MC_ERR_CUDA, MC_ERR_CAPACITY = range(8)
 MC_NO_TAXON = 0xFFFFFFFF
+MC_DEBUG_COUNTERS = 25  # entries of mc_classify_debug's counters
 MC_NO_TARGET = 0xFFFFFFFF
 MC_MAX_CANDIDATES = 8
 
@@ -113,6 +114,10 @@ _SIGS = {
     "mc_db_create": ([ctypes.POINTER(mc_db_params), _u32, _vp, _vp, ctypes.POINTER(_vp)], _i),
     "mc_db_add_targets": ([_vp, _u32, _vp, _vp, _vp, ctypes.POINTER(_u32)], _i),
     "mc_db_finalize": ([_vp], _i),
+    "mc_db_feature_counts": ([_vp, _u64, _vp, _vp, ctypes.POINTER(_u64)], _i),
+    "mc_db_finalize_after": ([_vp, _u32, ctypes.POINTER(_vp), ctypes.POINTER(_vp), ctypes.POINTER(_u64)], _i),
+    "mc_merge_candidates": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _u32, ctypes.POINTER(_vp),
+                             ctypes.POINTER(_u32), _vp, _u32, _vp, _vp, _vp, _vp, _vp], _i),
     "mc_classify": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp], _i),
     "mc_classify_debug": ([_vp, ctypes.POINTER(mc_classify_params), _u32, _vp, _vp, _u32, _vp, _vp, _vp, _vp, _vp,
                            _vp, _vp], _i),
@@ -244,6 +249,37 @@ def mc_db_add_targets(db: int, n_targets: int, seq, offs, taxon: np.ndarray) -> 
 
 def mc_db_finalize(db: int):
     _check(_lib.mc_db_finalize(db))
+
+
+def mc_db_feature_counts(db: int, keys=None, counts=None, max_keys: int = 0) -> int:
+    """Features of the pending targets and their counts (device uint32
+    buffers of max_keys entries); returns the number of features (nothing is
+    written when they do not fit: call with max_keys = 0 to size them)."""
+    n = _u64()
+    code = _lib.mc_db_feature_counts(db, max_keys, _ptr(keys), _ptr(counts), ctypes.byref(n))
+    if code not in (MC_OK, MC_ERR_CAPACITY) or (code == MC_ERR_CAPACITY and max_keys):
+        _check(code)
+    return n.value
+
+
+def mc_db_finalize_after(db: int, prior):
+    """prior: [(keys, counts, n)] of the earlier shards (device buffers)."""
+    n = len(prior)
+    keys = (_vp * max(1, n))(*[_ptr(k) for k, _, _ in prior])
+    cnts = (_vp * max(1, n))(*[_ptr(c) for _, c, _ in prior])
+    sizes = (_u64 * max(1, n))(*[int(x) for _, _, x in prior])
+    _check(_lib.mc_db_finalize_after(db, n, keys, cnts, sizes))
+
+
+def mc_merge_candidates(db: int, params: mc_classify_params, n_queries: int, cands, target_base, taxon_of_target,
+                        n_targets: int, label, hits, top_target=None, cands_out=None, stream=None):
+    """cands: device buffers (one per shard) as written by mc_classify_debug."""
+    n = len(cands)
+    lists = (_vp * max(1, n))(*[_ptr(c) for c in cands])
+    base = (_u32 * max(1, n))(*[int(b) for b in target_base])
+    _check(_lib.mc_merge_candidates(db, ctypes.byref(params), n_queries, n, lists, base, _ptr(taxon_of_target),
+                                    n_targets, _ptr(label), _ptr(hits), _ptr(top_target), _ptr(cands_out),
+                                    _stream(stream)))
 
 
 def mc_classify(db: int, params: mc_classify_params, n_seq: int, seq, offs, n_queries: int, qoffs, label, hits,

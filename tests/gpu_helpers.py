@@ -71,7 +71,7 @@ def gpu_classify(mc, db, reads, roffs, qoffs, with_cands=False, m=4, **cp):
     nq = len(qoffs) - 1
     d_r = dev(u8(reads)) if len(reads) else dev(np.zeros(1, np.uint8))
     cands = torch.zeros(max(1, nq * m * 4), dtype=torch.int32, device="cuda") if with_cands else None
-    counters = torch.zeros(7, dtype=torch.int64, device="cuda")
+    counters = torch.zeros(mc.MC_DEBUG_COUNTERS, dtype=torch.int64, device="cuda")
     label, hits, top = db.classify(d_r, dev(roffs), dev(qoffs), cands=cands, counters=counters,
                                    max_candidates=m, **cp)
     mc.mc_classify_status(db.handle)

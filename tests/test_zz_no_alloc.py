@@ -36,7 +36,7 @@ def test_noalloc_matches_classify_on_two_calls_in_a_row():
         ref = [torch.empty(nq, dtype=torch.int32, device="cuda") for _ in range(3)]
         mc.mc_classify(db.handle, cp, nq, d_r, d_ro, nq, d_qo, *ref)
         mc.mc_classify_status(db.handle)
-        counters = torch.zeros(7, dtype=torch.int64, device="cuda")
+        counters = torch.zeros(mc.MC_DEBUG_COUNTERS, dtype=torch.int64, device="cuda")
         dbg = [torch.empty(nq, dtype=torch.int32, device="cuda") for _ in range(3)]
         mc.mc_classify_debug(db.handle, cp, nq, d_r, d_ro, nq, d_qo, *dbg, None, counters)
         mc.mc_classify_status(db.handle)
