@@ -437,6 +437,8 @@ typedef struct mc_server_stats {
     uint64_t hbm_in_use, hbm_limit, hbm_peak;
     double p50_latency_s, p99_latency_s, max_latency_s;  /* over finished jobs */
     double busy_s;               /* from the first submission to the last completion */
+    double extension_mean_s, extension_max_s;  /* time of an applied extension (add + finalize,
+                                                  database stream idle at both ends) */
 } mc_server_stats;
 
 /* Creates a server over a finalized database.  The server owns the

@@ -507,46 +507,55 @@ int finalize_impl(mc_db* db, uint32_t n_lists, const uint32_t* const* keys, cons
     if (!db->dirty && db->has_table) return MC_OK;
     cudaStream_t s = db->stream;
     const uint64_t n_old = db->n_kept;
-    const uint64_t n_total = n_old + db->pending_n;
-    const uint64_t n_real = n_old + db->pending_real;
-    // sort input: previously kept pairs (sorted) followed by the new pairs;
-    // without previous pairs the pending buffer itself is sorted in place
-    // (or already is, after mc_db_feature_counts).  Until the sort starts a
-    // failure leaves the pending pairs as they were.
-    DevBuf a, b;
+    // 1. the new pairs are sorted (unless mc_db_feature_counts did it): the
+    // sort allocates its scratch before it touches the pairs, so a refused
+    // allocation leaves them as they were and the call can be repeated
+    if (!db->pending_sorted && db->pending_n) {
+        DevBuf b;
+        if (!grab(db, b, db->pending_n * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
+        cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)db->pending.p, (uint64_t*)b.p, db->pending_n,
+                                       db->pending_real, s);
+        release(db, b);
+        if (e != cudaSuccess) {
+            if (e != cudaErrorMemoryAllocation) db->failed = true;
+            return cuda_fail(e, "finalize: sort");
+        }
+        db->pending_n = db->pending_real;  // the first pending_real pairs are sorted, the rest is stale
+        db->pending_sorted = true;
+    }
+    const uint64_t n_new = db->pending_real;
+    const uint64_t n_real = n_old + n_new;
+    // 2. live extension (Section 4.1: new targets get the next ids, so every
+    // new location is larger than the stored ones): the stored pairs, in
+    // layout order, are already sorted; merging them with the new pairs
+    // gives the sorted pairs of the whole database without sorting the
+    // stored ones again.  Without a stored layout the new pairs are it.
+    DevBuf a;
     const bool a_is_pending = n_old == 0;
     if (a_is_pending) {
         a = db->pending;
     } else {
-        if (!within_budget(db, n_total * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
-        if (!grab(db, a, n_total * 8)) return fail(MC_ERR_OOM, "finalize: allocation failed");
+        DevBuf old;
+        if (!within_budget(db, (n_old + n_real) * 8)) return fail(MC_ERR_OOM, "finalize: hbm_budget exceeded");
+        if (!grab(db, old, n_old * 8) || !grab(db, a, n_real * 8)) {
+            release(db, old);
+            release(db, a);
+            return fail(MC_ERR_OOM, "finalize: allocation failed");
+        }
         cudaError_t e = mc::reconstruct_pairs((const uint64_t*)db->table.p, db->table_len, db->fmt, db->locs.p,
-                                              db->loc_jbits, (const uint32_t*)db->wbase.p, (uint64_t*)a.p, s);
-        if (e == cudaSuccess && db->pending_n)
-            e = cudaMemcpyAsync((uint64_t*)a.p + n_old, db->pending.p, db->pending_n * 8, cudaMemcpyDeviceToDevice, s);
+                                              db->loc_jbits, (const uint32_t*)db->wbase.p, (uint64_t*)old.p, s);
+        if (e == cudaSuccess)
+            e = mc::merge_sorted_pairs((const uint64_t*)old.p, n_old, (const uint64_t*)db->pending.p, n_new,
+                                       (uint64_t*)a.p, s);
+        release(db, old);
         if (e != cudaSuccess) {
             release(db, a);
-            return cuda_fail(e, "finalize: gather of the stored pairs");
+            return cuda_fail(e, "finalize: merge of the stored pairs");
         }
     }
     auto release_tmp = [&]() {
         if (!a_is_pending) release(db, a);
-        release(db, b);
     };
-    if (!(a_is_pending && db->pending_sorted)) {
-        if (!grab(db, b, n_total * 8)) {
-            release_tmp();
-            return fail(MC_ERR_OOM, "finalize: allocation failed");
-        }
-        cudaError_t e = mc::sort_pairs(db->mem, (uint64_t*)a.p, (uint64_t*)b.p, n_total, n_real, s);
-        if (e != cudaSuccess) {
-            release_tmp();
-            // the sort allocates its scratch before it touches the pairs
-            if (e != cudaErrorMemoryAllocation) db->failed = true;
-            return cuda_fail(e, "finalize: sort");
-        }
-        release(db, b);
-    }
     uint64_t prior_over = 0;
     if (n_lists) {
         cudaError_t e = mc::apply_prior(db->mem, (uint64_t*)a.p, n_real, db->cap, n_lists, keys, counts, list_n,

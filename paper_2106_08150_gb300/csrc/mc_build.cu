@@ -947,6 +947,77 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     return cudaSuccess;
 }
 
+// ------------------------------------------------------------ merge path
+// Live extension (Section 4.1: new targets get the next ids): the stored
+// pairs (reconstructed in layout order) and the sorted pairs of the new
+// targets are two sorted runs; merging them gives the sorted pairs of the
+// whole database without sorting the stored ones again.  Merge path
+// (Odeh, Green, Mwassi, Shmueli, Birk 2012): a block takes 2,048
+// consecutive outputs, finds where that output range starts and ends in
+// both inputs by a binary search along the diagonals, stages the two input
+// slices in shared memory, and each thread merges eight outputs.
+namespace {
+constexpr int MP_ITEMS = 8;
+constexpr uint64_t MP_TILE = (uint64_t)BT * MP_ITEMS;
+
+// Number of elements of a in the first d outputs of merge(a, b), ties
+// taken from a first.
+__device__ __forceinline__ uint64_t merge_split(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb,
+                                                uint64_t d) {
+    uint64_t lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) >> 1;
+        if (a[mid] <= b[d - mid - 1]) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(BT) k_merge_path(const uint64_t* __restrict__ a, uint64_t na,
+                                                   const uint64_t* __restrict__ b, uint64_t nb,
+                                                   uint64_t* __restrict__ c) {
+    __shared__ uint64_t in[MP_TILE];
+    __shared__ uint64_t out[MP_TILE];
+    __shared__ uint64_t split[2];
+    const uint64_t n = na + nb;
+    for (uint64_t d0 = (uint64_t)blockIdx.x * MP_TILE; d0 < n; d0 += (uint64_t)gridDim.x * MP_TILE) {
+        const uint64_t d1 = min(d0 + MP_TILE, n);
+        if (threadIdx.x < 2) split[threadIdx.x] = merge_split(a, na, b, nb, threadIdx.x ? d1 : d0);
+        __syncthreads();
+        const uint64_t i0 = split[0], i1 = split[1];
+        const uint32_t ta = (uint32_t)(i1 - i0), tb = (uint32_t)((d1 - d0) - ta);
+        for (uint32_t k = threadIdx.x; k < ta + tb; k += BT) in[k] = k < ta ? a[i0 + k] : b[(d0 - i0) + (k - ta)];
+        __syncthreads();
+        const uint64_t* sa = in;
+        const uint64_t* sb = in + ta;
+        const uint32_t dl = threadIdx.x * MP_ITEMS;
+        if (dl < ta + tb) {
+            uint32_t lo = dl > tb ? dl - tb : 0, hi = dl < ta ? dl : ta;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (sa[mid] <= sb[dl - mid - 1]) lo = mid + 1; else hi = mid;
+            }
+            uint32_t ia = lo, ib = dl - lo;
+            for (uint32_t k = 0; k < MP_ITEMS && dl + k < ta + tb; ++k) {
+                const bool take_a = ib >= tb || (ia < ta && sa[ia] <= sb[ib]);
+                out[dl + k] = take_a ? sa[ia++] : sb[ib++];
+            }
+        }
+        __syncthreads();
+        for (uint32_t k = threadIdx.x; k < ta + tb; k += BT) c[d0 + k] = out[k];
+        __syncthreads();
+    }
+}
+}  // namespace
+
+cudaError_t merge_sorted_pairs(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* c,
+                               cudaStream_t s) {
+    const uint64_t n = na + nb;
+    if (n == 0) return cudaSuccess;
+    MC_LAUNCH("merge_path", s,
+              k_merge_path<<<grid_for((n + MP_TILE - 1) / MP_TILE, 4), BT, 0, s>>>(a, na, b, nb, c));
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------- sharded builds
 // Section 4.3 partitions the reference targets over GPUs.  A shard holds a
 // contiguous range of target ids, so every location of an earlier shard is

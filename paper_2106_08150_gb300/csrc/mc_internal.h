@@ -119,6 +119,10 @@ __host__ __device__ inline uint32_t loc_bytes(uint32_t jbits) { return jbits ? 4
 cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, uint32_t cap, const uint32_t* wbase,
                            uint32_t n_targets, uint32_t jbits, FinalizeOut* out, cudaStream_t s);
 
+// c[0..na+nb) = the merge of the sorted pair runs a and b (ties from a).
+cudaError_t merge_sorted_pairs(const uint64_t* a, uint64_t na, const uint64_t* b, uint64_t nb, uint64_t* c,
+                               cudaStream_t s);
+
 // Sharded builds (Section 4.3): distinct features of sorted pairs a[0..n)
 // (h2 keys ascending) with their counts clamped to cap; *n_keys = the
 // number of features, written only when they fit max.

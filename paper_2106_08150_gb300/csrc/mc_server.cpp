@@ -123,6 +123,7 @@ struct mc_server {
     // statistics
     uint64_t jobs_submitted = 0, jobs_done = 0, queries_done = 0, launch_sets = 0, n_ext = 0, epoch = 0;
     uint64_t ext_requested = 0, ext_applied = 0;
+    std::vector<double> ext_seconds;  // time of each applied extension (add + finalize)
     uint64_t hbm_in_use = 0, hbm_peak = 0;
     double t_first = -1, t_last = 0;
     std::vector<double> latencies;
@@ -175,8 +176,15 @@ int apply_extension(mc_server* s, Extension& e, uint64_t* epoch_out) {
     // add + finalize run on the database stream and return after it is idle;
     // launch sets in flight keep reading the previous layout
     uint32_t first = 0;
+    const auto t0 = std::chrono::steady_clock::now();
     if (rc == MC_OK) rc = mc_db_add_targets(s->db, n, (const char*)dseq, (const uint64_t*)doffs, e.taxon.data(), &first);
     if (rc == MC_OK) rc = mc_db_finalize(s->db);
+    if (rc == MC_OK) {
+        // add + finalize return with the database stream idle: this is the device work of the extension
+        const double dt = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->ext_seconds.push_back(dt);
+    }
     cudaFreeAsync(dseq, cs);
     cudaFreeAsync(doffs, cs);
     cudaGetLastError();
@@ -569,6 +577,10 @@ int mc_server_stats_get(mc_server* s, mc_server_stats* out) {
         out->max_latency_s = l.back();
     }
     out->busy_s = s->t_first < 0 ? 0 : std::max(0.0, s->t_last - s->t_first);
+    for (double x : s->ext_seconds) {
+        out->extension_mean_s += x / (double)s->ext_seconds.size();
+        out->extension_max_s = std::max(out->extension_max_s, x);
+    }
     return MC_OK;
 }
 

@@ -94,7 +94,8 @@ class mc_server_stats(ctypes.Structure):
     _fields_ = [(n, ctypes.c_uint64) for n in
                 ["jobs_submitted", "jobs_done", "queries_done", "launch_sets", "extensions", "epoch", "hbm_in_use",
                  "hbm_limit", "hbm_peak"]] + \
-               [(n, ctypes.c_double) for n in ["p50_latency_s", "p99_latency_s", "max_latency_s", "busy_s"]]
+               [(n, ctypes.c_double) for n in ["p50_latency_s", "p99_latency_s", "max_latency_s", "busy_s",
+                                               "extension_mean_s", "extension_max_s"]]
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)

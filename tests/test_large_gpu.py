@@ -7,7 +7,10 @@ bench.py times, and checked against the oracle on sampled outputs: the
 oracle builds the buckets of every feature of 2,000 sampled queries (a
 quarter of them from the repeat-rich genomes) plus every feature of one key
 range, which are then complete, so the dump of that key range and the
-labels, hit counts and top targets of the sampled queries must be equal."""
+labels, hit counts and top targets of the sampled queries must be equal.
+Mixed-length query batches (sizes lognormal, lengths 50-300, single-end
+and pairs) are classified against the same full-size database through a
+CUDA-graph plan and checked the same way on 1,000 sampled queries."""
 import os
 
 import numpy as np
@@ -105,6 +108,34 @@ def test_fullsize_large_database_matches_oracle_on_samples(mc):
         sub_reads, sub_roffs, sub_qoffs = _sub_queries(w, qs)
         _, sk, cnt = oracle.sketch(sub_reads, sub_roffs, **p)
         feats = np.unique(np.concatenate([sk[i][:cnt[i]] for i in range(len(cnt))]))
+
+        # mixed-length batches against the same database (the batched workload:
+        # sizes lognormal, lengths 50-300, half single-end half pairs), run as
+        # one replay of a CUDA-graph plan with the tuned shape; 1,000 sampled
+        # queries of them are checked below
+        batches = synth.mixed_batches(1003, w.genomes, w.goffs, n_batches=24)
+        mb = [(dev(r) if len(r) else dev(np.zeros(1, np.uint8)), dev(ro), dev(qo), len(ro) - 1, len(qo) - 1)
+              for r, ro, qo, _ in batches]
+        outs = [[torch.empty(max(1, nqb), dtype=torch.int32, device="cuda") for _ in range(3)]
+                for *_, nqb in mb]
+        descs = [mc.batch(n_seq, r, ro, qo, *o) for (r, ro, qo, n_seq, _), o in zip(mb, outs)]
+        cp0 = mc.classify_params(**dict(w.cls_params, max_insert=0))
+        plan = mc.Plan(db.handle, cp0, len(descs), sum(x[4] for x in mb), tuned)
+        try:
+            plan.run(descs)
+            mc.mc_classify_status(db.handle)
+        finally:
+            plan.free()
+        all_r, all_ro, all_qo, _ = synth.concat_batches(batches)
+        got_b = [np.concatenate([host_u32(o[i])[: x[4]] for o, x in zip(outs, mb)]) for i in range(3)]
+        nb = len(all_qo) - 1
+
+        class _W:  # the concatenated batches, shaped for _sub_queries
+            reads, roffs, qoffs = all_r, all_ro, all_qo
+        qb = np.sort(rng.choice(nb, size=1000, replace=False))
+        b_reads, b_roffs, b_qoffs = _sub_queries(_W, qb)
+        _, skb, cntb = oracle.sketch(b_reads, b_roffs, **p)
+        feats = np.unique(np.concatenate([feats] + [skb[i][:cntb[i]] for i in range(len(cntb))]))
         lo, hi = 0, (1 << 32) // 4096
         keys = np.unique(np.concatenate([feats, np.arange(lo, hi, dtype=np.uint32)]))
         odb = oracle.DB(w.genomes, w.goffs, key_filter=keys, n_threads=n_threads, **p)
@@ -125,5 +156,11 @@ def test_fullsize_large_database_matches_oracle_on_samples(mc):
         assert (g_top[qs] == ot_).all()
         assert (g_label[qs] == ol_).all()
         assert (g_label[qs] != oracle.NO_TAXON).mean() > 0.8
+        # the sampled queries of the mixed batches
+        bl, bh, bt = odb.classify(w.parent, w.taxon_of_target, b_reads, b_roffs, b_qoffs, n_threads=n_threads,
+                                  **dict(w.cls_params, max_insert=0))
+        assert (got_b[1][qb] == bh).all()
+        assert (got_b[2][qb] == bt).all()
+        assert (got_b[0][qb] == bl).all()
     finally:
         db.free()
