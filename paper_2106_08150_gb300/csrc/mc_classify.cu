@@ -942,81 +942,116 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
 // array) without a hash table.  Same outputs as query_score.
 
 // Bitonic sort of 32*E keys held E per lane, element i = lane*E + r, into
-// ascending order of i.
+// ascending order of i.  Mirror form of the network: each merge stage of
+// block size K starts by comparing i with its mirror i ^ (K - 1) and goes on
+// with half-cleaners i ^ J, J = K/4 .. 1, and every comparator puts the
+// smaller key at the smaller index, so the steps within a lane's registers
+// need no direction select.
 template <int E>
 __device__ __forceinline__ void warp_bitonic_sort(uint32_t (&k)[E]) {
     const uint32_t lane = lane_id();
 #pragma unroll
     for (int K = 2; K <= 32 * E; K <<= 1) {
-        // direction of this lane's blocks once they span lanes
-        const bool lane_asc = ((lane * (uint32_t)E) & (uint32_t)K) == 0;
+        if (K <= E) {
 #pragma unroll
-        for (int J = K >> 1; J > 0; J >>= 1) {
+            for (int r = 0; r < E; ++r) {
+                if ((r & (K >> 1)) == 0) {
+                    const int o = r ^ (K - 1);
+                    const uint32_t a = k[r], b = k[o];
+                    k[r] = min(a, b);
+                    k[o] = max(a, b);
+                }
+            }
+        } else {
+            // mirror partner of element (lane, r): lane ^ (K/E - 1), register E-1-r
+            const int lm = K / E - 1;
+            const bool lower = (lane & (uint32_t)(K / E / 2)) == 0;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const uint32_t o1 = __shfl_xor_sync(FULL_MASK, k[E - 1 - r], lm);
+                const uint32_t o2 = __shfl_xor_sync(FULL_MASK, k[r], lm);
+                k[r] = lower ? min(k[r], o1) : max(k[r], o1);
+                k[E - 1 - r] = lower ? min(k[E - 1 - r], o2) : max(k[E - 1 - r], o2);
+            }
+        }
+#pragma unroll
+        for (int J = K >> 2; J > 0; J >>= 1) {
             if (J < E) {
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     if ((r & J) == 0) {
                         const uint32_t a = k[r], b = k[r | J];
-                        const uint32_t mn = min(a, b), mx = max(a, b);
-                        const bool asc = K < E ? ((r & K) == 0) : lane_asc;
-                        k[r] = asc ? mn : mx;
-                        k[r | J] = asc ? mx : mn;
+                        k[r] = min(a, b);
+                        k[r | J] = max(a, b);
                     }
                 }
             } else {
                 const int lj = J / E;
-                const bool keep_min = ((lane & (uint32_t)lj) == 0) == lane_asc;
+                const bool lower = (lane & (uint32_t)lj) == 0;
 #pragma unroll
                 for (int r = 0; r < E; ++r) {
                     const uint32_t o = __shfl_xor_sync(FULL_MASK, k[r], lj);
-                    k[r] = keep_min ? min(k[r], o) : max(k[r], o);
+                    k[r] = lower ? min(k[r], o) : max(k[r], o);
                 }
             }
         }
     }
 }
 
-// Shared-memory index of sorted element i: one padding word per 32, so that
-// lane-major access (i = lane*E + r, for E = 8, 16, 32) and strided access
-// (i = r*32 + lane) both hit 32 distinct banks.
-__device__ __forceinline__ uint32_t spad(uint32_t i) { return i + (i >> 5); }
-
-// Per-warp shared memory of the sort path: bucket list, its prefix, the
-// sorted keys and the scores of run starts (both padded by spad).
+// Per-warp shared memory of the sort path: bucket list, its prefix, and per
+// run of equal locations in the sorted gather (at most 32*E runs) its
+// location, its first sorted index and its score.
 template <int E>
 __host__ __device__ constexpr size_t sort_warp_bytes(uint32_t list_cap) {
-    return align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + 2 * align16((size_t)33 * E * 4);
+    return align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + align16((32 * (size_t)E + 4) * 4) +
+           align16((32 * (size_t)E + 4) * 2) + align16((32 * (size_t)E) * 2);
+}
+
+struct SortWarpMem {
+    uint64_t* list;   // found buckets, offset << 16 | size
+    uint32_t* l_pre;  // exclusive prefix of the bucket sizes
+    uint32_t* loc;    // location of run j, ascending
+    uint16_t* rs;     // first sorted index of run j; rs[D] = H
+    uint16_t* sc;     // sliding-window score of run j (0 once excluded)
+};
+
+template <int E>
+__device__ __forceinline__ SortWarpMem sort_warp_mem(unsigned char* p, uint32_t list_cap) {
+    SortWarpMem m;
+    m.list = reinterpret_cast<uint64_t*>(p);
+    p += align16((size_t)list_cap * 8);
+    m.l_pre = reinterpret_cast<uint32_t*>(p);
+    p += align16(((size_t)list_cap + 4) * 4);
+    m.loc = reinterpret_cast<uint32_t*>(p);
+    p += align16((32 * (size_t)E + 4) * 4);
+    m.rs = reinterpret_cast<uint16_t*>(p);
+    p += align16((32 * (size_t)E + 4) * 2);
+    m.sc = reinterpret_cast<uint16_t*>(p);
+    return m;
 }
 
 constexpr int SORT_WARPS = 4;  // warps per CTA of the sort path
 
-// First index in [lo, hi) of sorted a[] (padded by spad) whose value is
-// greater than v (hi if none), galloping from lo (ranges are mostly short).
-__device__ __forceinline__ uint32_t gallop_upper_bound(const uint32_t* a, uint32_t lo, uint32_t hi, uint32_t v) {
-    uint32_t step = 1, prev = lo;
-    uint32_t pos = lo;
-    while (pos < hi && a[spad(pos)] <= v) {
-        prev = pos + 1;
-        pos += step;
-        step <<= 1;
+// First run index in [lo, hi) whose location is greater than v (hi if none).
+__device__ __forceinline__ uint32_t runs_upper_bound(const uint32_t* loc, uint32_t lo, uint32_t hi, uint32_t v) {
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (loc[mid] <= v) lo = mid + 1; else hi = mid;
     }
-    uint32_t l = prev, h = pos < hi ? pos : hi;  // a[l-1] <= v, a[h] > v (or h == hi)
-    while (l < h) {
-        const uint32_t mid = (l + h) >> 1;
-        if (a[spad(mid)] <= v) l = mid + 1; else h = mid;
-    }
-    return l;
+    return lo;
 }
 
-// One query of at most 32*E locations on the sort path; returns Q_DONE.
+// One query of at most 32*E locations on the sort path.
 template <int E>
-__device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q, uint64_t* list,
-                                          uint32_t* l_pre, uint32_t* A, uint32_t* SC, uint32_t n_list, uint32_t sws,
-                                          uint32_t H, Counters& ctr) {
+__device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                          const SortWarpMem& M, uint32_t n_list, uint32_t sws, uint32_t H,
+                                          Counters& ctr) {
     const uint32_t lane = lane_id();
     const uint32_t jb = db.jbits;
     const uint32_t* __restrict__ locs = static_cast<const uint32_t*>(db.locs);
-    constexpr uint32_t NO_LOC = 0xFFFFFFFFu;  // never a stored location; sorts last
+    const uint64_t* list = M.list;
+    uint32_t* l_pre = M.l_pre;
+    constexpr uint32_t NO_LOC = 0xFFFFFFFFu;  // padding; sorts last and lies beyond H
 
     // exclusive prefix of the bucket sizes
     uint32_t tot = 0;
@@ -1055,42 +1090,73 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
         }
     }
     warp_bitonic_sort<E>(k);
-#pragma unroll
-    for (int r = 0; r < E; ++r) A[spad(lane * E + r)] = k[r];
-    __syncwarp();
 
-    // Runs of equal locations (window count statistic) and their
-    // sliding-window scores: score(x) = elements of the sorted array in
-    // [x, hi(x)], hi(x) = x + sws - 1 cut at the last window id of x's
-    // target.  hi grows with x, so each lane's range end only moves forward
-    // (galloping from where it was).  The first top-m round is folded in.
-    const uint32_t jmask = (1u << jb) - 1u;
-    uint32_t n_start = 0, pend = 0;
-    Cand best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
-    for (int r = 0; r < E; ++r) {
-        const uint32_t i = lane * E + r;
-        uint32_t sc = 0;
-        if (i < H) {
-            const uint32_t x = A[spad(i)];
-            if (i == 0 || x != A[spad(i - 1)]) {
-                ++n_start;
-                // no wrap: stays in x's target (sws >= 1 whenever a query has locations)
-                const uint32_t hi = x + min(sws ? sws - 1 : 0u, jmask - (x & jmask));
-                pend = gallop_upper_bound(A, max(pend, i + 1), H, hi);
-                sc = pend - i;
-                const Cand c = Cand{sc, x >> jb, x & jmask, 0};
-                if (better(c, best)) best = c;
+    // Runs of equal locations (the window count statistic of Section 5.6):
+    // run j has location loc[j] and covers sorted indices [rs[j], rs[j+1]).
+    uint32_t D;
+    {
+        const uint32_t before = __shfl_up_sync(FULL_MASK, k[E - 1], 1);
+        uint32_t starts = 0;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const uint32_t i = lane * E + r;
+            const uint32_t pv = r ? k[r - 1] : before;
+            if (i < H && (i == 0 || k[r] != pv)) starts |= 1u << r;
+        }
+        const uint32_t n = __popc(starts);
+        uint32_t inc = n;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t x = __shfl_up_sync(FULL_MASK, inc, d);
+            if ((int)lane >= d) inc += x;
+        }
+        D = __shfl_sync(FULL_MASK, inc, 31);
+        uint32_t pos = inc - n;
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if (starts & (1u << r)) {
+                M.loc[pos] = k[r];
+                M.rs[pos] = (uint16_t)(lane * E + r);
+                ++pos;
             }
         }
-        SC[spad(i)] = sc;
+        if (lane == 0) M.rs[D] = (uint16_t)H;
     }
-    const uint32_t D = __reduce_add_sync(FULL_MASK, n_start);
+    __syncwarp();
     ctr.locations += H;
     ctr.distinct += D;
 
+    // Sliding-window scores (Section 5.6): the score of run j is the number
+    // of sorted locations in [loc[j], hi], hi = loc[j] + sws - 1 cut at the
+    // last window id of the target.  Runs have distinct locations, so at most
+    // sws - 1 runs after j lie in that range; e is the first run beyond it
+    // and the score is rs[e] - rs[j].  Four runs are checked per step (the
+    // locations ascend, so the count of those <= hi is the advance).  The
+    // first top-m round is folded in.
+    const uint32_t jmask = (1u << jb) - 1u;
+    const uint32_t w1 = sws ? sws - 1 : 0u;  // no wrap: stays in the run's target
+    Cand best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
+    for (uint32_t j = lane; j < D; j += 32) {
+        const uint32_t x = M.loc[j];
+        const uint32_t hi = x + min(w1, jmask - (x & jmask));
+        uint32_t e = j + 1;
+        for (;;) {
+            uint32_t adv = 0;
+#pragma unroll
+            for (int d = 0; d < 4; ++d) adv += (e + d < D && M.loc[e + d] <= hi) ? 1u : 0u;
+            e += adv;
+            if (adv < 4) break;
+        }
+        const uint32_t sc = (uint32_t)M.rs[e] - (uint32_t)M.rs[j];
+        M.sc[j] = (uint16_t)sc;
+        const Cand c = Cand{sc, x >> jb, x & jmask, 0};
+        if (better(c, best)) best = c;
+    }
+    __syncwarp();
+
     // top m with one candidate per target (Section 4.2 / 5.6): rounds of
     // warp arg-max; the winner's target is excluded from later rounds by
-    // zeroing the scores of its entries; the label is folded as in
+    // zeroing the scores of its runs; the label is folded as in
     // query_score.  Unless the full top-m list is requested, later rounds
     // only matter for "close" candidates, so after the first round every
     // score below the close threshold is cleared at once.
@@ -1102,14 +1168,13 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
     for (int rd = 0; rd < m; ++rd) {
         if (rd) {
             best = Cand{0, 0xFFFFFFFFu, 0xFFFFFFFFu, 0};
-            for (int r = 0; r < E; ++r) {
-                const uint32_t i = spad(lane * E + r);
-                const uint32_t sc = SC[i];
+            for (uint32_t j = lane; j < D; j += 32) {
+                const uint32_t sc = M.sc[j];
                 if (sc == 0) continue;
-                const uint32_t x = A[i];
+                const uint32_t x = M.loc[j];
                 const uint32_t t = x >> jb;
                 if (t == prev_t) {
-                    SC[i] = 0;
+                    M.sc[j] = 0;
                     continue;
                 }
                 const Cand c = Cand{sc, t, x & jmask, 0};
@@ -1126,11 +1191,11 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
         if (best.score == 0) break;
         prev_t = best.t;
         if (Q.cands) {
-            // last window of the range present: the last element <= hi
+            // last window of the range present: the location of the last run <= hi
             const uint32_t x0 = (best.t << jb) | best.j0;
-            const uint32_t hi = x0 + min(sws ? sws - 1 : 0u, jmask - best.j0);
-            const uint32_t e = gallop_upper_bound(A, 0, H, hi);
-            best.j1 = A[spad(e - 1)] & jmask;
+            const uint32_t hi = x0 + min(w1, jmask - best.j0);
+            const uint32_t e = runs_upper_bound(M.loc, 0, D, hi);
+            best.j1 = M.loc[e - 1] & jmask;
         }
         if ((int)lane == rd) mine = best;
         if (rd == 0) {
@@ -1142,10 +1207,8 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
             if (!Q.cands) {
                 // smallest score s with 100 s >= bar
                 const uint32_t s_min = (uint32_t)((bar + 99) / 100);
-                for (int r = 0; r < E; ++r) {
-                    const uint32_t i = spad(lane * E + r);
-                    if (SC[i] < s_min) SC[i] = 0;
-                }
+                for (uint32_t j = lane; j < D; j += 32)
+                    if (M.sc[j] < s_min) M.sc[j] = 0;
             }
         } else if (hits >= Q.hits_min && 100ull * best.score >= bar) {
             const uint32_t tx = best.t < db.n_targets ? db.taxon_of_target[best.t] : NO_TAXON;
@@ -1170,14 +1233,7 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
-    unsigned char* p = smem + w * sort_warp_bytes<E>(list_cap);
-    uint64_t* list = reinterpret_cast<uint64_t*>(p);
-    p += align16((size_t)list_cap * 8);
-    uint32_t* l_pre = reinterpret_cast<uint32_t*>(p);
-    p += align16(((size_t)list_cap + 4) * 4);
-    uint32_t* A = reinterpret_cast<uint32_t*>(p);
-    p += align16((size_t)33 * E * 4);
-    uint32_t* SC = reinterpret_cast<uint32_t*>(p);
+    const SortWarpMem M = sort_warp_mem<E>(smem + w * sort_warp_bytes<E>(list_cap), list_cap);
     Counters ctr;
     const uint32_t total = total_queries(Q);
     if (q0 >= total) return;
@@ -1192,9 +1248,9 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db
             continue;
         }
         const uint64_t* src = glist + (uint64_t)i * list_cap;
-        for (uint32_t j = lane; j < mt.x; j += 32) list[j] = __ldg(src + j);
+        for (uint32_t j = lane; j < mt.x; j += 32) M.list[j] = __ldg(src + j);
         __syncwarp();
-        query_sort<E>(db, Q, q0 + i, list, l_pre, A, SC, mt.x, meta_sws(mt), mt.z, ctr);
+        query_sort<E>(db, Q, q0 + i, M, mt.x, meta_sws(mt), mt.z, ctr);
         ctr.features += meta_feat(mt);
         ctr.found += mt.x;
         ctr.sectors += mt.w;
