@@ -946,55 +946,84 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
 // block size K starts by comparing i with its mirror i ^ (K - 1) and goes on
 // with half-cleaners i ^ J, J = K/4 .. 1, and every comparator puts the
 // smaller key at the smaller index, so the steps within a lane's registers
-// need no direction select.
+// need no direction select.  Stages up to K = E stay in the lane's
+// registers; the stages beyond run as a loop whose body holds one mirror
+// step, the cross-lane half-cleaners (each guarded by the stage) and the
+// E/2 .. 1 in-register half-cleaners, which keeps the code small.
+template <int E>
+__device__ __forceinline__ void sort_in_lane_halves(uint32_t (&k)[E]) {
+#pragma unroll
+    for (int J = E >> 1; J > 0; J >>= 1) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            if ((r & J) == 0) {
+                const uint32_t a = k[r], b = k[r | J];
+                k[r] = min(a, b);
+                k[r | J] = max(a, b);
+            }
+        }
+    }
+}
+
 template <int E>
 __device__ __forceinline__ void warp_bitonic_sort(uint32_t (&k)[E]) {
     const uint32_t lane = lane_id();
 #pragma unroll
-    for (int K = 2; K <= 32 * E; K <<= 1) {
-        if (K <= E) {
+    for (int K = 2; K <= E; K <<= 1) {
 #pragma unroll
-            for (int r = 0; r < E; ++r) {
-                if ((r & (K >> 1)) == 0) {
-                    const int o = r ^ (K - 1);
-                    const uint32_t a = k[r], b = k[o];
-                    k[r] = min(a, b);
-                    k[o] = max(a, b);
-                }
-            }
-        } else {
-            // mirror partner of element (lane, r): lane ^ (K/E - 1), register E-1-r
-            const int lm = K / E - 1;
-            const bool lower = (lane & (uint32_t)(K / E / 2)) == 0;
-#pragma unroll
-            for (int r = 0; r < E / 2; ++r) {
-                const uint32_t o1 = __shfl_xor_sync(FULL_MASK, k[E - 1 - r], lm);
-                const uint32_t o2 = __shfl_xor_sync(FULL_MASK, k[r], lm);
-                k[r] = lower ? min(k[r], o1) : max(k[r], o1);
-                k[E - 1 - r] = lower ? min(k[E - 1 - r], o2) : max(k[E - 1 - r], o2);
+        for (int r = 0; r < E; ++r) {
+            if ((r & (K >> 1)) == 0) {
+                const int o = r ^ (K - 1);
+                const uint32_t a = k[r], b = k[o];
+                k[r] = min(a, b);
+                k[o] = max(a, b);
             }
         }
 #pragma unroll
         for (int J = K >> 2; J > 0; J >>= 1) {
-            if (J < E) {
 #pragma unroll
-                for (int r = 0; r < E; ++r) {
-                    if ((r & J) == 0) {
-                        const uint32_t a = k[r], b = k[r | J];
-                        k[r] = min(a, b);
-                        k[r | J] = max(a, b);
-                    }
-                }
-            } else {
-                const int lj = J / E;
-                const bool lower = (lane & (uint32_t)lj) == 0;
-#pragma unroll
-                for (int r = 0; r < E; ++r) {
-                    const uint32_t o = __shfl_xor_sync(FULL_MASK, k[r], lj);
-                    k[r] = lower ? min(k[r], o) : max(k[r], o);
+            for (int r = 0; r < E; ++r) {
+                if ((r & J) == 0) {
+                    const uint32_t a = k[r], b = k[r | J];
+                    k[r] = min(a, b);
+                    k[r | J] = max(a, b);
                 }
             }
         }
+    }
+#pragma unroll 1
+    for (uint32_t kl = 2; kl <= 32; kl <<= 1) {  // K = kl * E
+        {
+            // mirror partner of element (lane, r): lane ^ (kl - 1), register
+            // E-1-r; the lower lane keeps the minimum.  As a mirror pair
+            // (r, E-1-r) of this lane meets the pair (E-1-r, r) of the
+            // partner, each register takes the partner's value first.
+            const uint32_t up = (lane & (kl >> 1)) ? 0xFFFFFFFFu : 0u;  // the upper lane keeps the max
+            const uint32_t lm = kl - 1;
+#pragma unroll
+            for (int r = 0; r < E / 2; ++r) {
+                const uint32_t a = k[r], b = k[E - 1 - r];
+                const uint32_t pa = __shfl_xor_sync(FULL_MASK, b, lm);  // partner's E-1-r
+                const uint32_t pb = __shfl_xor_sync(FULL_MASK, a, lm);  // partner's r
+                const uint32_t na = min(a, pa), nb = min(b, pb);
+                k[r] = na ^ ((na ^ max(a, pa)) & up);
+                k[E - 1 - r] = nb ^ ((nb ^ max(b, pb)) & up);
+            }
+        }
+#pragma unroll
+        for (int t = 3; t >= 0; --t) {  // lane distances kl/4 .. 1 (warp-uniform guard)
+            const uint32_t lj = 1u << t;
+            if (lj <= (kl >> 2)) {
+                const uint32_t up = (lane & lj) ? 0xFFFFFFFFu : 0u;
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const uint32_t o = __shfl_xor_sync(FULL_MASK, k[r], lj);
+                    const uint32_t n = min(k[r], o);
+                    k[r] = n ^ ((n ^ max(k[r], o)) & up);
+                }
+            }
+        }
+        sort_in_lane_halves<E>(k);
     }
 }
 
@@ -1006,6 +1035,10 @@ __host__ __device__ constexpr size_t sort_warp_bytes(uint32_t list_cap) {
     return align16((size_t)list_cap * 8) + align16(((size_t)list_cap + 4) * 4) + align16((32 * (size_t)E + 4) * 4) +
            align16((32 * (size_t)E + 4) * 2) + align16((32 * (size_t)E) * 2);
 }
+
+// Slot of loc[] and rs[] beyond every run (the arrays hold 32*E + 4).
+template <int E>
+constexpr uint32_t SORT_SPARE_SLOT = 32 * E + 3;
 
 struct SortWarpMem {
     uint64_t* list;   // found buckets, offset << 16 | size
@@ -1041,17 +1074,21 @@ __device__ __forceinline__ uint32_t runs_upper_bound(const uint32_t* loc, uint32
     return lo;
 }
 
-// One query of at most 32*E locations on the sort path.
+// Sort path, step 1 of a query: copies its bucket list from src to working
+// memory and issues the loads of its H <= 32*E locations into k (element
+// x = r * 32 + lane of the flat location list; NO_LOC beyond H).
+constexpr uint32_t NO_LOC = 0xFFFFFFFFu;  // padding; sorts last and lies beyond H
+
 template <int E>
-__device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
-                                          const SortWarpMem& M, uint32_t n_list, uint32_t sws, uint32_t H,
-                                          Counters& ctr) {
+__device__ __forceinline__ void sort_gather(const ClassifyDb& db, const SortWarpMem& M, const uint64_t* src,
+                                           uint32_t n_list, uint32_t H, uint32_t (&k)[E]) {
     const uint32_t lane = lane_id();
-    const uint32_t jb = db.jbits;
     const uint32_t* __restrict__ locs = static_cast<const uint32_t*>(db.locs);
-    const uint64_t* list = M.list;
+    uint64_t* list = M.list;
     uint32_t* l_pre = M.l_pre;
-    constexpr uint32_t NO_LOC = 0xFFFFFFFFu;  // padding; sorts last and lies beyond H
+    __syncwarp();  // the previous query is done with the list
+    for (uint32_t j = lane; j < n_list; j += 32) list[j] = __ldg(src + j);
+    __syncwarp();
 
     // exclusive prefix of the bucket sizes
     uint32_t tot = 0;
@@ -1070,39 +1107,46 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
     if (lane == 0) l_pre[n_list] = tot;
     __syncwarp();
 
-    // gather: element x = r * 32 + lane of the flat location list
-    uint32_t k[E];
-    {
-        uint32_t lo = 0, hi = n_list;  // bucket of x = lane: last b with l_pre[b] <= lane
-        while (hi - lo > 1) {
-            const uint32_t mid = (lo + hi) >> 1;
-            if (l_pre[mid] <= lane) lo = mid; else hi = mid;
-        }
-        uint32_t bkt = lo;
+    uint32_t lo = 0, hi = n_list;  // bucket of x = lane: last b with l_pre[b] <= lane
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (l_pre[mid] <= lane) lo = mid; else hi = mid;
+    }
+    uint32_t bkt = lo;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const uint32_t x = (uint32_t)r * 32 + lane;
-            k[r] = NO_LOC;
-            if (x < H) {
-                while (l_pre[bkt + 1] <= x) ++bkt;
-                k[r] = __ldg(locs + (list[bkt] >> 16) + (x - l_pre[bkt]));
-            }
+    for (int r = 0; r < E; ++r) {
+        const uint32_t x = (uint32_t)r * 32 + lane;
+        k[r] = NO_LOC;
+        if (x < H) {
+            while (l_pre[bkt + 1] <= x) ++bkt;
+            k[r] = __ldg(locs + (list[bkt] >> 16) + (x - l_pre[bkt]));
         }
     }
+}
+
+// Sort path, step 2 of a query: its H gathered locations k (as left by
+// sort_gather) are sorted, scored and labelled, and the outputs written.
+template <int E>
+__device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q,
+                                          const SortWarpMem& M, uint32_t sws, uint32_t H, uint32_t (&k)[E],
+                                          Counters& ctr) {
+    const uint32_t lane = lane_id();
+    const uint32_t jb = db.jbits;
     warp_bitonic_sort<E>(k);
 
     // Runs of equal locations (the window count statistic of Section 5.6):
     // run j has location loc[j] and covers sorted indices [rs[j], rs[j+1]).
     uint32_t D;
     {
+        // bit r of starts: element lane*E + r (< H) begins a run
         const uint32_t before = __shfl_up_sync(FULL_MASK, k[E - 1], 1);
         uint32_t starts = 0;
 #pragma unroll
-        for (int r = 0; r < E; ++r) {
-            const uint32_t i = lane * E + r;
-            const uint32_t pv = r ? k[r - 1] : before;
-            if (i < H && (i == 0 || k[r] != pv)) starts |= 1u << r;
-        }
+        for (int r = 0; r < E; ++r) starts |= (uint32_t)(k[r] != (r ? k[r - 1] : before)) << r;
+        const uint32_t first = lane * E;
+        const uint32_t valid = H > first ? min((uint32_t)E, H - first) : 0u;
+        starts &= valid >= 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
+        if (lane == 0 && H > 0) starts |= 1u;
         const uint32_t n = __popc(starts);
         uint32_t inc = n;
 #pragma unroll
@@ -1111,15 +1155,24 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
             if ((int)lane >= d) inc += x;
         }
         D = __shfl_sync(FULL_MASK, inc, 31);
+        // the run starts in order (for E = 32 the other elements write to a
+        // spare slot instead of being predicated off, which keeps the
+        // kernel's predicate registers within what the compiler can allocate)
         uint32_t pos = inc - n;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            if (starts & (1u << r)) {
+            const uint32_t b = (starts >> r) & 1u;
+            if (E >= 32) {
+                const uint32_t at = b ? pos : SORT_SPARE_SLOT<E>;
+                M.loc[at] = k[r];
+                M.rs[at] = (uint16_t)(lane * E + r);
+            } else if (b) {
                 M.loc[pos] = k[r];
                 M.rs[pos] = (uint16_t)(lane * E + r);
-                ++pos;
             }
+            pos += b;
         }
+        __syncwarp();
         if (lane == 0) M.rs[D] = (uint16_t)H;
     }
     __syncwarp();
@@ -1221,10 +1274,52 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
     write_result(Q, q, label, hits, top, mine);
 }
 
+// Queries of one sort-path class: a warp reads the metadata of 32
+// consecutive queries at once (groups 32 * (gw + n * nwarp), n = 0, 1, ...)
+// and takes those with h_lo < H <= 32*E; with `last`, queries beyond 32*E
+// are queued for the medium path as they are met.
+struct SortClassScan {
+    uint32_t base, gw, nwarp, nq;  // 32 * n of the current group, warp, warps, chunk size
+    uint4 mt;                      // this lane's query of the group
+    uint32_t todo;                 // lanes of the group still to be processed
+};
+
+template <int E>
+__device__ __forceinline__ bool next_sort_query(SortClassScan& it, const uint4* __restrict__ meta, uint32_t h_lo,
+                                               uint32_t last, uint32_t* __restrict__ mid_list,
+                                               uint32_t* __restrict__ mid_n, uint32_t& i, uint4& mt) {
+    const uint32_t lane = lane_id();
+    while (it.todo == 0) {
+        it.base += 32;
+        const uint64_t first = (uint64_t)it.gw * 32 + (uint64_t)it.base * it.nwarp;
+        if (first >= it.nq) return false;
+        const uint64_t qi = first + lane;
+        it.mt = qi < it.nq ? meta[qi] : make_uint4(ESCALATED, 0, 0, 0);
+        // taken by a smaller class, escalated, or outside the chunk
+        const bool skip = it.mt.x == ESCALATED || (h_lo && it.mt.z <= h_lo);
+        const bool big = !skip && it.mt.z > 32u * E;
+        if (last && big) mid_list[atomicAdd(mid_n, 1u)] = (uint32_t)qi;
+        it.todo = __ballot_sync(FULL_MASK, !skip && !big);
+    }
+    const int l = __ffs(it.todo) - 1;
+    it.todo &= it.todo - 1;
+    i = it.gw * 32 + it.base * it.nwarp + (uint32_t)l;
+    mt.x = __shfl_sync(FULL_MASK, it.mt.x, l);
+    mt.y = __shfl_sync(FULL_MASK, it.mt.y, l);
+    mt.z = __shfl_sync(FULL_MASK, it.mt.z, l);
+    mt.w = __shfl_sync(FULL_MASK, it.mt.w, l);
+    return true;
+}
+
+// Resident CTAs per SM that the register budget of a sort-path kernel is
+// sized for (shared memory admits 15, 10 and 5 for E = 8, 16, 32).
+template <int E>
+constexpr int sort_min_ctas() { return E == 8 ? 8 : (E == 16 ? 7 : 4); }
+
 // Sort path over the chunk's queries with h_lo < H <= 32*E gathered
 // locations; with `last`, queries beyond 32*E are queued for the medium path.
 template <int E>
-__global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
+__global__ void __launch_bounds__(SORT_WARPS * 32, sort_min_ctas<E>()) k_classify_sort(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                   uint32_t chunk, uint32_t list_cap,
                                                                   const uint64_t* __restrict__ glist,
                                                                   const uint4* __restrict__ meta, uint32_t h_lo,
@@ -1232,30 +1327,28 @@ __global__ void __launch_bounds__(SORT_WARPS * 32) k_classify_sort(ClassifyDb db
                                                                   uint32_t* __restrict__ mid_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
-    const uint32_t lane = lane_id();
     const SortWarpMem M = sort_warp_mem<E>(smem + w * sort_warp_bytes<E>(list_cap), list_cap);
     Counters ctr;
     const uint32_t total = total_queries(Q);
     if (q0 >= total) return;
-    const uint32_t nq = min(chunk, total - q0);
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t i = gw; i < nq; i += nwarp) {
-        const uint4 mt = meta[i];
-        if (mt.x == ESCALATED || (h_lo && mt.z <= h_lo)) continue;  // a smaller class took it
-        if (mt.z > 32u * E) {
-            if (last && lane == 0) mid_list[atomicAdd(mid_n, 1u)] = i;
-            continue;
-        }
-        const uint64_t* src = glist + (uint64_t)i * list_cap;
-        for (uint32_t j = lane; j < mt.x; j += 32) M.list[j] = __ldg(src + j);
-        __syncwarp();
-        query_sort<E>(db, Q, q0 + i, M, mt.x, meta_sws(mt), mt.z, ctr);
+    SortClassScan it;
+    it.nq = min(chunk, total - q0);
+    it.gw = gw;
+    it.nwarp = nwarp;
+    it.base = (uint32_t)-32;  // the first next_sort_query step moves to n = 0
+    it.todo = 0;
+    uint32_t i;
+    uint4 mt;
+    uint32_t k[E];
+    while (next_sort_query<E>(it, meta, h_lo, last, mid_list, mid_n, i, mt)) {
+        sort_gather<E>(db, M, glist + (uint64_t)i * list_cap, mt.x, mt.z, k);
+        query_sort<E>(db, Q, q0 + i, M, meta_sws(mt), mt.z, k, ctr);
         ctr.features += meta_feat(mt);
         ctr.found += mt.x;
         ctr.sectors += mt.w;
         ++ctr.queries;
-        __syncwarp();
     }
     flush_counters(Q, ctr, E == 8 ? 1 : (E == 16 ? 2 : 3));
 }

@@ -62,17 +62,22 @@ __device__ __forceinline__ void encode4(uint32_t x, uint32_t& code8, uint32_t& i
     inv4 = ~valid & 0xFu;
 }
 
-// Bitonic sort of one value per lane across the warp (ascending by lane).
+// Bitonic sort of one value per lane across the warp (ascending by lane),
+// in mirror form: each merge stage of size k first pairs lane i with lane
+// i ^ (k - 1), then with i ^ j for j = k/4 .. 1, and the lower lane of a
+// pair always keeps the minimum (five lane-bit predicates in all).
 __device__ __forceinline__ uint32_t warp_sort32(uint32_t v) {
     const uint32_t lane = lane_id();
 #pragma unroll
     for (int k = 2; k <= 32; k <<= 1) {
+        {
+            const uint32_t u = __shfl_xor_sync(FULL_MASK, v, k - 1);
+            v = (lane & (uint32_t)(k >> 1)) == 0 ? min(v, u) : max(v, u);
+        }
 #pragma unroll
-        for (int j = k >> 1; j > 0; j >>= 1) {
+        for (int j = k >> 2; j > 0; j >>= 1) {
             const uint32_t u = __shfl_xor_sync(FULL_MASK, v, j);
-            const bool up = (lane & k) == 0;
-            const bool lower = (lane & j) == 0;
-            v = (lower == up) ? min(v, u) : max(v, u);
+            v = (lane & (uint32_t)j) == 0 ? min(v, u) : max(v, u);
         }
     }
     return v;
@@ -122,11 +127,28 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
 #pragma unroll
         for (int g = 0; g < R / 4; ++g) {
             uint32_t x = 0;
+            if (GLOBAL_SEQ) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const uint64_t b = b0 + 4 * g + i;
-                const uint32_t c = b < lim ? (GLOBAL_SEQ ? (uint32_t)__ldg(seq[w] + b) : (uint32_t)seq[w][b]) : 0u;
-                x |= c << (8 * i);
+                for (int i = 0; i < 4; ++i) {
+                    const uint64_t b = b0 + 4 * g + i;
+                    const uint32_t c = b < lim ? (uint32_t)__ldg(seq[w] + b) : 0u;
+                    x |= c << (8 * i);
+                }
+            } else {
+                // staged bases: the aligned words holding bases bg .. bg+3 and a
+                // funnel shift; a word is read only if it holds a base before
+                // lim, so every read stays inside the staged range
+                const uint64_t bg = b0 + 4 * g;
+                if (bg < lim) {
+                    const uintptr_t a = reinterpret_cast<uintptr_t>(seq[w] + bg);
+                    const uint32_t sh = (uint32_t)(a & 3u);
+                    const uint32_t* wp = reinterpret_cast<const uint32_t*>(a - sh);
+                    const uint32_t lo = wp[0];
+                    const uint32_t hi = (sh != 0 && bg + (4 - sh) < lim) ? wp[1] : 0u;
+                    x = __funnelshift_r(lo, hi, 8 * sh);
+                    const uint64_t nb = lim - bg;
+                    if (nb < 4) x &= (1u << (8 * (uint32_t)nb)) - 1u;
+                }
             }
             uint32_t c8, i4;
             encode4(x, c8, i4);
@@ -189,11 +211,14 @@ __device__ __forceinline__ void warp_sketch_multi(const uint8_t* const (&seq)[NW
             const uint32_t D = __popc(nd);
             fast[w] = D >= p.s || C == Nv;
             if (fast[w]) {
-                __syncwarp();
-                if (fresh) cand[w * 32 + __popc(nd & lt)] = v;
-                __syncwarp();
+                if (D != C) {  // duplicates: compact the distinct values
+                    __syncwarp();
+                    if (fresh) cand[w * 32 + __popc(nd & lt)] = v;
+                    __syncwarp();
+                    v = cand[w * 32 + lane];
+                }
                 count[w] = D < p.s ? D : p.s;
-                feature[w] = lane < count[w] ? cand[w * 32 + lane] : 0u;
+                feature[w] = lane < count[w] ? v : 0u;
             }
         }
     }
