@@ -207,7 +207,7 @@ def kernel_source_hash(kernel: str) -> str:
 
 # scoring kernels and their block of mc_classify_debug's per-kernel counters
 SCORE_KERNELS = {"classify_score": 0, "classify_sort256": 1, "classify_sort512": 2, "classify_sort1024": 3,
-                 "classify_medium": 4, "classify_large": 5}
+                 "classify_sort2048": 6, "classify_medium": 4, "classify_large": 5}
 
 
 def algorithmic_bytes(kernel: str, w, st: dict, ctr) -> float | None:

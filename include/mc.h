@@ -303,7 +303,7 @@ typedef struct mc_batch {
  *                loc_bytes == 4) and histogram keys of that width
  *                (wide_keys 0); otherwise the hash path is used.
  *  sort_max    : sort path: largest number of gathered locations a query
- *                may have to be sorted, 256, 512 or 1024 (default); each
+ *                may have to be sorted, 256, 512, 1024 or 2048 (default); each
  *                size class up to it has its own kernel; larger queries go
  *                to the hash path's medium and large kernels.
  *  hist_slots  : hash path: shared-memory histogram slots per query: 256,
@@ -559,9 +559,10 @@ int mc_sketch(const mc_db_params* params, uint32_t n_seq, const char* seq, const
  * 32-byte sectors of the gathered buckets, [6] queries finished on the
  * medium-histogram path; then per scoring kernel k (0 hash-path score
  * kernel, 1-3 sort path for up to 256/512/1024 locations, 4 medium path,
- * 5 large path): [7 + 3k] queries it finished, [8 + 3k] their found
- * features, [9 + 3k] their 32-byte sectors. */
-#define MC_DEBUG_COUNTERS 25
+ * 5 large path, 6 sort path for up to 2048 locations): [7 + 3k] queries it
+ * finished, [8 + 3k] their found features, [9 + 3k] their 32-byte
+ * sectors. */
+#define MC_DEBUG_COUNTERS 28
 int mc_classify_debug(const mc_db* db, const mc_classify_params* params, uint32_t n_seq, const char* seq,
                       const uint64_t* offs, uint32_t n_queries, const uint32_t* qoffs, uint32_t* label,
                       uint32_t* hits, uint32_t* top_target, uint32_t* cands, uint64_t* counters,

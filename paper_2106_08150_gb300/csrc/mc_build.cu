@@ -586,6 +586,7 @@ namespace {
 constexpr int FIN_ITEMS = 8;
 constexpr uint64_t FIN_TILE = (uint64_t)BT * FIN_ITEMS;  // warp w: [base + 256 w, base + 256 (w+1))
 constexpr uint32_t FIN_BUCKETS = 4096;  // window ranges of the target lookup table
+constexpr uint32_t FIN_WB_SMEM_MAX = 12288;  // window bases k_fin_emit keeps in shared memory (48 KiB)
 
 __device__ __forceinline__ uint32_t hk_of(uint64_t v) { return (uint32_t)(v >> 32); }
 
@@ -647,18 +648,28 @@ __global__ void __launch_bounds__(BT) k_fin_count(const uint64_t* __restrict__ a
 // block first tabulates that target for the first window of each of
 // FIN_BUCKETS equal window ranges, which narrows every search to the
 // targets that overlap gw's range (one or two for genome-sized targets).
+// With wb_smem, wbase (n_targets + 1 words) is copied to shared memory too,
+// so that the search and the window offset are shared-memory reads.
 __global__ void __launch_bounds__(BT) k_fin_emit(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap,
                                                  const uint64_t* __restrict__ tkept, const uint64_t* __restrict__ tkeys,
                                                  uint64_t n_tiles, const uint32_t* __restrict__ wbase,
                                                  uint32_t n_targets, uint32_t jbits, void* __restrict__ locs,
                                                  uint32_t* __restrict__ khk, uint64_t* __restrict__ koff,
-                                                 uint64_t* __restrict__ kstart, unsigned long long* overflow) {
-    __shared__ uint32_t first_target[FIN_BUCKETS + 1];
+                                                 uint64_t* __restrict__ kstart, unsigned long long* overflow,
+                                                 bool wb_smem) {
+    extern __shared__ uint32_t fin_smem[];
+    uint32_t* first_target = fin_smem;  // FIN_BUCKETS + 1 words
     __shared__ uint32_t wk[NWARP], wsx[NWARP];
     const int w = threadIdx.x >> 5;
     const uint32_t lane = lane_id();
     const uint32_t lt = lanemask_lt();
     const uint32_t* wb = wbase;
+    if (wb_smem) {
+        uint32_t* copy = fin_smem + FIN_BUCKETS + 1;
+        for (uint32_t t = threadIdx.x; t <= n_targets; t += BT) copy[t] = wbase[t];
+        __syncthreads();
+        wb = copy;
+    }
     const uint64_t n_win = wb[n_targets];
     uint32_t bshift = 0;
     while ((n_win >> bshift) >= FIN_BUCKETS) ++bshift;
@@ -885,9 +896,15 @@ cudaError_t finalize_pairs(const Mem& mem, const uint64_t* sorted, uint64_t n, u
     Tmp<uint32_t> khk(mem, n_keys, s);
     if (!locs.ok() || !koff.ok() || !kstart.ok() || !khk.ok()) return cudaErrorMemoryAllocation;
     if (n > 0) {
+        // wbase in shared memory when it fits next to the range table
+        const bool wb_smem = n_targets + 1 <= FIN_WB_SMEM_MAX;
+        const size_t smem = (size_t)(FIN_BUCKETS + 1 + (wb_smem ? n_targets + 1 : 0)) * 4;
+        if ((e = cudaFuncSetAttribute(k_fin_emit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
         MC_LAUNCH("fin_emit", s,
-                  k_fin_emit<<<g, BT, 0, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets, jbits,
-                                              locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr));
+                  k_fin_emit<<<g, BT, smem, s>>>(sorted, n, cap, tkept.ptr, tkeys.ptr, tiles, wbase, n_targets, jbits,
+                                                 locs.ptr, khk.ptr, koff.ptr, kstart.ptr, ctr.ptr, wb_smem));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(kstart.ptr + n_keys, &n, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
         if ((e = cudaMemcpyAsync(koff.ptr + n_keys, &n_kept, 8, cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;

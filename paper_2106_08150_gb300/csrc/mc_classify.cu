@@ -22,6 +22,7 @@
 // global scratch memory.  Both paths run the same code, so the result does
 // not depend on the path.
 #include <algorithm>
+#include <type_traits>
 
 #include "mc_internal.h"
 #include "mc_sketch.cuh"
@@ -224,9 +225,9 @@ struct Counters {
 };
 
 // Per-kernel counter block of mc_classify_debug: kernel k (0 hash score,
-// 1-3 sort path 256/512/1024, 4 medium path, 5 large path) adds the
-// queries it finished, their found buckets and their 32-byte sectors at
-// counters[7 + 3k ...].
+// 1-3 sort path 256/512/1024, 4 medium path, 5 large path, 6 sort path
+// 2048) adds the queries it finished, their found buckets and their
+// 32-byte sectors at counters[7 + 3k ...].
 constexpr int KC_SCORE = 0, KC_MEDIUM = 4, KC_LARGE = 5;
 
 // Batch holding query q of a multi-batch launch: the last batch whose
@@ -882,10 +883,82 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
     flush_counters(Q, ctr, KC_SCORE);
 }
 
-// Medium path: the chunk's queries whose histogram did not fit the main
-// path, one warp each (work queue), KM_SLOTS histogram slots per warp in
-// shared memory, the bucket list taken over from the lookup.  Queries that
-// do not fit here either go to the large path.
+// Queries of the chunk with h_lo < H <= h_hi gathered locations (h_lo = 0:
+// no lower bound), not escalated: a warp reads the metadata of 32
+// consecutive queries at once (groups 32 * (gw + n * nwarp), n = 0, 1, ...)
+// and takes those in range by ballot.  With mid_list, the queries beyond
+// h_hi are queued there (chunk index) as they are met.
+struct ChunkScan {
+    uint32_t base, gw, nwarp, nq;  // 32 * n of the current group, warp, warps, chunk size
+    uint4 mt;                      // this lane's query of the group
+    uint32_t todo;                 // lanes of the group still to be processed
+};
+
+__device__ __forceinline__ ChunkScan chunk_scan(uint32_t nq) {
+    ChunkScan it;
+    it.nq = nq;
+    it.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    it.nwarp = (gridDim.x * blockDim.x) >> 5;
+    it.base = (uint32_t)-32;  // the first next_chunk_query step moves to n = 0
+    it.todo = 0;
+    return it;
+}
+
+__device__ __forceinline__ bool next_chunk_query(ChunkScan& it, const uint4* __restrict__ meta, uint32_t h_lo,
+                                                uint32_t h_hi, uint32_t* __restrict__ mid_list,
+                                                uint32_t* __restrict__ mid_n, uint32_t& i, uint4& mt) {
+    const uint32_t lane = lane_id();
+    while (it.todo == 0) {
+        it.base += 32;
+        const uint64_t first = (uint64_t)it.gw * 32 + (uint64_t)it.base * it.nwarp;
+        if (first >= it.nq) return false;
+        const uint64_t qi = first + lane;
+        it.mt = qi < it.nq ? meta[qi] : make_uint4(ESCALATED, 0, 0, 0);
+        const bool in = it.mt.x != ESCALATED && !(h_lo && it.mt.z <= h_lo);
+        if (mid_list && in && it.mt.z > h_hi) mid_list[atomicAdd(mid_n, 1u)] = (uint32_t)qi;
+        it.todo = __ballot_sync(FULL_MASK, in && it.mt.z <= h_hi);
+    }
+    const int l = __ffs(it.todo) - 1;
+    it.todo &= it.todo - 1;
+    i = it.gw * 32 + it.base * it.nwarp + (uint32_t)l;
+    mt.x = __shfl_sync(FULL_MASK, it.mt.x, l);
+    mt.y = __shfl_sync(FULL_MASK, it.mt.y, l);
+    mt.z = __shfl_sync(FULL_MASK, it.mt.z, l);
+    mt.w = __shfl_sync(FULL_MASK, it.mt.w, l);
+    return true;
+}
+
+// One medium-path query (chunk index i): bucket list to working memory,
+// hash-histogram scoring; a query that does not fit is queued for the
+// large path.
+template <int GB, class KeyT, class LocT>
+__device__ __forceinline__ void medium_query(const ClassifyDb& db, const ClassifyQuery& Q, uint32_t q0,
+                                             uint32_t list_cap, const uint64_t* __restrict__ glist,
+                                             const Scratch<uint16_t, KeyT>& S, uint32_t i, const uint4& mt,
+                                             uint32_t* __restrict__ ovf_list, uint32_t* __restrict__ ovf_n,
+                                             Counters& ctr, unsigned long long& n_medium) {
+    const uint32_t lane = lane_id();
+    const uint64_t* src = glist + (uint64_t)i * list_cap;
+    for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
+    __syncwarp();
+    const uint32_t q = q0 + i;
+    if (query_score<GB, LocT>(db, Q, q, S, mt.x, meta_sws(mt), ctr) == Q_ESCALATE) {
+        if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
+    } else {
+        ctr.features += meta_feat(mt);
+        ctr.found += mt.x;
+        ctr.sectors += mt.w;
+        ++ctr.queries;
+        ++n_medium;
+    }
+    __syncwarp();
+}
+
+// Medium path: the queries queued by the hash path's score kernel or the
+// sort path's largest size class, one warp each (work queue), KM_SLOTS
+// histogram slots per warp in shared memory, the bucket list taken over
+// from the lookup.  Queries that do not fit here either go to the large
+// path.
 template <int GB, class KeyT, class LocT>
 __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                    uint32_t list_cap,
@@ -902,29 +975,15 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
     const size_t per_warp = scratch_bytes<uint16_t, KeyT>(KM_SLOTS, list_cap, 0, 0);
     const Scratch<uint16_t, KeyT> S = carve<uint16_t, KeyT>(smem + w * per_warp, KM_SLOTS, list_cap, 0, 0, WIN_A);
     Counters ctr;
-    const uint32_t n = *mid_n;
     unsigned long long n_medium = 0;
+    const uint32_t n = *mid_n;
     for (;;) {
         uint32_t k = 0;
         if (lane == 0) k = atomicAdd(mid_work, 1u);
         k = __shfl_sync(FULL_MASK, k, 0);
         if (k >= n) break;
         const uint32_t i = mid_list[k];
-        const uint4 mt = meta[i];
-        const uint64_t* src = glist + (uint64_t)i * list_cap;
-        for (uint32_t j = lane; j < mt.x; j += 32) S.list[j] = __ldg(src + j);
-        __syncwarp();
-        const uint32_t q = q0 + i;
-        if (query_score<GB, LocT>(db, Q, q, S, mt.x, meta_sws(mt), ctr) == Q_ESCALATE) {
-            if (lane == 0) ovf_list[atomicAdd(ovf_n, 1u)] = q;
-        } else {
-            ctr.features += meta_feat(mt);
-            ctr.found += mt.x;
-            ctr.sectors += mt.w;
-            ++ctr.queries;
-            ++n_medium;
-        }
-        __syncwarp();
+        medium_query<GB, KeyT, LocT>(db, Q, q0, list_cap, glist, S, i, meta[i], ovf_list, ovf_n, ctr, n_medium);
     }
     flush_counters(Q, ctr, KC_MEDIUM);
     if (Q.counters && lane == 0 && n_medium) atomicAdd(Q.counters + 6, n_medium);
@@ -1139,15 +1198,17 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
     uint32_t D;
     {
         // bit r of starts: element lane*E + r (< H) begins a run
+        using Mask = typename std::conditional<(E > 32), unsigned long long, uint32_t>::type;
+        constexpr int MB = 8 * (int)sizeof(Mask);
         const uint32_t before = __shfl_up_sync(FULL_MASK, k[E - 1], 1);
-        uint32_t starts = 0;
+        Mask starts = 0;
 #pragma unroll
-        for (int r = 0; r < E; ++r) starts |= (uint32_t)(k[r] != (r ? k[r - 1] : before)) << r;
+        for (int r = 0; r < E; ++r) starts |= (Mask)(k[r] != (r ? k[r - 1] : before)) << r;
         const uint32_t first = lane * E;
         const uint32_t valid = H > first ? min((uint32_t)E, H - first) : 0u;
-        starts &= valid >= 32 ? 0xFFFFFFFFu : ((1u << valid) - 1u);
-        if (lane == 0 && H > 0) starts |= 1u;
-        const uint32_t n = __popc(starts);
+        starts &= valid >= (uint32_t)MB ? ~(Mask)0 : (((Mask)1 << valid) - 1);
+        if (lane == 0 && H > 0) starts |= 1;
+        const uint32_t n = (uint32_t)(MB == 64 ? __popcll((unsigned long long)starts) : __popc((uint32_t)starts));
         uint32_t inc = n;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -1161,7 +1222,7 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
         uint32_t pos = inc - n;
 #pragma unroll
         for (int r = 0; r < E; ++r) {
-            const uint32_t b = (starts >> r) & 1u;
+            const uint32_t b = (uint32_t)(starts >> r) & 1u;
             if (E >= 32) {
                 const uint32_t at = b ? pos : SORT_SPARE_SLOT<E>;
                 M.loc[at] = k[r];
@@ -1274,83 +1335,41 @@ __device__ __forceinline__ void query_sort(const ClassifyDb& db, const ClassifyQ
     write_result(Q, q, label, hits, top, mine);
 }
 
-// Queries of one sort-path class: a warp reads the metadata of 32
-// consecutive queries at once (groups 32 * (gw + n * nwarp), n = 0, 1, ...)
-// and takes those with h_lo < H <= 32*E; with `last`, queries beyond 32*E
-// are queued for the medium path as they are met.
-struct SortClassScan {
-    uint32_t base, gw, nwarp, nq;  // 32 * n of the current group, warp, warps, chunk size
-    uint4 mt;                      // this lane's query of the group
-    uint32_t todo;                 // lanes of the group still to be processed
-};
-
-template <int E>
-__device__ __forceinline__ bool next_sort_query(SortClassScan& it, const uint4* __restrict__ meta, uint32_t h_lo,
-                                               uint32_t last, uint32_t* __restrict__ mid_list,
-                                               uint32_t* __restrict__ mid_n, uint32_t& i, uint4& mt) {
-    const uint32_t lane = lane_id();
-    while (it.todo == 0) {
-        it.base += 32;
-        const uint64_t first = (uint64_t)it.gw * 32 + (uint64_t)it.base * it.nwarp;
-        if (first >= it.nq) return false;
-        const uint64_t qi = first + lane;
-        it.mt = qi < it.nq ? meta[qi] : make_uint4(ESCALATED, 0, 0, 0);
-        // taken by a smaller class, escalated, or outside the chunk
-        const bool skip = it.mt.x == ESCALATED || (h_lo && it.mt.z <= h_lo);
-        const bool big = !skip && it.mt.z > 32u * E;
-        if (last && big) mid_list[atomicAdd(mid_n, 1u)] = (uint32_t)qi;
-        it.todo = __ballot_sync(FULL_MASK, !skip && !big);
-    }
-    const int l = __ffs(it.todo) - 1;
-    it.todo &= it.todo - 1;
-    i = it.gw * 32 + it.base * it.nwarp + (uint32_t)l;
-    mt.x = __shfl_sync(FULL_MASK, it.mt.x, l);
-    mt.y = __shfl_sync(FULL_MASK, it.mt.y, l);
-    mt.z = __shfl_sync(FULL_MASK, it.mt.z, l);
-    mt.w = __shfl_sync(FULL_MASK, it.mt.w, l);
-    return true;
-}
-
 // Resident CTAs per SM that the register budget of a sort-path kernel is
-// sized for (shared memory admits 15, 10 and 5 for E = 8, 16, 32).
+// sized for (shared memory admits 15, 10, 5 and 3 for E = 8, 16, 32, 64).
 template <int E>
-constexpr int sort_min_ctas() { return E == 8 ? 8 : (E == 16 ? 7 : 4); }
+constexpr int sort_min_ctas() { return E == 8 ? 8 : (E == 16 ? 7 : (E == 32 ? 5 : 3)); }
 
 // Sort path over the chunk's queries with h_lo < H <= 32*E gathered
-// locations; with `last`, queries beyond 32*E are queued for the medium path.
+// locations; with mid_list (the largest class), larger ones are queued for
+// the medium path.
 template <int E>
 __global__ void __launch_bounds__(SORT_WARPS * 32, sort_min_ctas<E>()) k_classify_sort(ClassifyDb db, ClassifyQuery Q, uint32_t q0,
                                                                   uint32_t chunk, uint32_t list_cap,
                                                                   const uint64_t* __restrict__ glist,
                                                                   const uint4* __restrict__ meta, uint32_t h_lo,
-                                                                  uint32_t last, uint32_t* __restrict__ mid_list,
+                                                                  uint32_t* __restrict__ mid_list,
                                                                   uint32_t* __restrict__ mid_n) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const SortWarpMem M = sort_warp_mem<E>(smem + w * sort_warp_bytes<E>(list_cap), list_cap);
     Counters ctr;
     const uint32_t total = total_queries(Q);
-    if (q0 >= total) return;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nwarp = (gridDim.x * blockDim.x) >> 5;
-    SortClassScan it;
-    it.nq = min(chunk, total - q0);
-    it.gw = gw;
-    it.nwarp = nwarp;
-    it.base = (uint32_t)-32;  // the first next_sort_query step moves to n = 0
-    it.todo = 0;
-    uint32_t i;
-    uint4 mt;
-    uint32_t k[E];
-    while (next_sort_query<E>(it, meta, h_lo, last, mid_list, mid_n, i, mt)) {
-        sort_gather<E>(db, M, glist + (uint64_t)i * list_cap, mt.x, mt.z, k);
-        query_sort<E>(db, Q, q0 + i, M, meta_sws(mt), mt.z, k, ctr);
-        ctr.features += meta_feat(mt);
-        ctr.found += mt.x;
-        ctr.sectors += mt.w;
-        ++ctr.queries;
+    if (q0 < total) {
+        ChunkScan it = chunk_scan(min(chunk, total - q0));
+        uint32_t i;
+        uint4 mt;
+        uint32_t k[E];
+        while (next_chunk_query(it, meta, h_lo, 32u * E, mid_list, mid_n, i, mt)) {
+            sort_gather<E>(db, M, glist + (uint64_t)i * list_cap, mt.x, mt.z, k);
+            query_sort<E>(db, Q, q0 + i, M, meta_sws(mt), mt.z, k, ctr);
+            ctr.features += meta_feat(mt);
+            ctr.found += mt.x;
+            ctr.sectors += mt.w;
+            ++ctr.queries;
+        }
+        flush_counters(Q, ctr, E == 8 ? 1 : (E == 16 ? 2 : (E == 32 ? 3 : 6)));
     }
-    flush_counters(Q, ctr, E == 8 ? 1 : (E == 16 ? 2 : 3));
 }
 
 // Large path: queries queued by the shared-memory path, one warp each, with
@@ -1464,12 +1483,12 @@ LargeKernel pick_large(const ClassifyDb& db) {
 
 // Kernels and launch shapes of one launch set.
 using SortKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint32_t, const uint64_t*, const uint4*,
-                            uint32_t, uint32_t, uint32_t*, uint32_t*);
+                            uint32_t, uint32_t*, uint32_t*);
 
-// The sort path's size classes: queries of up to 256, 512 and 1024
-// gathered locations, each with its own kernel (E = 8, 16, 32 per lane).
-constexpr int N_SORT_CLASSES = 3;
-constexpr uint32_t SORT_CLASS_MAX[N_SORT_CLASSES] = {256, 512, 1024};
+// The sort path's size classes: queries of up to 256, 512, 1024 and 2048
+// gathered locations, each with its own kernel (E = 8, 16, 32, 64 per lane).
+constexpr int N_SORT_CLASSES = 4;
+constexpr uint32_t SORT_CLASS_MAX[N_SORT_CLASSES] = {256, 512, 1024, 2048};
 
 struct Geometry {
     LookupKernel kl;
@@ -1529,9 +1548,10 @@ cudaError_t geometry(const ClassifyDb& db, const Tuning& t, const ClassifyScratc
     g->sort = compact && t.score_mode != SCORE_HASH;
     g->n_sort = 0;
     if (g->sort) {
-        const SortKernel kts[N_SORT_CLASSES] = {k_classify_sort<8>, k_classify_sort<16>, k_classify_sort<32>};
+        const SortKernel kts[N_SORT_CLASSES] = {k_classify_sort<8>, k_classify_sort<16>, k_classify_sort<32>,
+                                                k_classify_sort<64>};
         const size_t bytes[N_SORT_CLASSES] = {sort_warp_bytes<8>(g->list_cap), sort_warp_bytes<16>(g->list_cap),
-                                              sort_warp_bytes<32>(g->list_cap)};
+                                              sort_warp_bytes<32>(g->list_cap), sort_warp_bytes<64>(g->list_cap)};
         for (int c2 = 0; c2 < N_SORT_CLASSES && SORT_CLASS_MAX[c2] <= t.sort_max; ++c2) {
             g->kt[c2] = kts[c2];
             g->smem_t[c2] = SORT_WARPS * bytes[c2];
@@ -1586,20 +1606,35 @@ cudaError_t launch_lookup(const Geometry& g, const ClassifyDb& db, const Classif
     return cudaGetLastError();
 }
 
-// Score (and the medium path for what it leaves) of the chunk at q0.
+// Medium path of the chunk at q0 (its queue).
+cudaError_t launch_medium(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
+                          uint32_t q0, cudaStream_t s) {
+    uint32_t* qc = queue_counters(sc);
+    MC_LAUNCH("classify_medium", s,
+              g.km<<<g.grid_m, MED_WARPS * 32, g.smem_m, s>>>(db, Q, q0, g.list_cap, sc.glist, sc.meta, sc.mid, qc + 2,
+                                                             qc + 3, sc.ovf, qc));
+    return cudaGetLastError();
+}
+
+// Score of the chunk at q0: the sort path's size classes (the largest one
+// queues the queries beyond it) or the hash path's score kernel (which
+// queues the queries whose histogram did not fit), then the medium path
+// for what they queued.
 cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
                          uint32_t q0, cudaStream_t s) {
     uint32_t* qc = queue_counters(sc);
     cudaError_t e = cudaMemsetAsync(qc + 2, 0, 2 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     if (g.sort) {
-        static const char* const names[N_SORT_CLASSES] = {"classify_sort256", "classify_sort512", "classify_sort1024"};
+        static const char* const names[N_SORT_CLASSES] = {"classify_sort256", "classify_sort512", "classify_sort1024",
+                                                          "classify_sort2048"};
         for (int c = 0; c < g.n_sort; ++c) {
             const uint32_t h_lo = c ? SORT_CLASS_MAX[c - 1] : 0;
-            const uint32_t last = c == g.n_sort - 1;
+            const bool last = c == g.n_sort - 1;
             MC_LAUNCH(names[c], s,
-                      g.kt[c]<<<g.grid_t[c], SORT_WARPS * 32, g.smem_t[c], s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist,
-                                                                                 sc.meta, h_lo, last, sc.mid, qc + 2));
+                      g.kt[c]<<<g.grid_t[c], SORT_WARPS * 32, g.smem_t[c], s>>>(
+                          db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, h_lo, last ? sc.mid : nullptr,
+                          last ? qc + 2 : nullptr));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
         }
     } else {
@@ -1608,10 +1643,7 @@ cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const Classify
                                                               sc.mid, qc + 2));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    MC_LAUNCH("classify_medium", s,
-              g.km<<<g.grid_m, MED_WARPS * 32, g.smem_m, s>>>(db, Q, q0, g.list_cap, sc.glist, sc.meta, sc.mid, qc + 2,
-                                                             qc + 3, sc.ovf, qc));
-    return cudaGetLastError();
+    return launch_medium(g, db, Q, sc, q0, s);
 }
 
 cudaError_t launch_large(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
@@ -1734,7 +1766,7 @@ bool tuning_valid(const Tuning& t) {
     };
     return in(t.hist_slots, {256, 512, 1024}) && in(t.probe_batch, {2, 4, 8}) && in(t.gather_batch, {4, 8, 16}) &&
            in(t.lookup_warps, {4, 8}) && in(t.score_warps, {2, 4}) && t.wide_keys <= 1 &&
-           in(t.score_mode, {SCORE_SORT, SCORE_HASH}) && in(t.sort_max, {256, 512, 1024});
+           in(t.score_mode, {SCORE_SORT, SCORE_HASH}) && in(t.sort_max, {256, 512, 1024, 2048});
 }
 
 uint32_t classify_default_large_warps() {
@@ -1921,7 +1953,7 @@ cudaError_t classify_autotune(const ClassifyDb& db, const ClassifyQuery& Q, cons
         }
         // the sort path, for each largest size class
         if (db.jbits) {
-            for (uint32_t smax : {256u, 512u, 1024u}) {
+            for (uint32_t smax : {256u, 512u, 1024u, 2048u}) {
                 Tuning t = cur;
                 t.score_mode = SCORE_SORT;
                 t.sort_max = smax;

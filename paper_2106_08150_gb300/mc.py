@@ -25,7 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 MC_OK, MC_ERR_ARG, MC_ERR_STATE, MC_ERR_OOM, MC_ERR_TABLE_FULL, MC_ERR_TIMEOUT, MC_ERR_CUDA, MC_ERR_CAPACITY = range(8)
 MC_NO_TAXON = 0xFFFFFFFF
-MC_DEBUG_COUNTERS = 25  # entries of mc_classify_debug's counters
+MC_DEBUG_COUNTERS = 28  # entries of mc_classify_debug's counters
 MC_NO_TARGET = 0xFFFFFFFF
 MC_MAX_CANDIDATES = 8
 

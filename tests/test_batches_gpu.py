@@ -98,6 +98,7 @@ TUNINGS = [
     dict(sort_max=256),
     dict(sort_max=512, probe_batch=8, lookup_warps=4),
     dict(score_mode=1, sort_max=1024, probe_batch=2),
+    dict(score_mode=1, sort_max=2048, probe_batch=4),
     dict(score_mode=2),
     dict(score_mode=2, hist_slots=256, probe_batch=2, gather_batch=4, lookup_warps=4, score_warps=2),
     dict(score_mode=2, hist_slots=1024, probe_batch=8, gather_batch=16, lookup_warps=8, score_warps=4),
@@ -145,7 +146,7 @@ def test_plan_replays_new_batch_sets(mc, setup):
     total = sum(b.nq for b in dbs)
     plan = mc.Plan(db.handle, cp, max_batches=len(dbs), max_queries=total)
     try:
-        assert plan.kernels == 6  # lookup, three sort-path size classes, medium path, large path
+        assert plan.kernels == 7  # lookup, four sort-path size classes, medium path, large path
         for subset in [list(range(len(dbs))), [3, 0, 5], [7], list(range(len(dbs)))[::-1], []]:
             for b in dbs:
                 b.reset()
@@ -213,7 +214,7 @@ def test_autotune_picks_a_valid_setting_with_equal_results(mc, setup):
     dbs = [DevBatch(mc, *b[:3]) for b in batches]
     want = [_per_batch(mc, db, cp, b) for b in dbs]
     best, rec = mc.mc_autotune(db.handle, cp, [b.desc for b in dbs], reps=2)
-    assert len(rec) == 6 + 18 + 3  # lookup shapes, hash-path shapes, sort-path size limits
+    assert len(rec) == 6 + 18 + 4  # lookup shapes, hash-path shapes, sort-path size limits
     assert {r[0] for r in rec} == {0, 1} and all(r[2] > 0 for r in rec)
     bt = best.as_dict()
     assert bt["hist_slots"] in (256, 512, 1024) and bt["probe_batch"] in (2, 4, 8)
