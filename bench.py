@@ -66,6 +66,8 @@ def parse_args():
                     help="offered loads of the served section, as fractions of the tuned batched throughput")
     ap.add_argument("--serve-pool", type=int, default=32, help="distinct jobs the served section cycles through")
     ap.add_argument("--no-autotune", action="store_true", help="default launch shape for the classify kernels")
+    ap.add_argument("--no-insert-comparison", action="store_true",
+                    help="skip timing the hash-table insert build beside the sort build")
     return ap.parse_args()
 
 
@@ -551,12 +553,64 @@ def run_gpu(args, rank, world, local_rank):
     }
     if w.held is not None and world == 1:
         out["extension"] = run_extension(w, dev, stream, tuned)
+    if world == 1 and not args.no_insert_comparison:
+        out["build_insert_comparison"] = run_insert_comparison(w, dev, stream, kernels, args.steps, st)
     if args.batches and world == 1:
         out["batched"] = run_batched(args, w, dev, stream)
     if args.serve_seconds > 0 and world == 1 and w.held is not None:
         rate = out.get("batched", {}).get("graph_tuned", {}).get("mreads_s")
         out["served"] = run_served_sweep(args, w, dev, stream, rate, tuned)
     return out, w
+
+
+# ------------------------------------------- build primitive comparison
+# kernels of the library's build after sketching: sort (digit totals and
+# four radix passes) and layout (finalize and feature table)
+SORT_BUILD_KERNELS = {"sort": ["radix_totals", "radix_pass"],
+                      "layout": ["fin_count", "fin_emit", "tab_dispmax", "exclusive_max_i64", "tab_emit",
+                                 "scan_tile_sums", "scan_downsweep"]}
+
+
+def run_insert_comparison(w, dev, stream, kernels, steps, st, reps: int = 2):
+    """The paper's build primitive (a hash table keyed by feature, filled
+    with warp-aggregated atomics, Sections 5.1 and 5.3) against the
+    library's sort-based build, on the same pairs: the sketches of all the
+    workload's windows.  The hash build is membench.hash_insert_build
+    (count, scan, fill; last of `reps` runs); the sort build's times are
+    its kernels in the timed step (CUDA events).  Both exclude sketching."""
+    import torch
+    import membench
+    from paper_2106_08150_gb300 import mc
+    p = w.db_params
+    prm = mc.db_params(**p)
+    n_t = w.n_targets
+    d_g = torch.from_numpy(w.genomes).to(dev)
+    d_go = torch.from_numpy(w.goffs.view(np.int64)).to(dev)
+    win = torch.zeros(n_t + 1, dtype=torch.int64, device=dev)
+    mc.mc_window_offsets(prm, n_t, d_go, win, stream=stream)
+    stream.synchronize()
+    n_win = int(win[-1].item())
+    s = p["sketch_size"]
+    sk = torch.empty(max(1, n_win * s), dtype=torch.int32, device=dev)
+    cnt = torch.empty(max(1, n_win), dtype=torch.int32, device=dev)
+    mc.mc_sketch(prm, n_t, d_g, d_go, win, n_win, sk, cnt, stream=stream)
+    stream.synchronize()
+    del d_g
+    log_slots = int(st["table_slots"]).bit_length() - 1
+    res = None
+    for _ in range(reps):
+        res = membench.hash_insert_build(sk, cnt, n_win, s, p["bucket_cap"], log_slots, stream=stream)
+        torch.cuda.empty_cache()
+    sort = {}
+    for part, names in SORT_BUILD_KERNELS.items():
+        sort[part + "_ms"] = round(sum(kernels[k]["total_ms"] for k in names if k in kernels) / steps, 3)
+    sort["total_ms"] = round(sort["sort_ms"] + sort["layout_ms"], 3)
+    return {"pairs": int(st["n_pairs"]), "hash_insert": res, "sort_build": sort,
+            "same_keys": res["n_keys"] == int(st["n_keys"]), "same_kept": res["n_kept"] == int(st["n_locations"]),
+            "note": "hash insert: count (atomicCAS/atomicAdd, warp-aggregated by __match_any_sync) + exclusive scan "
+                    "+ fill (atomic cursors), buckets in arrival order, cap keeps the first arrivals; sort build: "
+                    "radix sort + finalize + feature table, buckets ordered, cap keeps the smallest; sketching "
+                    "excluded from both"}
 
 
 # ------------------------------------------------------ live extension

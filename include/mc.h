@@ -303,14 +303,14 @@ typedef struct mc_batch {
  *                loc_bytes == 4) and histogram keys of that width
  *                (wide_keys 0); otherwise the hash path is used.
  *  sort_max    : sort path: largest number of gathered locations a query
- *                may have to be sorted, 256, 512, 1024 or 2048 (default); each
+ *                may have to be sorted, 256, 512, 1024 (default) or 2048; each
  *                size class up to it has its own kernel; larger queries go
  *                to the hash path's medium and large kernels.
  *  hist_slots  : hash path: shared-memory histogram slots per query: 256,
  *                512 (default) or 1024.  Queries whose distinct locations
  *                do not fit go to the medium (2,048 slots) and large paths.
  *  probe_batch : feature-table probes in flight per lane (32 lanes probe
- *                together): 2, 4 (default) or 8.
+ *                together): 2 (default), 4 or 8.
  *  gather_batch: hash path: bucket-location loads in flight per lane: 4, 8
  *                (default) or 16.
  *  lookup_warps: warps per CTA of the lookup kernel: 4 or 8 (default).

@@ -15,6 +15,7 @@ import subprocess
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "membench.cu")
+_SRC_INSERT = os.path.join(_HERE, "insertbench.cu")
 _LIB = os.path.join(_HERE, "libmembench.so")
 _lib = None
 
@@ -28,10 +29,11 @@ def _nvcc() -> str:
 
 def build(force: bool = False) -> str:
     """Compile membench.cu for sm_103a into libmembench.so."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_INSERT))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
-                               "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, _SRC])
+                               "-std=c++17", "-Xcompiler", "-fPIC", "-shared", "-o", tmp, _SRC, _SRC_INSERT])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -46,6 +48,13 @@ def _load():
                                              ctypes.POINTER(ctypes.c_double)]
         lib.membench_random_read.restype = ctypes.c_int
         lib.membench_last_error.restype = ctypes.c_char_p
+        u32, u64, vp = ctypes.c_uint32, ctypes.c_uint64, ctypes.c_void_p
+        pd = ctypes.POINTER(ctypes.c_double)
+        lib.membench_insert_count.argtypes = [vp, vp, u64, u32, u32, u32, vp, vp, vp, vp, pd]
+        lib.membench_insert_count.restype = ctypes.c_int
+        lib.membench_insert_fill.argtypes = [vp, vp, u64, u32, u32, u32, vp, vp, vp, vp, u32, vp, vp, pd]
+        lib.membench_insert_fill.restype = ctypes.c_int
+        lib.membench_insert_last_error.restype = ctypes.c_char_p
         _lib = lib
     return _lib
 
@@ -61,3 +70,59 @@ def random_read_gbs(buf_bytes: int, width: int, n_reads: int, stream: int | None
         raise ValueError(lib.membench_last_error().decode()) if rc == 1 else \
             RuntimeError(lib.membench_last_error().decode())
     return v.value
+
+
+def _insert_check(lib, rc: int):
+    if rc != 0:
+        msg = lib.membench_insert_last_error().decode()
+        raise ValueError(msg) if rc == 1 else RuntimeError(msg)
+
+
+def hash_insert_build(sketch, counts, n_windows: int, s: int, cap: int, log_slots: int, stream=None,
+                      max_probe: int = 4096, return_tables: bool = False) -> dict:
+    """The paper's build primitive, timed: every (feature, window) pair of
+    the window sketches (device tensors: sketch int32[n_windows * s],
+    counts int32[n_windows], as mc_sketch writes them) inserted into a hash
+    table of 2^log_slots slots with warp-aggregated atomics, at most `cap`
+    locations per feature (insertbench.cu).  Passes: count, exclusive scan
+    of min(count, cap) (torch), fill.  Returns their times in ms (CUDA
+    events on `stream`, default the current torch stream) and the table's
+    distinct features and kept locations (with return_tables, also the
+    device tensors keys, count, offset and vals)."""
+    import torch
+    lib = _load()
+    dev = sketch.device
+    st = torch.cuda.current_stream(dev) if stream is None else stream
+    handle = ctypes.c_void_p(st.cuda_stream)
+    slots = 1 << log_slots
+    keys = torch.full((slots,), -1, dtype=torch.int32, device=dev)
+    cnt = torch.zeros(slots, dtype=torch.int32, device=dev)
+    err = torch.zeros(1, dtype=torch.int32, device=dev)
+    ms_count, ms_fill = ctypes.c_double(), ctypes.c_double()
+    torch.cuda.synchronize(dev)
+    _insert_check(lib, lib.membench_insert_count(sketch.data_ptr(), counts.data_ptr(), n_windows, s, log_slots,
+                                                 max_probe, keys.data_ptr(), cnt.data_ptr(), err.data_ptr(), handle,
+                                                 ctypes.byref(ms_count)))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(st):
+        a.record()
+        capped = torch.clamp(cnt, max=cap).to(torch.int64)
+        offset = torch.cumsum(capped, 0)
+        n_kept = int(offset[-1].item()) if slots else 0
+        offset -= capped
+        b.record()
+    b.synchronize()
+    ms_scan = a.elapsed_time(b)
+    del capped
+    cursor = torch.zeros(slots, dtype=torch.int32, device=dev)
+    vals = torch.empty(max(1, n_kept), dtype=torch.int32, device=dev)
+    _insert_check(lib, lib.membench_insert_fill(sketch.data_ptr(), counts.data_ptr(), n_windows, s, log_slots,
+                                                max_probe, keys.data_ptr(), offset.data_ptr(), cursor.data_ptr(),
+                                                vals.data_ptr(), cap, err.data_ptr(), handle, ctypes.byref(ms_fill)))
+    n_keys = int((keys != -1).sum().item())
+    out = {"count_ms": round(ms_count.value, 3), "scan_ms": round(ms_scan, 3), "fill_ms": round(ms_fill.value, 3),
+           "total_ms": round(ms_count.value + ms_scan + ms_fill.value, 3), "n_keys": n_keys, "n_kept": n_kept,
+           "slots": slots}
+    if return_tables:
+        out["tables"] = {"keys": keys, "count": cnt, "offset": offset, "vals": vals}
+    return out

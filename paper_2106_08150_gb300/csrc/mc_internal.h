@@ -215,7 +215,7 @@ constexpr uint32_t SCORE_SORT = 1, SCORE_HASH = 2;
 struct Tuning {
     uint32_t hist_slots, probe_batch, gather_batch, lookup_warps, score_warps, wide_keys, score_mode, sort_max;
 };
-constexpr Tuning DEFAULT_TUNING{512, 4, 8, 8, 4, 0, SCORE_SORT, 2048};
+constexpr Tuning DEFAULT_TUNING{512, 2, 8, 8, 4, 0, SCORE_SORT, 1024};
 bool tuning_valid(const Tuning& t);
 
 // Device scratch of one classify launch set for up to n_q_cap queries.

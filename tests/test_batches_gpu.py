@@ -146,7 +146,7 @@ def test_plan_replays_new_batch_sets(mc, setup):
     total = sum(b.nq for b in dbs)
     plan = mc.Plan(db.handle, cp, max_batches=len(dbs), max_queries=total)
     try:
-        assert plan.kernels == 7  # lookup, four sort-path size classes, medium path, large path
+        assert plan.kernels == 6  # lookup, sort-path size classes up to 1024 (default), medium path, large path
         for subset in [list(range(len(dbs))), [3, 0, 5], [7], list(range(len(dbs)))[::-1], []]:
             for b in dbs:
                 b.reset()
