@@ -393,8 +393,9 @@ def run_gpu(args, rank, world, local_rank):
 
     # end-to-end through the public API with host buffers (pinned), copies
     # timed every step.  The genome copy is split into chunks on a copy
-    # stream so that adding chunk i overlaps copying chunk i+1, and the
-    # reads are copied while the database is built.
+    # stream so that adding chunk i overlaps copying chunk i+1; the reads
+    # follow in parts, each classified (its own mc_classify call into its
+    # slice of the outputs) as soon as it has arrived.
     e2e = None
     if not args.no_e2e:
         n_chunks = 8
@@ -404,14 +405,24 @@ def run_gpu(args, rank, world, local_rank):
         chunks = [(int(a), int(b)) for a, b in zip(cut[:-1], cut[1:]) if b > a]
         hg = torch.from_numpy(w.genomes).pin_memory()
         hgo = [torch.from_numpy((w.goffs[a:b + 1] - w.goffs[a]).view(np.int64)).pin_memory() for a, b in chunks]
-        hr, hro = torch.from_numpy(w.reads).pin_memory(), torch.from_numpy(w.roffs.view(np.int64)).pin_memory()
-        hqo = torch.from_numpy(w.qoffs.view(np.int32)).pin_memory()
+        hr = torch.from_numpy(w.reads).pin_memory()
+        # read parts: queries [q_a, q_b), their mates and bases, offsets rebased
+        n_parts = 4
+        qcut = np.linspace(0, nq, n_parts + 1).astype(np.int64)
+        rparts = []
+        for qa, qb in zip(qcut[:-1], qcut[1:]):
+            ma, mb = int(w.qoffs[qa]), int(w.qoffs[qb])
+            ba, bb = int(w.roffs[ma]), int(w.roffs[mb])
+            ho = torch.from_numpy((w.roffs[ma:mb + 1] - np.uint64(ba)).view(np.int64)).pin_memory()
+            hq = torch.from_numpy((w.qoffs[qa:qb + 1] - np.uint32(ma)).view(np.int32)).pin_memory()
+            rparts.append((int(qa), int(qb), mb - ma, ba, bb, ho, hq))
         hl = torch.empty(nq, dtype=torch.int32).pin_memory()
         hh = torch.empty(nq, dtype=torch.int32).pin_memory()
         dg = torch.empty_like(hg, device=dev)
         dgo = [torch.empty_like(x, device=dev) for x in hgo]
-        dr, dro, dqo = torch.empty_like(hr, device=dev), torch.empty_like(hro, device=dev), torch.empty_like(hqo, device=dev)
-        h2d = sum(x.numel() * x.element_size() for x in [hg, hr, hro, hqo] + hgo)
+        dr = torch.empty_like(hr, device=dev)
+        dparts = [(torch.empty_like(ho, device=dev), torch.empty_like(hq, device=dev)) for *_, ho, hq in rparts]
+        h2d = sum(x.numel() * x.element_size() for x in [hg, hr] + hgo + [t for *_, ho, hq in rparts for t in (ho, hq)])
         d2h = 2 * nq * 4
         copy_stream = torch.cuda.Stream(device=dev)
 
@@ -427,11 +438,14 @@ def run_gpu(args, rank, world, local_rank):
                     ev = torch.cuda.Event()
                     ev.record(copy_stream)
                     evs.append(ev)
-                dr.copy_(hr, non_blocking=True)
-                dro.copy_(hro, non_blocking=True)
-                dqo.copy_(hqo, non_blocking=True)
-                ev_reads = torch.cuda.Event()
-                ev_reads.record(copy_stream)
+                ev_parts = []
+                for (qa, qb, nm, ba, bb, ho, hq), (do_, dq_) in zip(rparts, dparts):
+                    dr[ba:bb].copy_(hr[ba:bb], non_blocking=True)
+                    do_.copy_(ho, non_blocking=True)
+                    dq_.copy_(hq, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(copy_stream)
+                    ev_parts.append(ev)
             tp = [time.perf_counter()]
             db = mc.Database.create(w.parent, stream=stream, **w.db_params)
             if tuned is not None:
@@ -443,8 +457,10 @@ def run_gpu(args, rank, world, local_rank):
             tp.append(time.perf_counter())
             db.finalize()
             tp.append(time.perf_counter())
-            stream.wait_event(ev_reads)
-            mc.mc_classify(db.handle, cp, w.n_seq, dr, dro, nq, dqo, label, hits, top, stream=stream)
+            for (qa, qb, nm, ba, bb, ho, hq), (do_, dq_), ev in zip(rparts, dparts, ev_parts):
+                stream.wait_event(ev)
+                mc.mc_classify(db.handle, cp, nm, dr[ba:], do_, qb - qa, dq_, label[qa:qb], hits[qa:qb], top[qa:qb],
+                               stream=stream)
             with torch.cuda.stream(stream):
                 hl.copy_(label, non_blocking=True)
                 hh.copy_(hits, non_blocking=True)
