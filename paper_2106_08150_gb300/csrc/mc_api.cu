@@ -1103,8 +1103,7 @@ namespace {
 
 mc::ClassifyQuery batch_query(const mc_db* db, const mc_classify_params* p, uint32_t n_q_cap,
                               const mc::BatchDesc* desc, const uint32_t* bhdr) {
-    mc::ClassifyQuery q;
-    std::memset(&q, 0, sizeof q);
+    mc::ClassifyQuery q{};
     q.n_q = n_q_cap;
     q.m = p->max_candidates;
     q.hits_min = p->hits_min;
