@@ -884,22 +884,23 @@ __global__ void __launch_bounds__(CLS_WARPS * 32, 8) k_classify_score(ClassifyDb
 }
 
 // Queries of the chunk with h_lo < H <= h_hi gathered locations (h_lo = 0:
-// no lower bound), not escalated: a warp reads the metadata of 32
-// consecutive queries at once (groups 32 * (gw + n * nwarp), n = 0, 1, ...)
-// and takes those in range by ballot.  With mid_list, the queries beyond
-// h_hi are queued there (chunk index) as they are met.
+// no lower bound), not escalated: a warp takes groups of 32 consecutive
+// queries from a counter (*ctr, zero before the launch), reads their
+// metadata at once and takes those in range by ballot, so that warps that
+// start late take fewer groups.  With mid_list, the queries beyond h_hi
+// are queued there (chunk index) as they are met.
 struct ChunkScan {
-    uint32_t base, gw, nwarp, nq;  // 32 * n of the current group, warp, warps, chunk size
-    uint4 mt;                      // this lane's query of the group
-    uint32_t todo;                 // lanes of the group still to be processed
+    uint32_t base, nq;  // first query of the current group, chunk size
+    uint32_t* ctr;      // next group
+    uint4 mt;           // this lane's query of the group
+    uint32_t todo;      // lanes of the group still to be processed
 };
 
-__device__ __forceinline__ ChunkScan chunk_scan(uint32_t nq) {
+__device__ __forceinline__ ChunkScan chunk_scan(uint32_t nq, uint32_t* ctr) {
     ChunkScan it;
     it.nq = nq;
-    it.gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    it.nwarp = (gridDim.x * blockDim.x) >> 5;
-    it.base = (uint32_t)-32;  // the first next_chunk_query step moves to n = 0
+    it.ctr = ctr;
+    it.base = 0;
     it.todo = 0;
     return it;
 }
@@ -909,9 +910,12 @@ __device__ __forceinline__ bool next_chunk_query(ChunkScan& it, const uint4* __r
                                                 uint32_t* __restrict__ mid_n, uint32_t& i, uint4& mt) {
     const uint32_t lane = lane_id();
     while (it.todo == 0) {
-        it.base += 32;
-        const uint64_t first = (uint64_t)it.gw * 32 + (uint64_t)it.base * it.nwarp;
+        uint32_t g = 0;
+        if (lane == 0) g = atomicAdd(it.ctr, 1u);
+        g = __shfl_sync(FULL_MASK, g, 0);
+        const uint64_t first = (uint64_t)g * 32;
         if (first >= it.nq) return false;
+        it.base = (uint32_t)first;
         const uint64_t qi = first + lane;
         it.mt = qi < it.nq ? meta[qi] : make_uint4(ESCALATED, 0, 0, 0);
         const bool in = it.mt.x != ESCALATED && !(h_lo && it.mt.z <= h_lo);
@@ -920,7 +924,7 @@ __device__ __forceinline__ bool next_chunk_query(ChunkScan& it, const uint4* __r
     }
     const int l = __ffs(it.todo) - 1;
     it.todo &= it.todo - 1;
-    i = it.gw * 32 + it.base * it.nwarp + (uint32_t)l;
+    i = it.base + (uint32_t)l;
     mt.x = __shfl_sync(FULL_MASK, it.mt.x, l);
     mt.y = __shfl_sync(FULL_MASK, it.mt.y, l);
     mt.z = __shfl_sync(FULL_MASK, it.mt.z, l);
@@ -976,6 +980,10 @@ __global__ void __launch_bounds__(MED_WARPS * 32) k_classify_medium(ClassifyDb d
     const Scratch<uint16_t, KeyT> S = carve<uint16_t, KeyT>(smem + w * per_warp, KM_SLOTS, list_cap, 0, 0, WIN_A);
     Counters ctr;
     unsigned long long n_medium = 0;
+    // a kernel launched after this one with programmatic stream
+    // serialization (a sort-path class, which shares no data with this one)
+    // may start while this one's few long queries finish
+    asm volatile("griddepcontrol.launch_dependents;");
     const uint32_t n = *mid_n;
     for (;;) {
         uint32_t k = 0;
@@ -1349,14 +1357,15 @@ __global__ void __launch_bounds__(SORT_WARPS * 32, sort_min_ctas<E>()) k_classif
                                                                   const uint64_t* __restrict__ glist,
                                                                   const uint4* __restrict__ meta, uint32_t h_lo,
                                                                   uint32_t* __restrict__ mid_list,
-                                                                  uint32_t* __restrict__ mid_n) {
+                                                                  uint32_t* __restrict__ mid_n,
+                                                                  uint32_t* __restrict__ group_ctr) {
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5;
     const SortWarpMem M = sort_warp_mem<E>(smem + w * sort_warp_bytes<E>(list_cap), list_cap);
     Counters ctr;
     const uint32_t total = total_queries(Q);
     if (q0 < total) {
-        ChunkScan it = chunk_scan(min(chunk, total - q0));
+        ChunkScan it = chunk_scan(min(chunk, total - q0), group_ctr);
         uint32_t i;
         uint4 mt;
         uint32_t k[E];
@@ -1370,6 +1379,12 @@ __global__ void __launch_bounds__(SORT_WARPS * 32, sort_min_ctas<E>()) k_classif
         }
         flush_counters(Q, ctr, E == 8 ? 1 : (E == 16 ? 2 : (E == 32 ? 3 : 6)));
     }
+    // Launched as a programmatic dependent of the medium path, this kernel
+    // may run alongside it; waiting for that grid before exiting makes this
+    // kernel's completion imply the medium path's, so that later work in
+    // the stream or graph never overtakes it.  A no-op for an ordinary
+    // launch.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // Large path: queries queued by the shared-memory path, one warp each, with
@@ -1483,7 +1498,7 @@ LargeKernel pick_large(const ClassifyDb& db) {
 
 // Kernels and launch shapes of one launch set.
 using SortKernel = void (*)(ClassifyDb, ClassifyQuery, uint32_t, uint32_t, uint32_t, const uint64_t*, const uint4*,
-                            uint32_t, uint32_t*, uint32_t*);
+                            uint32_t, uint32_t*, uint32_t*, uint32_t*);
 
 // The sort path's size classes: queries of up to 256, 512, 1024 and 2048
 // gathered locations, each with its own kernel (E = 8, 16, 32, 64 per lane).
@@ -1585,7 +1600,7 @@ constexpr ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, u
     const size_t per_warp_b = scratch_bytes<uint32_t>(KB_SLOTS, LIST_B, LIST_B, BUF_B);
     L.chunk = n_q_cap < CHUNK ? n_q_cap : CHUNK;
     L.ovf = 0;
-    L.meta = align256(L.ovf + ((size_t)n_q_cap + 8) * 4);
+    L.meta = align256(L.ovf + ((size_t)n_q_cap + 16) * 4);
     L.mid = align256(L.meta + (size_t)L.chunk * sizeof(uint4));
     L.glist = align256(L.mid + (size_t)L.chunk * 4);
     L.large = align256(L.glist + (size_t)L.chunk * list_cap * 8);
@@ -1595,7 +1610,8 @@ constexpr ScratchLayout scratch_layout(uint32_t n_q_cap, uint32_t sketch_size, u
 
 // Queue counters: [0] large-path queue length, [1] large-path work counter,
 // [2] medium-path queue length, [3] medium-path work counter, [4] saved
-// large-path queue length (autotuner).
+// large-path queue length (autotuner), [5 + c] group counter of sort-path
+// class c.
 uint32_t* queue_counters(const ClassifyScratch& sc) { return sc.ovf + sc.n_q_cap; }
 
 cudaError_t launch_lookup(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
@@ -1616,34 +1632,64 @@ cudaError_t launch_medium(const Geometry& g, const ClassifyDb& db, const Classif
     return cudaGetLastError();
 }
 
-// Score of the chunk at q0: the sort path's size classes (the largest one
-// queues the queries beyond it) or the hash path's score kernel (which
-// queues the queries whose histogram did not fit), then the medium path
-// for what they queued.
+// Score of the chunk at q0.  Sort path: the largest size class first (it
+// queues the queries beyond it), then the medium path, then the other
+// classes, the most populous one (512) launched with programmatic stream
+// serialization so that it fills the SMs the medium path's few long
+// queries leave idle (they share no data: the sort kernels read the
+// lookup's outputs and write other queries' results; their groups of
+// queries come from a counter, so the CTAs that start late take fewer).
+// Hash path: the score kernel, then the medium path for the queries whose
+// histogram did not fit.
 cudaError_t launch_score(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
                          uint32_t q0, cudaStream_t s) {
     uint32_t* qc = queue_counters(sc);
-    cudaError_t e = cudaMemsetAsync(qc + 2, 0, 2 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(qc + 2, 0, 2 * sizeof(uint32_t), s);  // medium queue; [4] is kept
     if (e != cudaSuccess) return e;
-    if (g.sort) {
-        static const char* const names[N_SORT_CLASSES] = {"classify_sort256", "classify_sort512", "classify_sort1024",
-                                                          "classify_sort2048"};
-        for (int c = 0; c < g.n_sort; ++c) {
-            const uint32_t h_lo = c ? SORT_CLASS_MAX[c - 1] : 0;
-            const bool last = c == g.n_sort - 1;
-            MC_LAUNCH(names[c], s,
-                      g.kt[c]<<<g.grid_t[c], SORT_WARPS * 32, g.smem_t[c], s>>>(
-                          db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta, h_lo, last ? sc.mid : nullptr,
-                          last ? qc + 2 : nullptr));
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        }
-    } else {
+    if (g.sort && (e = cudaMemsetAsync(qc + 5, 0, N_SORT_CLASSES * sizeof(uint32_t), s)) != cudaSuccess) return e;
+    if (!g.sort) {
         MC_LAUNCH("classify_score", s,
                   g.ks<<<g.grid_s, g.threads_s, g.smem_s, s>>>(db, Q, q0, sc.chunk, g.list_cap, sc.glist, sc.meta,
                                                               sc.mid, qc + 2));
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        return launch_medium(g, db, Q, sc, q0, s);
     }
-    return launch_medium(g, db, Q, sc, q0, s);
+    static const char* const names[N_SORT_CLASSES] = {"classify_sort256", "classify_sort512", "classify_sort1024",
+                                                      "classify_sort2048"};
+    const int last = g.n_sort - 1;
+    const int pdl = last >= 2 ? 1 : -1;  // the class launched as the medium path's dependent
+    int order[N_SORT_CLASSES + 1], n = 0;
+    order[n++] = last;
+    order[n++] = -1;  // medium path
+    if (pdl >= 0) order[n++] = pdl;
+    for (int c = 0; c < last; ++c)
+        if (c != pdl) order[n++] = c;
+    for (int k = 0; k < n; ++k) {
+        const int c = order[k];
+        if (c < 0) {
+            if ((e = launch_medium(g, db, Q, sc, q0, s)) != cudaSuccess) return e;
+            continue;
+        }
+        const uint32_t h_lo = c ? SORT_CLASS_MAX[c - 1] : 0;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g.grid_t[c]);
+        cfg.blockDim = dim3(SORT_WARPS * 32);
+        cfg.dynamicSmemBytes = g.smem_t[c];
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = c == pdl ? 1 : 0;
+        uint32_t* ml = c == last ? sc.mid : nullptr;
+        uint32_t* mn = c == last ? qc + 2 : nullptr;
+        MC_LAUNCH(names[c], s,
+                  e = cudaLaunchKernelEx(&cfg, g.kt[c], db, Q, q0, (uint32_t)sc.chunk, g.list_cap,
+                                         (const uint64_t*)sc.glist, (const uint4*)sc.meta, h_lo, ml, mn, qc + 5 + c));
+        if (e != cudaSuccess) return e;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_large(const Geometry& g, const ClassifyDb& db, const ClassifyQuery& Q, const ClassifyScratch& sc,
