@@ -1,10 +1,14 @@
-"""Random-access read bandwidth of the GPU, for the benchmark's roofline.
+"""Measurement aids of bench.py (libmembench.so), not part of the
+classification library.
 
-The classification kernels probe the feature table and gather buckets with
-16-32 byte reads at random positions, which HBM serves far below its copy
-bandwidth.  `random_read_gbs` measures that rate on the current device
-(membench.cu, built into libmembench.so next to it).  It is a measurement
-aid of bench.py, not part of the classification library.
+- `random_read_gbs`: random-access read bandwidth of the GPU, for the
+  benchmark's roofline.  The classification kernels probe the feature table
+  and gather buckets with 16-32 byte reads at random positions, which HBM
+  serves far below its copy bandwidth (membench.cu).
+- `hash_insert_build`: the paper's build primitive, every (feature,
+  location) pair inserted into a hash table with warp-aggregated atomics
+  (insertbench.cu), timed on the same pairs as the library's sort-based
+  build.
 """
 from __future__ import annotations
 
