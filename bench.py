@@ -406,16 +406,9 @@ def run_gpu(args, rank, world, local_rank):
         hg = torch.from_numpy(w.genomes).pin_memory()
         hgo = [torch.from_numpy((w.goffs[a:b + 1] - w.goffs[a]).view(np.int64)).pin_memory() for a, b in chunks]
         hr = torch.from_numpy(w.reads).pin_memory()
-        # read parts: queries [q_a, q_b), their mates and bases, offsets rebased
-        n_parts = 4
-        qcut = np.linspace(0, nq, n_parts + 1).astype(np.int64)
-        rparts = []
-        for qa, qb in zip(qcut[:-1], qcut[1:]):
-            ma, mb = int(w.qoffs[qa]), int(w.qoffs[qb])
-            ba, bb = int(w.roffs[ma]), int(w.roffs[mb])
-            ho = torch.from_numpy((w.roffs[ma:mb + 1] - np.uint64(ba)).view(np.int64)).pin_memory()
-            hq = torch.from_numpy((w.qoffs[qa:qb + 1] - np.uint32(ma)).view(np.int32)).pin_memory()
-            rparts.append((int(qa), int(qb), mb - ma, ba, bb, ho, hq))
+        rparts = [(qa, qb, nm, ba, bb, torch.from_numpy(ro.view(np.int64)).pin_memory(),
+                   torch.from_numpy(qo.view(np.int32)).pin_memory())
+                  for qa, qb, nm, ba, bb, ro, qo in read_parts(w.roffs, w.qoffs, 4)]
         hl = torch.empty(nq, dtype=torch.int32).pin_memory()
         hh = torch.empty(nq, dtype=torch.int32).pin_memory()
         dg = torch.empty_like(hg, device=dev)
@@ -577,6 +570,24 @@ def run_gpu(args, rank, world, local_rank):
         rate = out.get("batched", {}).get("graph_tuned", {}).get("mreads_s")
         out["served"] = run_served_sweep(args, w, dev, stream, rate, tuned)
     return out, w
+
+
+def read_parts(roffs: np.ndarray, qoffs: np.ndarray, n_parts: int) -> list:
+    """The queries split into n_parts consecutive parts for classification
+    in pieces: per part (q_a, q_b, mates, b_a, b_b, roffs, qoffs) with its
+    queries [q_a, q_b), its bases [b_a, b_b) of the read array and its mate
+    and query offsets rebased to start at 0 (u64 / u32), so that each part is
+    one self-contained mc_classify call on reads[b_a:]."""
+    nq = len(qoffs) - 1
+    qcut = np.linspace(0, nq, n_parts + 1).astype(np.int64)
+    out = []
+    for qa, qb in zip(qcut[:-1], qcut[1:]):
+        ma, mb = int(qoffs[qa]), int(qoffs[qb])
+        ba, bb = int(roffs[ma]), int(roffs[mb])
+        ro = (roffs[ma:mb + 1] - np.uint64(ba)).astype(np.uint64)
+        qo = (qoffs[qa:qb + 1] - np.uint32(ma)).astype(np.uint32)
+        out.append((int(qa), int(qb), mb - ma, ba, bb, ro, qo))
+    return out
 
 
 # ------------------------------------------- build primitive comparison
