@@ -600,15 +600,20 @@ __device__ __forceinline__ bool same_feature(uint64_t x, uint32_t hk) {
     return x != SENTINEL_PAIR && hk_of(x) == hk;
 }
 
+// The pair, its predecessor and the pair cap places earlier are loaded
+// together (each only bounded by the array), so that the loads of all the
+// items a thread handles are in flight at once.
 __device__ __forceinline__ void fin_flags(const uint64_t* __restrict__ a, uint64_t n, uint32_t cap, uint64_t e,
                                           uint64_t& v, bool& st, bool& kept, bool& over) {
     st = kept = over = false;
-    if (e >= n) return;
-    v = a[e];
-    if (v == SENTINEL_PAIR) return;
+    const bool in = e < n;
+    v = in ? a[e] : SENTINEL_PAIR;
+    const uint64_t prev = (in && e > 0) ? a[e - 1] : SENTINEL_PAIR;
+    const uint64_t back = (in && e >= cap) ? a[e - cap] : SENTINEL_PAIR;
+    if (!in || v == SENTINEL_PAIR) return;
     const uint32_t hk = hk_of(v);
-    st = e == 0 || !same_feature(a[e - 1], hk);
-    const bool dropped = e >= cap && same_feature(a[e - cap], hk);
+    st = e == 0 || !same_feature(prev, hk);
+    const bool dropped = e >= cap && same_feature(back, hk);
     kept = !dropped;
     // the first dropped pair of an overflowing run: the pair cap earlier starts the run
     over = dropped && (e == cap || !same_feature(a[e - cap - 1], hk));
