@@ -18,6 +18,8 @@ CPU); the protocol functions drive any shard object with the four methods of
 """
 from __future__ import annotations
 
+import json
+
 import numpy as np
 
 
@@ -131,6 +133,28 @@ class GpuShard:
         mc.mc_merge_candidates(self.db.handle, cp, nq, lists, bases, self.taxon_global, self.taxon_global.numel(),
                                label, hits, top, cands, stream=self.stream)
         return label[:nq], hits[:nq], top[:nq], cands[: nq * max_candidates * 4].reshape(nq, max_candidates, 4)
+
+    def save(self, path: str):
+        """Writes this shard (Section 4.3: each GPU keeps its partition): its
+        condensed layout at `path` (mc_db_save) and its global id base at
+        `path + ".shard.json"`."""
+        self.db.save(path)
+        with open(path + ".shard.json", "w") as f:
+            json.dump({"merge_base": self.merge_base}, f)
+
+    @classmethod
+    def load(cls, mc, path: str, taxon_global, stream=None) -> "GpuShard":
+        """A shard written by save(), ready to classify and merge (its
+        database finalized; taxon_global as in the constructor)."""
+        with open(path + ".shard.json") as f:
+            meta = json.load(f)
+        s = cls.__new__(cls)
+        s.mc = mc
+        s.merge_base = int(meta["merge_base"])
+        s.taxon_global = taxon_global
+        s.stream = stream
+        s.db = mc.Database.load(path, stream=stream)
+        return s
 
     def free(self):
         self.db.free()

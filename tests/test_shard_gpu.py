@@ -111,3 +111,37 @@ def test_feature_counts_capacity_and_state(mc):
         assert (gk == ok).all() and (gc == oc).all() and (gl == ol).all()
     finally:
         s.free()
+
+
+def test_saved_and_loaded_shards_merge_to_the_single_oracle(mc, tmp_path):
+    """Partitions saved one file per shard and loaded again (Section 4.3)
+    classify and merge exactly like the single database."""
+    from paper_2106_08150_gb300.shard import GpuShard
+    w = _workload(6)
+    shards = _shards(mc, w, 3)
+    try:
+        counts = [s.feature_counts() for s in shards]
+        for r, s in enumerate(shards):
+            s.finalize_after(counts[:r])
+        for r, s in enumerate(shards):
+            s.save(str(tmp_path / f"shard{r}.mcdb"))
+    finally:
+        for s in shards:
+            s.free()
+    tg = dev(w.taxon_of_target)
+    loaded = [GpuShard.load(mc, str(tmp_path / f"shard{r}.mcdb"), tg) for r in range(3)]
+    try:
+        cp = dict(w.cls_params, max_candidates=4)
+        d_r, d_ro, d_qo = dev(w.reads), dev(w.roffs), dev(w.qoffs)
+        lists = [s.classify_cands(d_r, d_ro, d_qo, **cp) for s in loaded]
+        label, hits, top, cands = loaded[0].merge(lists, [s.merge_base for s in loaded], **cp)
+        whole = oracle.DB(w.genomes, w.goffs, **w.db_params)
+        want = whole.classify(w.parent, w.taxon_of_target, w.reads, w.roffs, w.qoffs, with_cands=True, **cp)
+        assert [s.merge_base for s in loaded] == sorted(s.merge_base for s in loaded)
+        assert (host_u32(label) == want[0]).all()
+        assert (host_u32(hits) == want[1]).all()
+        assert (host_u32(top) == want[2]).all()
+        assert (host_u32(cands).reshape(want[-1].shape) == want[-1]).all()
+    finally:
+        for s in loaded:
+            s.free()
